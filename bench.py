@@ -1,0 +1,367 @@
+"""Benchmark: candidate pairs refined per second on the pathology-shaped join.
+
+Workload (one step = the join's whole query path over one batch): A = 10,000
+nucleus meshes (noisy icospheres, level 4/5, 5,120-20,480 triangles), B = 500
+vessel meshes (16-sided capped tubes along cubic B-splines, 10k-50k
+triangles), one unit cube on the 2^18 grid.  Per step: the device bounding-box
+filter join produces the candidate pairs, every candidate is refined
+(bidirectional edge piercing with early exit, then +z parity containment) and
+the intersecting pairs are compacted.  Meshes and their BVHs are resident
+(loading and BVH build are reported separately, as in the paper's measurement
+of query time).
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+Prints one JSON line (rank 0).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import re
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "candidate pairs refined/s & segment–tri tests/s; p50/p99 query latency"
+UNIT = "pairs/s"
+WORKLOAD = ("pathology join: 10,000 nuclei (icosphere L4/L5, 10% smooth radial noise, "
+            "log-normal radius mean 1/200 box) x 500 vessels (16-sided capped tubes on cubic "
+            "B-splines, 10k-50k triangles, radius 1/300-1/100 box), 2^18 grid, float32, "
+            "intersects predicate, candidates from the device bounding-box join")
+
+
+def _env_int(k, d):
+    try:
+        return int(os.environ.get(k, d))
+    except ValueError:
+        return d
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle samples during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device: int):
+        self.device = device
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.device), "--query-gpu=" + self.Q,
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if not self.proc:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [x.strip() for x in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx),
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def make_workload(seed: int):
+    from paper_2609_24513_gb300 import synth
+    return synth.pathology(seed)
+
+
+def profile_traffic(kernel_src: str):
+    """DRAM bytes per refine launch from the committed ncu summary, if that
+    summary was taken on the current kernel source (else None)."""
+    p = os.path.join(ROOT, "profiles", "k_refine_pathology.md")
+    if not os.path.exists(p):
+        return None
+    txt = open(p).read()
+    m = re.search(r"source sha1:\s*([0-9a-f]{12})", txt)
+    t = re.search(r"dram bytes per full launch:\s*([0-9.eE+]+)", txt)
+    if not m or not t:
+        return None
+    h = hashlib.sha1(open(kernel_src, "rb").read()).hexdigest()[:12]
+    return float(t.group(1)) if h == m.group(1) else None
+
+
+def cpu_baseline(A, B, cand, seconds: float, seed: int):
+    """The oracle (tier 2, single-threaded) on a bounded random sample."""
+    import oracle
+    rng = np.random.default_rng(seed)
+    order = rng.permutation(len(cand))
+    done, tests, t0 = 0, 0, time.perf_counter()
+    while done < len(order) and time.perf_counter() - t0 < seconds:
+        blk = cand[order[done:done + 8]]
+        _, st = oracle.join(A, B, blk, tier=2, stats=True)
+        tests += int(st[0])
+        done += len(blk)
+    el = time.perf_counter() - t0
+    return {"value": done / el, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": "%d of %d candidate pairs drawn uniformly (seed %d), oracle tier 2 "
+                      "(bounding-box-pruned brute force, exact int64), %.1f s"
+                      % (done, len(cand), seed, el),
+            "segtri_tests_per_s": tests / el}
+
+
+def run_reference(args, rank, world):
+    """Reference arm: the CPU oracle, timed on the host cores."""
+    if rank != 0:
+        return
+    import oracle
+    from paper_2609_24513_gb300 import synth
+    oracle.build()
+    A, B = make_workload(args.seed)
+    cand = oracle.mbb_candidates(A, B)
+    rng = np.random.default_rng(args.seed)
+    per_step = max(1.0, args.ref_step_s)
+    times, counts = [], []
+    for step in range(args.warmup + args.steps):
+        sel = cand[rng.permutation(len(cand))]
+        t0 = time.perf_counter()
+        n = 0
+        while n < len(sel) and time.perf_counter() - t0 < per_step:
+            oracle.join(A, B, sel[n:n + 8], tier=2)
+            n += len(sel[n:n + 8])
+        el = time.perf_counter() - t0
+        if step >= args.warmup:
+            times.append(el)
+            counts.append(n)
+    value = sum(counts) / sum(times)
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
+            "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1000 * sum(times) / len(times), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "int64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "candidates": int(len(cand)),
+                       "step": "bounded sample of the candidates, %.0f s of oracle work" % per_step},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": "%d candidate pairs per step, uniform random" % int(np.mean(counts))},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def run_ours(args, rank, world, local_rank):
+    import torch
+
+    from paper_2609_24513_gb300 import pierce
+    torch.cuda.set_device(local_rank)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
+    t0 = time.perf_counter()
+    A, B = make_workload(args.seed + 1000 * rank)     # weak scaling: one workload per rank
+    gen_s = time.perf_counter() - t0
+    ctx = pierce.Context(local_rank)
+    stream = torch.cuda.current_stream()
+    t0 = time.perf_counter()
+    ha, hb = ctx.load(A), ctx.load(B)
+    load_s = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    ctx.build(ha, args.width, args.leaf)
+    ctx.build(hb, args.width, args.leaf)
+    build_s = time.perf_counter() - t0
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    opts = dict(width=args.width, leaf_size=args.leaf, warps_per_pair=args.warps,
+                use_graph=args.graph, out_host=False, stream=stream)
+
+    def step():
+        res = pierce.pj_join_intersects_ex(ctx.h, ha, hb, **opts)
+        info = (int(res.n_candidates), int(res.count), res.refine_ms)
+        pierce.pj_free_pairs(ctx.h, res)
+        return info
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    ctx.reset_counters()
+    clocks = ClockSampler(local_rank)
+    clocks.start()
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    total_ms, refine_ms, C, K = 0.0, 0.0, 0, 0
+    for _ in range(args.steps):
+        flush.zero_()                                   # evict L2 between steps
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        C, K, rms = step()
+        e1.record(stream)
+        e1.synchronize()
+        total_ms += e0.elapsed_time(e1)
+        refine_ms += rms
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    clk = clocks.stop()
+    cnt = ctx.counters()
+    ms_step = total_ms / args.steps
+    if dist:
+        t = torch.tensor([ms_step], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms_step = float(t.item())
+    value = world * C / (ms_step / 1000.0)
+    segtri_s = cnt["segtri_tests"] / (total_ms / 1000.0)
+    launches = cnt["kernel_launches"]
+    # dominant kernel: the refinement launch
+    refine_avg = refine_ms / args.steps
+    bytes_launch = cnt["bytes_fetched"] / args.steps
+    peak, peak_kind = measured_peaks()
+    achieved = bytes_launch / (refine_avg / 1000.0) / 1e9
+    traffic = profile_traffic(os.path.join(ROOT, "paper_2609_24513_gb300", "csrc", "pj_join.cu"))
+
+    # end to end: candidates from pinned host memory, pairs back to the host
+    cand_host = _candidates_host(ctx, ha, hb, C)
+    pinned = torch.from_numpy(cand_host).pin_memory()
+    cand_np = pinned.numpy()
+    e2e_t, e2e_k = 0.0, 0
+    for i in range(args.warmup + args.steps):
+        flush.zero_()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        r = pierce.pj_join_intersects_ex(ctx.h, ha, hb, cand=cand_np, width=args.width,
+                                         leaf_size=args.leaf, warps_per_pair=args.warps,
+                                         out_host=True, stream=stream)
+        pairs = pierce.pairs_to_numpy(r)
+        pierce.pj_free_pairs(ctx.h, r)
+        el = time.perf_counter() - t0
+        if i >= args.warmup:
+            e2e_t += el
+            e2e_k = len(pairs)
+    e2e_value = world * len(cand_np) / (e2e_t / args.steps)
+
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32+int64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "candidates_per_step": C, "pairs_per_step": K,
+                       "bvh_width": args.width, "leaf_size": args.leaf,
+                       "warps_per_pair": args.warps or 1, "cuda_graph": bool(args.graph),
+                       "l2": "256 MB buffer written between timed steps",
+                       "setup_s": {"generate": round(gen_s, 2), "load": round(load_s, 3),
+                                   "bvh_build": round(build_s, 3)}},
+            "segtri_tests_per_s": segtri_s,
+            "exact_fallback_frac": cnt["exact_fallbacks"] / max(1, cnt["segtri_tests"]),
+            "counters_per_step": {k: v / args.steps for k, v in cnt.items()},
+            "gpu_launches": int(launches),
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak, "traffic": traffic,
+                         "kernel": "k_refine", "refine_ms": refine_avg,
+                         "peak_source": peak_kind,
+                         "bytes_per_launch": bytes_launch},
+            "e2e": {"value": e2e_value, "unit": UNIT,
+                    "h2d_bytes_per_step": int(cand_np.nbytes),
+                    "d2h_bytes_per_step": int(8 * e2e_k + 8)},
+            "clocks": clk}
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(A, B, cand_host, args.cpu_seconds, args.seed)
+    ctx.close()
+    if dist:
+        dist.destroy_process_group()
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
+def _candidates_host(ctx, ha, hb, n):
+    """The bounding-box candidates as a host array (the end-to-end query input),
+    from the mesh boxes the library computed at load time."""
+    return _mbb_host(ctx, ha, hb, n)
+
+
+def _mbb_host(ctx, ha, hb, n):
+    from paper_2609_24513_gb300 import pierce
+    aabb_a, _, _ = pierce.pj_export_mesh_data(ctx.h, ha, _nm(ctx, ha), _nt(ctx, ha))
+    aabb_b, _, _ = pierce.pj_export_mesh_data(ctx.h, hb, _nm(ctx, hb), _nt(ctx, hb))
+    out = []
+    for i in range(len(aabb_a)):
+        a = aabb_a[i]
+        ok = np.all((a[:3] <= aabb_b[:, 3:]) & (aabb_b[:, :3] <= a[3:]), axis=1)
+        js = np.nonzero(ok)[0]
+        out.append(np.stack([np.full(len(js), i), js], axis=1))
+    cand = np.concatenate(out).astype(np.int32)
+    assert len(cand) == n
+    return np.ascontiguousarray(cand)
+
+
+def _nm(ctx, h):
+    from paper_2609_24513_gb300 import pierce
+    return pierce.pj_dataset_info_get(ctx.h, h)["n_meshes"]
+
+
+def _nt(ctx, h):
+    from paper_2609_24513_gb300 import pierce
+    return pierce.pj_dataset_info_get(ctx.h, h)["n_tris"]
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--seed", type=int, default=2001)
+    ap.add_argument("--width", type=int, default=4)
+    ap.add_argument("--leaf", type=int, default=4)
+    ap.add_argument("--warps", type=int, default=0)
+    ap.add_argument("--graph", type=int, default=1)
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--ref-step-s", type=float, default=10.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    rank, world = _env_int("RANK", 0), _env_int("WORLD_SIZE", 1)
+    local_rank = _env_int("LOCAL_RANK", 0)
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+    else:
+        run_ours(args, rank, world, local_rank)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,272 @@
+/*
+ * pierce.h -- C ABI of the GB300 (sm_103a) refinement library for the 3-D
+ * intersection join of closed triangle meshes.
+ *
+ * Method (paper "Pierce: GPU Ray Tracing for Spatial Joins over Complex 3D
+ * Data"): a pair of closed meshes (A, B) intersects when an edge of one mesh
+ * pierces a triangle of the other (Sec. 3.1 observation 1; both directions,
+ * Sec. 3.2 "Bidirectional tracing"), or when one mesh lies inside the other
+ * by the parity of a +z ray cast from a representative vertex (Alg. 2,
+ * Sec. 3.3); the intersection join is the union of the two (Sec. 3.4).
+ *
+ * Exact semantics fixed by this library (the paper works in FP32):
+ *   - coordinates are integers in [0, 2^18) stored as float32, so every
+ *     orientation sign is decided exactly (FP32 filter, int64 fallback);
+ *   - "pierce" = the open edge segment crosses the open triangle
+ *     transversally (tangential contact never counts, Sec. 3.6);
+ *   - the representative vertex of B w.r.t. A is B's lexicographically
+ *     smallest (x, y, z) vertex that is not on A's closed surface; the +z ray
+ *     is perturbed symbolically to (x + e, y + e^2).
+ *
+ * Conventions for every function:
+ *   - the return value is a pj_status; PJ_OK on success.  No C++ exception
+ *     crosses this interface.  pj_last_error() gives a message for the last
+ *     failure on a context.
+ *   - "device" pointers are CUDA device pointers on the context's device;
+ *     "host" pointers are ordinary (pageable or pinned) host memory.
+ *   - the library copies every input it keeps; the caller keeps ownership of
+ *     its buffers and may free them when the call returns.
+ *   - calls on one context are serialised by an internal lock, except
+ *     pj_poll/pj_submit which may be called from any thread.
+ */
+#ifndef PIERCE_H
+#define PIERCE_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef int32_t pj_status;
+
+enum {
+  PJ_OK = 0,
+  PJ_ERR_INVALID_ARG = 1,   /* bad pointer, size, handle or option          */
+  PJ_ERR_NOT_QUANTIZED = 2, /* a coordinate is not an integer in [0, 2^18)  */
+  PJ_ERR_NOT_MANIFOLD = 3,  /* an undirected edge is not used exactly twice,
+                               or a triangle repeats a vertex                */
+  PJ_ERR_NO_MEMORY = 4,     /* a device or host allocation failed           */
+  PJ_ERR_BUSY = 5,          /* serving: the query can never fit the budget  */
+  PJ_ERR_TIMEOUT = 6,       /* a bounded wait gave up                       */
+  PJ_ERR_CUDA = 7,          /* a CUDA runtime call failed                   */
+  PJ_ERR_INTERNAL = 8,      /* a device-side capacity check failed          */
+  PJ_PENDING = 9            /* serving: the query has not finished yet      */
+};
+
+typedef struct pj_ctx pj_ctx;
+typedef int32_t pj_dataset;         /* handle returned by pj_load_meshes */
+
+/* Context configuration.  Zero-initialise and set what you need. */
+typedef struct {
+  int32_t device;            /* CUDA device ordinal                            */
+  int32_t reserved0;
+  int64_t budget_bytes;      /* serving admission budget; 0 = 40 GiB           */
+  int64_t wait_limit_us;     /* bound on host waits in pj_poll(block); 0 = 10 s */
+  int32_t serve_streams;     /* concurrent serving batches; 0 = 4              */
+  int32_t reserved1;
+} pj_config;
+
+/* BVH shape: width W in {2, 4, 8} children per node, leaf size L in
+ * {1, 2, 4, 8} triangles.  Zero fields pick W = 4, L = 4. */
+typedef struct {
+  int32_t width;
+  int32_t leaf_size;
+} pj_bvh_params;
+
+enum { PJ_LEAF_FILTERED = 0, PJ_LEAF_EXACT = 1 };
+enum { PJ_LAUNCH_PERSISTENT = 0, PJ_LAUNCH_PER_PAIR = 1 };
+
+/* Options of one join.  Zero-initialised = defaults. */
+typedef struct {
+  int32_t width;            /* which cached BVH to use; 0 = the dataset's last build */
+  int32_t leaf_size;
+  int32_t warps_per_pair;   /* 1, 2 or 4 warps cooperate on one pair; 0 = 1 */
+  int32_t leaf_mode;        /* PJ_LEAF_FILTERED (FP32 filter, int64 fallback)
+                               or PJ_LEAF_EXACT (int64 only)                 */
+  int32_t launch_mode;      /* PJ_LAUNCH_PERSISTENT: one work-stealing launch;
+                               PJ_LAUNCH_PER_PAIR: one launch per candidate  */
+  int32_t use_graph;        /* replay the device part as a captured CUDA graph */
+  int32_t out_host;         /* 1: result pairs in library-owned host memory   */
+  int32_t keep_flags;       /* 1: also return the per-candidate result bytes  */
+} pj_join_opts;
+
+/* Result of a join.  Owned by the library until pj_free_pairs. */
+typedef struct {
+  int64_t count;            /* number of intersecting pairs K                 */
+  int32_t *pairs;           /* K x 2 (idA, idB), in candidate order: sorted
+                               and unique when the candidates are            */
+  int32_t on_device;        /* 1 if pairs is a device pointer                 */
+  int32_t reserved;
+  int64_t n_candidates;     /* C: candidates refined                          */
+  uint8_t *flags;           /* device, C bytes (only with keep_flags)         */
+  float device_ms;          /* device time of the join, candidates to
+                               compacted pairs (CUDA events on the stream)    */
+  float mbb_ms;             /* of which: bounding-box filter join             */
+  float refine_ms;          /* of which: refinement (crossing + parity)       */
+  float compact_ms;         /* of which: compaction                           */
+  void *impl;
+} pj_pairs;
+
+/* Device counters, accumulated over joins until pj_reset_counters. */
+typedef struct {
+  uint64_t pairs_refined;       /* candidate pairs processed                    */
+  uint64_t node_pairs;          /* (node, node) traversal steps                 */
+  uint64_t box_tests;           /* child-box overlap tests                      */
+  uint64_t leaf_pairs;          /* (leaf, leaf) pairs tested                    */
+  uint64_t edge_slab_tests;     /* segment vs leaf-box slab tests               */
+  uint64_t segtri_tests;        /* strict segment/triangle tests                */
+  uint64_t exact_fallbacks;     /* of those, decided by the int64 path          */
+  uint64_t parity_rays;         /* +z parity traversals                         */
+  uint64_t parity_nodes;        /* nodes visited by parity traversals           */
+  uint64_t parity_tri_tests;    /* triangles tested by parity traversals        */
+  uint64_t bytes_fetched;       /* algorithmic bytes: nodes, triangles, vertices */
+  uint64_t pairs_hit;           /* pairs found intersecting                     */
+  uint64_t kernel_launches;     /* kernels launched by joins (host count)       */
+  uint64_t reserved[3];
+} pj_counters;
+
+/* Dataset summary. */
+typedef struct {
+  int64_t n_meshes, n_verts, n_tris, n_edges;
+  int64_t bvh_nodes;            /* wide nodes of the last build (0 if none)     */
+  int32_t bvh_width, bvh_leaf_size;
+  int32_t bvh_max_depth;        /* deepest wide-node level (root = 1)           */
+  int32_t reserved;
+  int64_t device_bytes;         /* device memory held by the dataset            */
+} pj_dataset_info;
+
+/* --------------------------------------------------------------------------
+ * Context
+ * ------------------------------------------------------------------------ */
+
+/* Create a context on cfg->device (cfg may be NULL: device 0, defaults).
+ * *out receives the context; free it with pj_destroy. */
+pj_status pj_create(const pj_config *cfg, pj_ctx **out);
+
+/* Destroy a context and free every dataset, BVH and result it owns.  Results
+ * not yet freed become invalid. */
+pj_status pj_destroy(pj_ctx *ctx);
+
+/* Message of the last failure on ctx (never NULL; "" if none).  The string is
+ * owned by the context and valid until the next call on it. */
+const char *pj_last_error(pj_ctx *ctx);
+
+/* --------------------------------------------------------------------------
+ * Loading (paper Sec. 4.2 "Preprocessing" / "Loading": flat triangles with a
+ * triangle-to-object map and per-object unique edges, Sec. 3.1 Step I)
+ * ------------------------------------------------------------------------ */
+
+/* Load a dataset of n_meshes closed meshes.
+ *   xyz            n_verts x 3 float32 (x, y, z interleaved); every value an
+ *                  integer in [0, 2^18)                 -> else PJ_ERR_NOT_QUANTIZED
+ *   tris           n_tris x 3 int32, vertex ids local to the mesh
+ *   mesh_vert_off  n_meshes + 1 int64, mesh k owns vertices [off[k], off[k+1])
+ *   mesh_tri_off   n_meshes + 1 int64, mesh k owns triangles [off[k], off[k+1])
+ *   ptr_is_device  0: the four arrays are host pointers; 1: xyz and tris are
+ *                  device pointers (the offsets are always host pointers)
+ * Each mesh must be a closed 2-manifold: every undirected edge used by
+ * exactly two of its triangles, no triangle repeating a vertex
+ * (-> PJ_ERR_NOT_MANIFOLD; pj_last_error names the mesh).  Meshes hold at most
+ * 2^28 - 2 triangles; a dataset at most 2^31 - 1 triangles and vertices.
+ * The library computes per-mesh bounding boxes, the unique edges (each owned
+ * by one triangle) and each mesh's vertices in lexicographic order.
+ * *out receives the dataset handle.  Synchronous. */
+pj_status pj_load_meshes(pj_ctx *ctx, const float *xyz, int64_t n_verts,
+                         const int32_t *tris, int64_t n_tris,
+                         const int64_t *mesh_vert_off,
+                         const int64_t *mesh_tri_off, int64_t n_meshes,
+                         int32_t ptr_is_device, pj_dataset *out);
+
+/* Free a dataset and its BVHs. */
+pj_status pj_free_dataset(pj_ctx *ctx, pj_dataset ds);
+
+/* Build (or reuse from the cache) the per-mesh BVHs of a dataset: an LBVH
+ * over 30-bit Morton codes of triangle centroids (Karras 2012), exact integer
+ * boxes, collapsed to W-wide nodes with leaves of at most L triangles.  The
+ * BVH stays resident, cached per (W, L); params may be NULL (W = 4, L = 4).
+ * Synchronous. */
+pj_status pj_build_bvh(pj_ctx *ctx, pj_dataset ds, const pj_bvh_params *params);
+
+pj_status pj_dataset_info_get(pj_ctx *ctx, pj_dataset ds, pj_dataset_info *out);
+
+/* --------------------------------------------------------------------------
+ * Join (paper Sec. 3.4 intersection join over candidate pairs)
+ * ------------------------------------------------------------------------ */
+
+/* Refine candidate pairs (idA in a, idB in b) with the intersection
+ * predicate and return the intersecting ones.
+ *   cand_pairs  n_cand x 2 int32 host pointer, or NULL: the candidates are
+ *               then produced on the device by the bounding-box filter join
+ *               (closed mesh boxes meet), in (idA, idB) lexicographic order
+ *   self_join   1: a == b and only pairs with idA < idB are considered
+ *   cuda_stream cudaStream_t to order the work on (NULL: the context's stream)
+ *   out         filled with the result; free with pj_free_pairs
+ * Both datasets need a BVH (pj_build_bvh).  Returns when the result is
+ * complete (the stream is synchronised). */
+pj_status pj_join_intersects(pj_ctx *ctx, pj_dataset a, pj_dataset b,
+                             const int32_t *cand_pairs, int64_t n_cand,
+                             int32_t self_join, void *cuda_stream,
+                             pj_pairs *out);
+
+/* As pj_join_intersects, with options and per-candidate translations.
+ *   cand_offsets  NULL, or n_cand x 3 int32 host pointer: candidate c tests
+ *                 A_i against B_j translated by cand_offsets[c] (integer grid
+ *                 units; the translated mesh must stay in [0, 2^18)).  Lets
+ *                 many placements share one resident mesh and BVH.
+ *   cand_on_device 1: cand_pairs / cand_offsets are device pointers.
+ *   opts          may be NULL (defaults). */
+pj_status pj_join_intersects_ex(pj_ctx *ctx, pj_dataset a, pj_dataset b,
+                                const int32_t *cand_pairs,
+                                const int32_t *cand_offsets, int64_t n_cand,
+                                int32_t cand_on_device, int32_t self_join,
+                                const pj_join_opts *opts, void *cuda_stream,
+                                pj_pairs *out);
+
+/* Free a join result. */
+pj_status pj_free_pairs(pj_ctx *ctx, pj_pairs *res);
+
+/* --------------------------------------------------------------------------
+ * Counters and diagnostics
+ * ------------------------------------------------------------------------ */
+
+pj_status pj_get_counters(pj_ctx *ctx, pj_counters *out);
+pj_status pj_reset_counters(pj_ctx *ctx);
+
+/* Leaf predicate on explicit segments and triangles (all device pointers,
+ * float32 integer-valued coordinates): res[k] = 1 if the open segment
+ * (p[k], q[k]) crosses the open triangle (a[k], b[k], c[k]) transversally.
+ * pq: n x 6 (p then q), abc: n x 9.  mode: PJ_LEAF_FILTERED or
+ * PJ_LEAF_EXACT.  n_fallback (host, may be NULL) receives how many tests the
+ * FP32 filter could not decide. */
+pj_status pj_segtri_batch(pj_ctx *ctx, const float *pq, const float *abc,
+                          int64_t n, int32_t mode, uint8_t *res,
+                          int64_t *n_fallback, void *cuda_stream);
+
+/* Copy a dataset's BVH (built with width W, leaf size L) to host buffers for
+ * inspection.  Pass NULL buffers to query the sizes first.
+ *   nodes      n_nodes x (7 W) float/int32 words per node: lo x/y/z[W],
+ *              hi x/y/z[W], child[W] (child: -1 empty; >= 0 wide node;
+ *              bit 31 set: leaf with first sorted triangle (bits 3-30) and
+ *              count - 1 (bits 0-2))
+ *   roots      n_meshes int32 root node per mesh
+ *   tri_order  n_tris int32: mesh-local triangle id at each sorted position
+ * *n_nodes receives the node count. */
+pj_status pj_export_bvh(pj_ctx *ctx, pj_dataset ds, int32_t width,
+                        int32_t leaf_size, int32_t *nodes, int32_t *roots,
+                        int32_t *tri_order, int64_t *n_nodes);
+
+/* Copy per-mesh data computed at load time to host buffers (any may be NULL):
+ *   aabb       n_meshes x 6 float (lo x, y, z, hi x, y, z)
+ *   lex_first  n_meshes int32: mesh-local id of the lexicographically
+ *              smallest vertex
+ *   edge_owner n_tris uint8: bit k set if the triangle owns its edge
+ *              (v_k, v_(k+1) mod 3) in the unique-edge set */
+pj_status pj_export_mesh_data(pj_ctx *ctx, pj_dataset ds, float *aabb,
+                              int32_t *lex_first, uint8_t *edge_owner);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* PIERCE_H */

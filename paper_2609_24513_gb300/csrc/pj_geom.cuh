@@ -1,0 +1,293 @@
+// Device geometry for the refinement kernels: exact orientation signs on the
+// 2^18 integer grid (FP32 filter with a per-test error bound, int64 fallback),
+// the strict segment/triangle test, the perturbed +z parity ray, the closed
+// point-on-triangle test and a conservative segment/box slab test.
+//
+// Paper: the edge ray of Sec. 3.1 Step I (origin v_a, extent |v_b - v_a|) is
+// kept as the unnormalised segment p + t (q - p), t in [0, 1]; a hit in
+// Step II is decided by the exact sign pattern of five orientations instead
+// of an FP32 ray/triangle distance, which makes the watertightness the
+// paper gets from its ray tracer (Sec. 3.6 "Robustness") exact.
+#pragma once
+#include <stdint.h>
+
+namespace pj {
+
+struct F3 {
+  float x, y, z;
+};
+struct I3 {
+  int x, y, z;
+};
+
+__device__ __forceinline__ F3 mkf3(float x, float y, float z) {
+  F3 r;
+  r.x = x;
+  r.y = y;
+  r.z = z;
+  return r;
+}
+__device__ __forceinline__ F3 sub(F3 a, F3 b) {
+  // exact: both operands are integers below 2^19 in magnitude
+  return mkf3(__fsub_rn(a.x, b.x), __fsub_rn(a.y, b.y), __fsub_rn(a.z, b.z));
+}
+__device__ __forceinline__ F3 add(F3 a, F3 b) {
+  return mkf3(__fadd_rn(a.x, b.x), __fadd_rn(a.y, b.y), __fadd_rn(a.z, b.z));
+}
+__device__ __forceinline__ I3 toi(F3 a) {
+  I3 r;
+  r.x = __float2int_rn(a.x);
+  r.y = __float2int_rn(a.y);
+  r.z = __float2int_rn(a.z);
+  return r;
+}
+
+// ---------------------------------------------------------------------------
+// FP32 filter.
+//
+// A triple product x . (y x z) of exact FP32 integer vectors, evaluated as
+// sum_i x_i * (y_j z_k - y_k z_j) with round-to-nearest and no contraction,
+// differs from the exact value by at most about 5u * perm (u = 2^-24,
+// perm = sum_i |x_i| (|y_j z_k| + |y_k z_j|)): 2u per minor, u per product
+// with x_i, u per each of the two additions.  This is the stage-A argument of
+// Shewchuk, "Adaptive Precision Floating-Point Arithmetic and Fast Robust
+// Geometric Predicates" (1997), specialised to single precision.  The filter
+// uses 8u = 2^-21 times the permanent computed in FP32, which covers the
+// rounding of the permanent itself.  A sign is certified only when
+// |det| > bound; everything else goes to the int64 path.
+// ---------------------------------------------------------------------------
+#define PJ_FILTER_COEF 4.76837158203125e-07f /* 2^-21 */
+
+struct CrossP {
+  F3 m;   // y x z (rounded)
+  F3 pm;  // |y_j z_k| + |y_k z_j| per component (rounded)
+};
+
+__device__ __forceinline__ CrossP cross_p(F3 y, F3 z) {
+  float p1 = __fmul_rn(y.y, z.z), p2 = __fmul_rn(y.z, z.y);
+  float p3 = __fmul_rn(y.z, z.x), p4 = __fmul_rn(y.x, z.z);
+  float p5 = __fmul_rn(y.x, z.y), p6 = __fmul_rn(y.y, z.x);
+  CrossP c;
+  c.m = mkf3(__fsub_rn(p1, p2), __fsub_rn(p3, p4), __fsub_rn(p5, p6));
+  c.pm = mkf3(__fadd_rn(fabsf(p1), fabsf(p2)), __fadd_rn(fabsf(p3), fabsf(p4)),
+              __fadd_rn(fabsf(p5), fabsf(p6)));
+  return c;
+}
+
+// x . c.m and its error bound
+__device__ __forceinline__ void dot_p(F3 x, const CrossP &c, float &det,
+                                     float &err) {
+  det = __fadd_rn(__fadd_rn(__fmul_rn(x.x, c.m.x), __fmul_rn(x.y, c.m.y)),
+                  __fmul_rn(x.z, c.m.z));
+  float perm =
+      __fadd_rn(__fadd_rn(__fmul_rn(fabsf(x.x), c.pm.x),
+                          __fmul_rn(fabsf(x.y), c.pm.y)),
+                __fmul_rn(fabsf(x.z), c.pm.z));
+  err = __fmul_rn(perm, PJ_FILTER_COEF);
+}
+
+// certified sign: +1 / -1, or 0 when the filter cannot decide
+__device__ __forceinline__ int cert(float v, float e) {
+  return v > e ? 1 : (v < -e ? -1 : 0);
+}
+
+// ---------------------------------------------------------------------------
+// int64 orientation (exact).  Differences are below 2^19 in magnitude (grid
+// 2^18, translated candidates stay on the grid), 2x2 minors below 2^39 and a
+// triple product below 3 * 2^58.
+// ---------------------------------------------------------------------------
+struct L3 {
+  long long x, y, z;
+};
+__device__ __forceinline__ L3 cross64(I3 a, I3 b) {
+  L3 r;
+  r.x = (long long)a.y * b.z - (long long)a.z * b.y;
+  r.y = (long long)a.z * b.x - (long long)a.x * b.z;
+  r.z = (long long)a.x * b.y - (long long)a.y * b.x;
+  return r;
+}
+__device__ __forceinline__ long long dot64(I3 a, L3 b) {
+  return (long long)a.x * b.x + (long long)a.y * b.y + (long long)a.z * b.z;
+}
+__device__ __forceinline__ I3 isub(I3 a, I3 b) {
+  I3 r;
+  r.x = a.x - b.x;
+  r.y = a.y - b.y;
+  r.z = a.z - b.z;
+  return r;
+}
+__device__ __forceinline__ int sgn64(long long v) { return (v > 0) - (v < 0); }
+
+// Strict crossing from the exact signs.  With A = a - p, B = b - p,
+// C = c - p, d = q - p:  orient(p,q,a,b) = d.(A x B), orient(p,q,b,c) =
+// d.(B x C), orient(p,q,c,a) = d.(C x A), orient(a,b,c,p) = -A.(B x C) and
+// orient(a,b,c,q) = orient(a,b,c,p) + the three former.
+__device__ __forceinline__ bool segtri_exact(F3 pf, F3 qf, F3 af, F3 bf,
+                                             F3 cf) {
+  I3 p = toi(pf), q = toi(qf);
+  I3 A = isub(toi(af), p), B = isub(toi(bf), p), C = isub(toi(cf), p);
+  I3 d = isub(q, p);
+  L3 bc = cross64(B, C);
+  long long u = dot64(d, cross64(A, B));
+  long long v = dot64(d, bc);
+  long long w = dot64(d, cross64(C, A));
+  long long sp = -dot64(A, bc);
+  long long sq = sp + u + v + w;
+  int su = sgn64(u);
+  if (su == 0 || sgn64(v) != su || sgn64(w) != su) return false;
+  int a1 = sgn64(sp), a2 = sgn64(sq);
+  return a1 != 0 && a2 != 0 && a1 != a2;
+}
+
+// Filtered strict test: returns 1 (cross), 0 (no cross) or -1 (undecided by
+// the filter; call segtri_exact).
+__device__ __forceinline__ int segtri_filter(F3 p, F3 q, F3 a, F3 b, F3 c) {
+  F3 d = sub(q, p);
+  F3 A = sub(a, p), B = sub(b, p), C = sub(c, p);
+  // side of p and q w.r.t. the triangle's plane
+  CrossP bc = cross_p(B, C);
+  float dA, eA;
+  dot_p(A, bc, dA, eA);  // -orient(a,b,c,p)
+  F3 Aq = sub(a, q), Bq = sub(b, q), Cq = sub(c, q);
+  CrossP bcq = cross_p(Bq, Cq);
+  float dQ, eQ;
+  dot_p(Aq, bcq, dQ, eQ);  // -orient(a,b,c,q)
+  int sp = -cert(dA, eA), sq = -cert(dQ, eQ);
+  if (sp != 0 && sp == sq) return 0;  // both endpoints strictly on one side
+  CrossP ab = cross_p(A, B), ca = cross_p(C, A);
+  float u, eu, v, ev, w, ew;
+  dot_p(d, ab, u, eu);
+  dot_p(d, bc, v, ev);
+  dot_p(d, ca, w, ew);
+  int su = cert(u, eu), sv = cert(v, ev), sw = cert(w, ew);
+  // two certified, opposite signs among u, v, w: the line misses
+  if ((su > 0 || sv > 0 || sw > 0) && (su < 0 || sv < 0 || sw < 0)) return 0;
+  if (sp == 0 || sq == 0 || su == 0 || sv == 0 || sw == 0) return -1;
+  return sp != sq ? 1 : 0;  // su == sv == sw here
+}
+
+// ---------------------------------------------------------------------------
+// Segment / closed box slab test, conservative: never rejects a box that the
+// exact closed segment meets.  Parameters t = (bound - p) / d use an exact
+// difference and a correctly rounded reciprocal and product, so each has a
+// relative error below 2^-22.9 and keeps its sign; comparing
+// t_enter <= t_exit * (1 + 2^-20) absorbs it (cf. Ize, "Robust BVH Ray
+// Traversal", JCGT 2013).  A zero direction component is decided exactly.
+// ---------------------------------------------------------------------------
+struct Seg {
+  F3 p;
+  F3 inv;   // 1/d per axis (unused where d == 0)
+  int zero; // bit k: d_k == 0
+};
+
+__device__ __forceinline__ Seg make_seg(F3 p, F3 q) {
+  Seg s;
+  s.p = p;
+  F3 d = sub(q, p);
+  s.zero = (d.x == 0.f) | ((d.y == 0.f) << 1) | ((d.z == 0.f) << 2);
+  s.inv = mkf3(d.x == 0.f ? 0.f : __frcp_rn(d.x), d.y == 0.f ? 0.f : __frcp_rn(d.y),
+               d.z == 0.f ? 0.f : __frcp_rn(d.z));
+  return s;
+}
+
+__device__ __forceinline__ void slab_axis(float p, float inv, bool zero,
+                                          float lo, float hi, float &tmin,
+                                          float &tmax) {
+  const float BIG = 1e30f;
+  float t0, t1;
+  if (zero) {
+    t0 = (p >= lo) ? -BIG : BIG;
+    t1 = (p <= hi) ? BIG : -BIG;
+  } else {
+    t0 = __fmul_rn(__fsub_rn(lo, p), inv);
+    t1 = __fmul_rn(__fsub_rn(hi, p), inv);
+  }
+  tmin = fmaxf(tmin, fminf(t0, t1));
+  tmax = fminf(tmax, fmaxf(t0, t1));
+}
+
+__device__ __forceinline__ bool slab_hit(const Seg &s, F3 lo, F3 hi) {
+  float tmin = 0.f, tmax = 1.f;
+  slab_axis(s.p.x, s.inv.x, s.zero & 1, lo.x, hi.x, tmin, tmax);
+  slab_axis(s.p.y, s.inv.y, s.zero & 2, lo.y, hi.y, tmin, tmax);
+  slab_axis(s.p.z, s.inv.z, s.zero & 4, lo.z, hi.z, tmin, tmax);
+  return tmin <= __fmul_rn(tmax, 1.00000095367431640625f);  // 1 + 2^-20
+}
+
+// ---------------------------------------------------------------------------
+// Parity ray (+z from v, perturbed to (x + e, y + e^2)) and point on a closed
+// triangle.  All exact in int64.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ long long o2xy(I3 a, I3 b, I3 c) {
+  return (long long)(b.x - a.x) * (c.y - a.y) -
+         (long long)(b.y - a.y) * (c.x - a.x);
+}
+
+// sign of orient2d_xy(a, b, v + (e, e^2)): the exact value plus the first
+// nonvanishing coefficient of -(b_y - a_y) e + (b_x - a_x) e^2
+__device__ __forceinline__ int side_eps(I3 a, I3 b, I3 v) {
+  long long o = o2xy(a, b, v);
+  if (o != 0) return sgn64(o);
+  if (a.y != b.y) return a.y > b.y ? 1 : -1;
+  return b.x > a.x ? 1 : (b.x < a.x ? -1 : 0);
+}
+
+// orient3d(a, b, c, v) = (v - a) . ((b - a) x (c - a))
+__device__ __forceinline__ long long orient64(I3 a, I3 b, I3 c, I3 v) {
+  return dot64(isub(v, a), cross64(isub(b, a), isub(c, a)));
+}
+
+__device__ __forceinline__ bool ray_up_hit(I3 v, I3 a, I3 b, I3 c) {
+  long long s2 = o2xy(a, b, c);
+  if (s2 == 0) return false;
+  int s = s2 > 0 ? 1 : -1;
+  if (side_eps(a, b, v) != s || side_eps(b, c, v) != s || side_eps(c, a, v) != s)
+    return false;
+  long long o = orient64(a, b, c, v);
+  return o != 0 && sgn64(o) == -s;  // v strictly below the plane
+}
+
+// 2-D closed point-in-triangle in the projection dropping axis `drop`
+__device__ __forceinline__ bool in_tri_2d(I3 v, I3 a, I3 b, I3 c, int drop) {
+  int ax, ay, bx, by, cx, cy, vx, vy;
+  if (drop == 2) {
+    ax = a.x; ay = a.y; bx = b.x; by = b.y; cx = c.x; cy = c.y; vx = v.x; vy = v.y;
+  } else if (drop == 0) {
+    ax = a.y; ay = a.z; bx = b.y; by = b.z; cx = c.y; cy = c.z; vx = v.y; vy = v.z;
+  } else {
+    ax = a.z; ay = a.x; bx = b.z; by = b.x; cx = c.z; cy = c.x; vx = v.z; vy = v.x;
+  }
+  long long area = (long long)(bx - ax) * (cy - ay) - (long long)(by - ay) * (cx - ax);
+  long long e0 = (long long)(bx - ax) * (vy - ay) - (long long)(by - ay) * (vx - ax);
+  long long e1 = (long long)(cx - bx) * (vy - by) - (long long)(cy - by) * (vx - bx);
+  long long e2 = (long long)(ax - cx) * (vy - cy) - (long long)(ay - cy) * (vx - cx);
+  if (area > 0) return e0 >= 0 && e1 >= 0 && e2 >= 0;
+  return e0 <= 0 && e1 <= 0 && e2 <= 0;
+}
+
+// v on the segment hull of collinear points a, b, c
+__device__ __forceinline__ bool on_collinear_hull(I3 v, I3 a, I3 b, I3 c) {
+  int lx = min(a.x, min(b.x, c.x)), hx = max(a.x, max(b.x, c.x));
+  int ly = min(a.y, min(b.y, c.y)), hy = max(a.y, max(b.y, c.y));
+  int lz = min(a.z, min(b.z, c.z)), hz = max(a.z, max(b.z, c.z));
+  if (v.x < lx || v.x > hx || v.y < ly || v.y > hy || v.z < lz || v.z > hz)
+    return false;
+  // a direction along the line: the two extreme corners of the box
+  I3 p0 = a, p1 = (b.x != a.x || b.y != a.y || b.z != a.z) ? b : c;
+  if (p1.x == p0.x && p1.y == p0.y && p1.z == p0.z) return true;  // single point
+  L3 cr = cross64(isub(p1, p0), isub(v, p0));
+  return cr.x == 0 && cr.y == 0 && cr.z == 0;
+}
+
+// v in the closed triangle abc (3-D point set)
+__device__ __forceinline__ bool on_triangle(I3 v, I3 a, I3 b, I3 c) {
+  L3 n = cross64(isub(b, a), isub(c, a));
+  if (n.x == 0 && n.y == 0 && n.z == 0) return on_collinear_hull(v, a, b, c);
+  if (dot64(isub(v, a), n) != 0) return false;
+  long long ax = n.x < 0 ? -n.x : n.x, ay = n.y < 0 ? -n.y : n.y,
+            az = n.z < 0 ? -n.z : n.z;
+  int drop = (az >= ax && az >= ay) ? 2 : (ax >= ay ? 0 : 1);
+  return in_tri_2d(v, a, b, c, drop);
+}
+
+}  // namespace pj

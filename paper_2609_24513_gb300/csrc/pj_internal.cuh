@@ -1,0 +1,134 @@
+// Internal data structures shared by the library's translation units.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <map>
+#include <memory>
+#include <mutex>
+#include <string>
+#include <utility>
+#include <vector>
+
+#include "../../include/pierce.h"
+
+namespace pj {
+
+// ---------------------------------------------------------------------------
+// Encodings
+// ---------------------------------------------------------------------------
+// A wide node of width W is 8 * ceil(7W / 8) 32-bit words (so that nodes
+// start on 32-byte boundaries): lo_x[W] lo_y[W] lo_z[W] hi_x[W] hi_y[W]
+// hi_z[W] child[W] (padding).  A child word is
+//   0xFFFFFFFF                 empty slot (its box is inverted: lo > hi)
+//   < 2^31                     index of a wide node (global in the dataset)
+//   bit 31 | first << 3 | n-1  leaf: n in [1, 8] triangles starting at the
+//                              mesh-local sorted position `first` (< 2^28)
+// A traversal item is a 32-bit word: an internal wide node index, or
+// bit 31 | (node * W + slot) for the leaf held in `slot` of `node`.
+constexpr uint32_t kEmpty = 0xFFFFFFFFu;
+constexpr uint32_t kLeafBit = 0x80000000u;
+
+__host__ __device__ inline int node_stride_words(int W) { return ((7 * W + 7) / 8) * 8; }
+
+// Triangle record in BVH-leaf order: three float4
+//   r0 = (ax, ay, az, bx)  r1 = (by, bz, cx, cy)  r2 = (cz, owner bits, local id, 0)
+// The owner bits (as int) say which of the edges (a,b), (b,c), (c,a) this
+// triangle carries in the mesh's unique-edge set.
+constexpr int kTriRecF4 = 3;
+
+struct Bvh {
+  int W = 0, L = 0;
+  int64_t n_nodes = 0;
+  int max_depth = 0;
+  float *d_nodes = nullptr;        // n_nodes * stride words
+  int32_t *d_roots = nullptr;      // per mesh
+  int32_t *d_tri_order = nullptr;  // sorted position -> global triangle id
+  float4 *d_trirec = nullptr;      // n_tris * 3
+  int64_t bytes = 0;
+};
+
+struct Dataset {
+  int64_t M = 0, V = 0, F = 0, E = 0;
+  float *d_xyz = nullptr;       // V * 3
+  int32_t *d_tris = nullptr;    // F * 3 global vertex ids
+  int64_t *d_voff = nullptr;    // M + 1
+  int64_t *d_toff = nullptr;    // M + 1
+  std::vector<int64_t> h_voff, h_toff;
+  float *d_aabb = nullptr;      // M * 6
+  int32_t *d_lexorder = nullptr;  // V: global vertex ids, per mesh in (x,y,z) order
+  uint8_t *d_emask = nullptr;   // F: owned-edge bits
+  std::map<std::pair<int, int>, Bvh> bvhs;
+  std::pair<int, int> last_bvh{0, 0};
+  int64_t bytes = 0;
+};
+
+// Counter slots (match pj_counters order)
+enum {
+  C_PAIRS = 0, C_NODE_PAIRS, C_BOX_TESTS, C_LEAF_PAIRS, C_SLAB_TESTS,
+  C_SEGTRI, C_FALLBACK, C_PARITY_RAYS, C_PARITY_NODES, C_PARITY_TRIS,
+  C_BYTES, C_HITS, C_NUM = 16
+};
+
+struct Workspace {
+  void *ptr = nullptr;
+  size_t cap = 0;
+};
+
+struct Ctx {
+  int device = 0;
+  int num_sms = 0;
+  cudaStream_t stream = nullptr;
+  std::mutex mu;
+  std::string err;
+  std::map<int, std::unique_ptr<Dataset>> datasets;
+  int next_ds = 1;
+  unsigned long long *d_counters = nullptr;  // C_NUM
+  int *d_err = nullptr;                      // device error word
+  // query workspaces (grown on demand)
+  std::map<std::string, Workspace> ws;
+  void *h_pinned = nullptr;                  // small pinned scratch (counts)
+  pj_config cfg{};
+  // captured graphs keyed by a shape string, with their kernel counts
+  std::map<std::string, cudaGraphExec_t> graphs;
+  std::map<std::string, unsigned long long> graph_kernels;
+  unsigned long long launches = 0;           // kernels launched by joins
+};
+
+// set ctx->err and return code
+pj_status fail(Ctx *c, pj_status code, const std::string &msg);
+pj_status cuda_fail(Ctx *c, cudaError_t e, const char *what);
+void *ws_get(Ctx *c, const char *name, size_t bytes, pj_status *st);
+
+#define PJ_CK(call)                                   \
+  do {                                                \
+    cudaError_t _e = (call);                          \
+    if (_e != cudaSuccess) return cuda_fail(ctx, _e, #call); \
+  } while (0)
+
+// device error codes written by kernels
+enum { DERR_NONE = 0, DERR_STACK = 1, DERR_QUEUE = 2, DERR_OFFSET = 3 };
+
+// build.cu
+pj_status build_bvh(Ctx *ctx, Dataset *ds, int W, int L, cudaStream_t s);
+// join.cu
+pj_status run_join(Ctx *ctx, Dataset *A, Dataset *B, const int32_t *cand,
+                   const int32_t *cand_off, int64_t n_cand, int cand_on_device,
+                   int self_join, const pj_join_opts *opts, cudaStream_t s,
+                   pj_pairs *out);
+pj_status run_segtri_batch(Ctx *ctx, const float *pq, const float *abc,
+                           int64_t n, int mode, uint8_t *res,
+                           int64_t *n_fallback, cudaStream_t s);
+
+// exclusive scan of n int64 values (device), total -> *d_total (device)
+pj_status scan_i64(Ctx *ctx, const int64_t *d_in, int64_t *d_out, int64_t n,
+                   int64_t *d_total, cudaStream_t s);
+
+inline int blocks_for(int64_t n, int t) {
+  int64_t b = (n + t - 1) / t;
+  if (b < 1) b = 1;
+  if (b > (1 << 30)) b = 1 << 30;
+  return (int)b;
+}
+
+}  // namespace pj

@@ -1,0 +1,1091 @@
+// The join's hot path: bounding-box filter join, pair refinement (crossing
+// by edge piercing + containment by +z parity), result compaction.
+//
+// Paper mapping:
+//   - Alg. 1 (edge ray tracing) run in both directions (Sec. 3.2) becomes,
+//     per candidate pair, a simultaneous descent of the two meshes' BVHs: a
+//     node of the source mesh is a packet of edge segments bounded by the
+//     node's box, so a (source node, target node) step prunes every edge of
+//     the packet against the target subtree at once.  At a (leaf, leaf) step
+//     each owned edge of one leaf is slab-tested against the other leaf's
+//     box and then tested exactly against its triangles, in both
+//     directions.  The first crossing ends the pair (warp vote).
+//   - Alg. 2's parity test (Sec. 3.3) runs for pairs without a crossing, in
+//     both directions (Sec. 3.4: not filtered by crossings, but a crossing
+//     already decides the intersection predicate).
+//   - Result materialisation (Sec. 3.5) is one flag per candidate followed
+//     by a prefix-sum compaction, so nothing needs deduplication.
+#include <algorithm>
+#include <cstdio>
+#include <cstring>
+#include <string>
+
+#include "pj_geom.cuh"
+#include "pj_internal.cuh"
+
+namespace pj {
+
+constexpr unsigned FULL = 0xffffffffu;
+
+// ---------------------------------------------------------------------------
+// Exclusive scan of int64 (three-phase: block scan, scan of block sums, add)
+// ---------------------------------------------------------------------------
+constexpr int SCAN_T = 1024;
+
+__device__ __forceinline__ int64_t warp_incl_scan(int64_t v, int lane) {
+  for (int o = 1; o < 32; o <<= 1) {
+    int64_t u = __shfl_up_sync(FULL, v, o);
+    if (lane >= o) v += u;
+  }
+  return v;
+}
+
+// block-wide exclusive scan of one value per thread (blockDim.x == SCAN_T)
+__device__ __forceinline__ int64_t block_excl_scan(int64_t v, int64_t *total) {
+  __shared__ int64_t wsum[32];
+  int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  int64_t inc = warp_incl_scan(v, lane);
+  if (lane == 31) wsum[w] = inc;
+  __syncthreads();
+  if (w == 0) {
+    int64_t s = lane < (int)(blockDim.x >> 5) ? wsum[lane] : 0;
+    s = warp_incl_scan(s, lane);
+    wsum[lane] = s;
+  }
+  __syncthreads();
+  int64_t base = w > 0 ? wsum[w - 1] : 0;
+  if (total) *total = wsum[(blockDim.x >> 5) - 1];
+  __syncthreads();
+  return base + inc - v;
+}
+
+__global__ void k_scan_blocks(const int64_t *in, int64_t *out, int64_t n, int64_t *bsum) {
+  int64_t i = blockIdx.x * (int64_t)SCAN_T + threadIdx.x;
+  int64_t v = i < n ? in[i] : 0;
+  int64_t tot;
+  int64_t e = block_excl_scan(v, &tot);
+  if (i < n) out[i] = e;
+  if (threadIdx.x == 0) bsum[blockIdx.x] = tot;
+}
+
+__global__ void k_scan_add(int64_t *out, int64_t n, const int64_t *boff) {
+  int64_t i = blockIdx.x * (int64_t)SCAN_T + threadIdx.x;
+  if (i < n) out[i] += boff[blockIdx.x];
+}
+
+__global__ void k_scan_total(const int64_t *in, const int64_t *out, int64_t n, int64_t *total) {
+  *total = n > 0 ? out[n - 1] + in[n - 1] : 0;
+}
+
+pj_status scan_i64(Ctx *ctx, const int64_t *d_in, int64_t *d_out, int64_t n,
+                   int64_t *d_total, cudaStream_t s) {
+  // level buffers: block sums and their scans
+  std::vector<int64_t> sizes;
+  int64_t m = n;
+  while (m > SCAN_T) {
+    m = (m + SCAN_T - 1) / SCAN_T;
+    sizes.push_back(m);
+  }
+  int64_t need = 0;
+  for (int64_t z : sizes) need += 2 * z;
+  pj_status st;
+  int64_t *buf = (int64_t *)ws_get(ctx, "scan", sizeof(int64_t) * (size_t)(need + 2), &st);
+  if (!buf) return st;
+  // up-sweep
+  const int64_t *cur_in = d_in;
+  int64_t *cur_out = d_out;
+  int64_t cur_n = n;
+  std::vector<int64_t *> lv_in, lv_out;
+  int64_t off = 0;
+  for (size_t l = 0; l <= sizes.size(); ++l) {
+    int nb = (int)((cur_n + SCAN_T - 1) / SCAN_T);
+    if (nb < 1) nb = 1;
+    int64_t *bsum = buf + need;  // scratch for the final single block
+    if (l < sizes.size()) bsum = buf + off;
+    k_scan_blocks<<<nb, SCAN_T, 0, s>>>(cur_in, cur_out, cur_n, bsum);
+    ++ctx->launches;
+    if (l == sizes.size()) break;
+    int64_t *bscan = buf + off + sizes[l];
+    lv_in.push_back(bsum);
+    lv_out.push_back(bscan);
+    cur_in = bsum;
+    cur_out = bscan;
+    cur_n = sizes[l];
+    off += 2 * sizes[l];
+  }
+  // down-sweep: add scanned block sums
+  for (int l = (int)sizes.size() - 1; l >= 0; --l) {
+    int64_t *target = l == 0 ? d_out : lv_out[l - 1];
+    int64_t tn = l == 0 ? n : sizes[l - 1];
+    int nb = (int)((tn + SCAN_T - 1) / SCAN_T);
+    k_scan_add<<<nb, SCAN_T, 0, s>>>(target, tn, lv_out[l]);
+    ++ctx->launches;
+  }
+  k_scan_total<<<1, 1, 0, s>>>(d_in, d_out, n, d_total);
+  ++ctx->launches;
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "scan");
+  return PJ_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Bounding-box filter join (the paper's filter step, Sec. 1 / Sec. 2):
+// candidates (i, j) whose closed mesh boxes meet, in lexicographic order.
+// ---------------------------------------------------------------------------
+constexpr int MBB_T = 256;
+
+template <bool EMIT>
+__global__ void k_mbb(const float *aabbA, int64_t MA, const float *aabbB, int64_t MB,
+                      int self_join, int64_t *counts, const int64_t *offsets,
+                      int32_t *cand) {
+  __shared__ float sb[6][MBB_T];
+  int64_t i = blockIdx.x * (int64_t)MBB_T + threadIdx.x;
+  float a[6];
+  bool live = i < MA;
+  for (int d = 0; d < 6; ++d) a[d] = live ? aabbA[6 * i + d] : 0.f;
+  int64_t cnt = 0, pos = (EMIT && live) ? offsets[i] : 0;
+  int64_t j0 = self_join ? blockIdx.x * (int64_t)MBB_T : 0;  // tiles below are all j < i
+  for (int64_t t0 = j0; t0 < MB; t0 += MBB_T) {
+    __syncthreads();
+    int64_t j = t0 + threadIdx.x;
+    for (int d = 0; d < 6; ++d) sb[d][threadIdx.x] = j < MB ? aabbB[6 * j + d] : 0.f;
+    __syncthreads();
+    if (!live) continue;
+    int lim = (int)std::min<int64_t>(MBB_T, MB - t0);
+    for (int k = 0; k < lim; ++k) {
+      int64_t jj = t0 + k;
+      if (self_join && jj <= i) continue;
+      bool ov = a[0] <= sb[3][k] && sb[0][k] <= a[3] && a[1] <= sb[4][k] &&
+                sb[1][k] <= a[4] && a[2] <= sb[5][k] && sb[2][k] <= a[5];
+      if (ov) {
+        if (EMIT) {
+          cand[2 * pos] = (int32_t)i;
+          cand[2 * pos + 1] = (int32_t)jj;
+          ++pos;
+        } else {
+          ++cnt;
+        }
+      }
+    }
+  }
+  if (!EMIT && live) counts[i] = cnt;
+}
+
+// ---------------------------------------------------------------------------
+// Candidate validation (explicit candidates): ids in range, translated
+// meshes on the grid.
+// ---------------------------------------------------------------------------
+__global__ void k_check_cand(const int32_t *cand, const int32_t *off, int64_t n,
+                             int64_t MA, int64_t MB, const float *aabbB, int *err) {
+  for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < n;
+       c += (int64_t)gridDim.x * blockDim.x) {
+    int a = cand[2 * c], b = cand[2 * c + 1];
+    if (a < 0 || a >= MA || b < 0 || b >= MB) {
+      atomicCAS(err + 1, 0, 1);
+      continue;
+    }
+    if (off) {
+      for (int d = 0; d < 3; ++d) {
+        float lo = aabbB[6 * (int64_t)b + d] + (float)off[3 * c + d];
+        float hi = aabbB[6 * (int64_t)b + 3 + d] + (float)off[3 * c + d];
+        if (lo < 0.f || hi > 262143.f) atomicCAS(err + 2, 0, 1);
+      }
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Refinement kernel
+// ---------------------------------------------------------------------------
+struct Side {
+  const float *nodes;
+  const int32_t *roots;
+  const float4 *trirec;
+  const int64_t *toff;
+  const int64_t *voff;
+  const float *aabb;
+  const float *xyz;
+  const int32_t *lexorder;
+};
+
+struct RefineArgs {
+  Side A, B;
+  const int32_t *cand;
+  const int32_t *cand_off;
+  const int64_t *n_cand;     // device count
+  uint8_t *flags;
+  unsigned long long *work;  // work counter
+  unsigned long long *counters;
+  int *err;
+  int stack_cap;             // task entries per warp
+  int warps_per_pair;        // 1, 2 or 4
+  int64_t MA, MB;            // mesh counts (candidate ids are checked)
+  long long single;          // >= 0: process only this candidate
+};
+
+struct Cnt {
+  unsigned long long v[C_NUM];
+};
+
+template <int W>
+struct Cfg {
+  static constexpr int SW = ((7 * W + 7) / 8) * 8;  // node stride in words
+  static constexpr int LQ = W * W + 32;            // leaf-pair queue entries
+  // per-warp shared memory besides the task stack
+  static constexpr int extra_bytes = LQ * 8 /*queue*/ + LQ * 8 /*descriptors*/ +
+                                     (LQ + 1) * 4 /*prefix*/ + 2 * SW * 4 /*staged nodes*/;
+};
+
+template <int W>
+__host__ __device__ constexpr int warp_smem_bytes(int stack_cap) {
+  return ((stack_cap * 8 + Cfg<W>::extra_bytes) + 15) / 16 * 16;
+}
+
+struct WarpMem {
+  uint2 *stk;
+  uint2 *lq;
+  uint2 *ldesc;
+  int *lpre;
+  float *stage;
+};
+
+template <int W>
+__device__ __forceinline__ WarpMem carve(unsigned char *base, int stack_cap) {
+  WarpMem m;
+  m.stk = reinterpret_cast<uint2 *>(base);
+  m.lq = m.stk + stack_cap;
+  m.ldesc = m.lq + Cfg<W>::LQ;
+  m.stage = reinterpret_cast<float *>(m.ldesc + Cfg<W>::LQ);
+  m.lpre = reinterpret_cast<int *>(m.stage + 2 * Cfg<W>::SW);
+  return m;
+}
+
+__device__ __forceinline__ F3 ld3(const float *p) { return mkf3(p[0], p[1], p[2]); }
+
+__device__ __forceinline__ void load_tri(const float4 *rec, int64_t s, F3 off, F3 &a,
+                                         F3 &b, F3 &c, int &own) {
+  float4 r0 = __ldg(rec + 3 * s), r1 = __ldg(rec + 3 * s + 1), r2 = __ldg(rec + 3 * s + 2);
+  a = add(mkf3(r0.x, r0.y, r0.z), off);
+  b = add(mkf3(r0.w, r1.x, r1.y), off);
+  c = add(mkf3(r1.z, r1.w, r2.x), off);
+  own = __float_as_int(r2.y);
+}
+
+// Leaf-pair work: one unit = (leaf pair, direction, source triangle).
+template <int W, bool EXACT>
+__device__ bool leaf_units(const Side &A, const Side &B, int64_t tA, int64_t tB, F3 off,
+                           WarpMem &sm, int nlq, int lane, Cnt &cnt) {
+  constexpr int SW = Cfg<W>::SW;
+  // descriptors and unit counts
+  for (int e = lane; e < nlq; e += 32) {
+    uint2 q = sm.lq[e];
+    uint32_t sa = q.x & ~kLeafBit, sb = q.y & ~kLeafBit;
+    uint32_t da = __float_as_uint(__ldg(A.nodes + (int64_t)(sa / W) * SW + 6 * W + sa % W));
+    uint32_t db = __float_as_uint(__ldg(B.nodes + (int64_t)(sb / W) * SW + 6 * W + sb % W));
+    sm.ldesc[e] = make_uint2(da, db);
+  }
+  __syncwarp();
+  // prefix over entries (sequential chunks of 32)
+  int run = 0;
+  if (lane == 0) sm.lpre[0] = 0;
+  for (int e0 = 0; e0 < nlq; e0 += 32) {
+    int e = e0 + lane;
+    int u = 0;
+    if (e < nlq) {
+      uint2 d = sm.ldesc[e];
+      u = (int)(d.x & 7u) + 1 + (int)(d.y & 7u) + 1;
+    }
+    int inc = u;
+    for (int o = 1; o < 32; o <<= 1) {
+      int t = __shfl_up_sync(FULL, inc, o);
+      if (lane >= o) inc += t;
+    }
+    if (e < nlq) sm.lpre[e + 1] = run + inc;
+    run += __shfl_sync(FULL, inc, 31);
+  }
+  __syncwarp();
+  const int U = run;
+  cnt.v[C_LEAF_PAIRS] += (lane == 0) ? nlq : 0;
+  cnt.v[C_BYTES] += (lane == 0) ? 8ull * nlq : 0;
+  bool hit = false;
+  for (int base = 0; base < U; base += 32) {
+    int u = base + lane;
+    if (u < U && !hit) {
+      // entry: largest e with lpre[e] <= u
+      int lo = 0, hi = nlq - 1;
+      while (lo < hi) {
+        int mid = (lo + hi + 1) >> 1;
+        if (sm.lpre[mid] <= u) lo = mid; else hi = mid - 1;
+      }
+      int e = lo;
+      int k = u - sm.lpre[e];
+      uint2 q = sm.lq[e];
+      uint2 d = sm.ldesc[e];
+      int nA = (int)(d.x & 7u) + 1;
+      bool dirA = k < nA;  // source triangle from A, target leaf in B
+      const Side &S = dirA ? A : B;
+      const Side &T = dirA ? B : A;
+      uint32_t sdesc = dirA ? d.x : d.y, tdesc = dirA ? d.y : d.x;
+      uint32_t tslot = (dirA ? q.y : q.x) & ~kLeafBit;
+      int64_t sbase = dirA ? tA : tB, tbase = dirA ? tB : tA;
+      F3 soff = dirA ? mkf3(0.f, 0.f, 0.f) : off;
+      F3 toff = dirA ? off : mkf3(0.f, 0.f, 0.f);
+      int si = dirA ? k : k - nA;
+      int64_t s_rec = sbase + ((sdesc >> 3) & 0x0FFFFFFFu) + si;
+      int64_t t_first = tbase + ((tdesc >> 3) & 0x0FFFFFFFu);
+      int t_n = (int)(tdesc & 7u) + 1;
+      // target leaf box from its parent node
+      const float *tn = T.nodes + (int64_t)(tslot / W) * SW;
+      int ts = tslot % W;
+      F3 tlo = add(mkf3(__ldg(tn + ts), __ldg(tn + W + ts), __ldg(tn + 2 * W + ts)), toff);
+      F3 thi = add(mkf3(__ldg(tn + 3 * W + ts), __ldg(tn + 4 * W + ts), __ldg(tn + 5 * W + ts)), toff);
+      F3 v[3];
+      int own;
+      load_tri(S.trirec, s_rec, soff, v[0], v[1], v[2], own);
+      cnt.v[C_BYTES] += 48 + 28;
+      for (int ek = 0; ek < 3 && !hit; ++ek) {
+        if (!((own >> ek) & 1)) continue;
+        F3 p = v[ek], qv = v[ek == 2 ? 0 : ek + 1];
+        Seg sg = make_seg(p, qv);
+        cnt.v[C_SLAB_TESTS] += 1;
+        if (!slab_hit(sg, tlo, thi)) continue;
+        F3 elo = mkf3(fminf(p.x, qv.x), fminf(p.y, qv.y), fminf(p.z, qv.z));
+        F3 ehi = mkf3(fmaxf(p.x, qv.x), fmaxf(p.y, qv.y), fmaxf(p.z, qv.z));
+        for (int t = 0; t < t_n; ++t) {
+          F3 a, b, c;
+          int town;
+          load_tri(T.trirec, t_first + t, toff, a, b, c, town);
+          cnt.v[C_BYTES] += 48;
+          float lx = fminf(a.x, fminf(b.x, c.x)), hx = fmaxf(a.x, fmaxf(b.x, c.x));
+          float ly = fminf(a.y, fminf(b.y, c.y)), hy = fmaxf(a.y, fmaxf(b.y, c.y));
+          float lz = fminf(a.z, fminf(b.z, c.z)), hz = fmaxf(a.z, fmaxf(b.z, c.z));
+          if (lx > ehi.x || elo.x > hx || ly > ehi.y || elo.y > hy || lz > ehi.z || elo.z > hz)
+            continue;
+          cnt.v[C_SEGTRI] += 1;
+          bool r;
+          if (EXACT) {
+            r = segtri_exact(p, qv, a, b, c);
+          } else {
+            int f = segtri_filter(p, qv, a, b, c);
+            if (f < 0) {
+              cnt.v[C_FALLBACK] += 1;
+              r = segtri_exact(p, qv, a, b, c);
+            } else {
+              r = f == 1;
+            }
+          }
+          if (r) {
+            hit = true;
+            break;
+          }
+        }
+      }
+    }
+    if (__any_sync(FULL, hit)) return true;
+  }
+  return false;
+}
+
+// Crossing test of one pair by simultaneous descent of both BVHs.
+// Returns 1 on a crossing, 0 if none, -1 on a capacity error.
+template <int W, bool EXACT>
+__device__ int pair_cross(const Side &A, const Side &B, int ia, int ib, F3 off,
+                          WarpMem &sm, int lane, int stack_cap, Cnt &cnt,
+                          volatile int *group_hit, int rank, int nrank) {
+  constexpr int SW = Cfg<W>::SW, LQ = Cfg<W>::LQ;
+  const int64_t tA = A.toff[ia], tB = B.toff[ib];
+  int sp = 1, nlq = 0;
+  if (lane == 0) sm.stk[0] = make_uint2((uint32_t)A.roots[ia], (uint32_t)B.roots[ib]);
+  __syncwarp();
+  float *sA = sm.stage, *sB = sm.stage + SW;
+  const unsigned lt = (1u << lane) - 1u;
+  bool split_done = nrank <= 1;
+  unsigned iters = 0;
+  while (sp > 0 || nlq > 0) {
+    if (++iters > (1u << 26)) return -1;  // defensive bound: a tree walk is finite
+    if (group_hit) {
+      int gh = __shfl_sync(FULL, *group_hit, 0);
+      if (gh) return 1;
+    }
+    if (sp > 0 && nlq + W * W <= LQ) {
+      if (sp - 1 + W * W > stack_cap) return -1;
+      uint2 t = sm.stk[sp - 1];
+      --sp;
+      __syncwarp();
+      const uint32_t a = t.x, b = t.y;
+      const bool aLeaf = a & kLeafBit, bLeaf = b & kLeafBit;
+      const uint32_t an = aLeaf ? (a & ~kLeafBit) / W : a;
+      const uint32_t bn = bLeaf ? (b & ~kLeafBit) / W : b;
+      const int as = aLeaf ? (int)((a & ~kLeafBit) % W) : 0;
+      const int bs = bLeaf ? (int)((b & ~kLeafBit) % W) : 0;
+      const float *ga = A.nodes + (int64_t)an * SW, *gb = B.nodes + (int64_t)bn * SW;
+      for (int k = lane; k < SW; k += 32) {
+        sA[k] = __ldg(ga + k);
+        sB[k] = __ldg(gb + k);
+      }
+      __syncwarp();
+      const int nA = aLeaf ? 1 : W, nB = bLeaf ? 1 : W, tot = nA * nB;
+      for (int base = 0; base < tot; base += 32) {
+        int tt = base + lane;
+        bool ok = tt < tot;
+        int i = ok ? tt / nB : 0;
+        int j = ok ? tt - i * nB : 0;
+        int sa = aLeaf ? as : i, sb = bLeaf ? bs : j;
+        uint32_t ca = __float_as_uint(sA[6 * W + sa]), cb = __float_as_uint(sB[6 * W + sb]);
+        ok = ok && ca != kEmpty && cb != kEmpty;
+        if (ok) {
+          ok = sA[sa] <= sB[3 * W + sb] + off.x && sB[sb] + off.x <= sA[3 * W + sa] &&
+               sA[W + sa] <= sB[4 * W + sb] + off.y && sB[W + sb] + off.y <= sA[4 * W + sa] &&
+               sA[2 * W + sa] <= sB[5 * W + sb] + off.z && sB[2 * W + sb] + off.z <= sA[5 * W + sa];
+        }
+        uint32_t na = aLeaf ? a : ((ca & kLeafBit) ? (kLeafBit | (an * W + sa)) : ca);
+        uint32_t nb = bLeaf ? b : ((cb & kLeafBit) ? (kLeafBit | (bn * W + sb)) : cb);
+        bool both = ok && (na & kLeafBit) && (nb & kLeafBit);
+        bool push = ok && !both;
+        unsigned m1 = __ballot_sync(FULL, push), m2 = __ballot_sync(FULL, both);
+        if (push) sm.stk[sp + __popc(m1 & lt)] = make_uint2(na, nb);
+        if (both) sm.lq[nlq + __popc(m2 & lt)] = make_uint2(na, nb);
+        sp += __popc(m1);
+        nlq += __popc(m2);
+      }
+      if (lane == 0) {
+        cnt.v[C_NODE_PAIRS] += 1;
+        cnt.v[C_BOX_TESTS] += tot;
+        cnt.v[C_BYTES] += 2 * SW * 4;
+      }
+      __syncwarp();
+      if (!split_done) {
+        // several warps share this pair: after the first expansion each keeps
+        // every nrank-th task and leaf pair
+        split_done = true;
+        int nsp = 0, nl = 0;
+        for (int e0 = 0; e0 < sp; e0 += 32) {
+          int e = e0 + lane;
+          bool keep = e < sp && (e % nrank) == rank;
+          uint2 v = keep ? sm.stk[e] : make_uint2(0, 0);
+          unsigned m = __ballot_sync(FULL, keep);
+          __syncwarp();
+          if (keep) sm.stk[nsp + __popc(m & lt)] = v;
+          nsp += __popc(m);
+          __syncwarp();
+        }
+        for (int e0 = 0; e0 < nlq; e0 += 32) {
+          int e = e0 + lane;
+          bool keep = e < nlq && ((sp + e) % nrank) == rank;
+          uint2 v = keep ? sm.lq[e] : make_uint2(0, 0);
+          unsigned m = __ballot_sync(FULL, keep);
+          __syncwarp();
+          if (keep) sm.lq[nl + __popc(m & lt)] = v;
+          nl += __popc(m);
+          __syncwarp();
+        }
+        sp = nsp;
+        nlq = nl;
+      }
+    }
+    if (nlq > 0 && (sp == 0 || nlq + W * W > LQ || nlq >= 32)) {
+      bool h = leaf_units<W, EXACT>(A, B, tA, tB, off, sm, nlq, lane, cnt);
+      nlq = 0;
+      __syncwarp();
+      if (h) return 1;
+    }
+  }
+  return 0;
+}
+
+// +z parity traversal from the exact point v against mesh `it` of side T
+// (translated by toff).  Returns bit 0 = parity, bit 1 = v on the surface,
+// or -1 on a capacity error.
+template <int W>
+__device__ int parity_query(const Side &T, int it, F3 toff, F3 vf, WarpMem &sm,
+                            int lane, int stack_cap, Cnt &cnt) {
+  constexpr int SW = Cfg<W>::SW, LQ = Cfg<W>::LQ;
+  const int64_t tbase = T.toff[it];
+  const I3 v = toi(vf);
+  const unsigned lt = (1u << lane) - 1u;
+  int sp = 1, nlq = 0;
+  if (lane == 0) sm.stk[0].x = (uint32_t)T.roots[it];
+  __syncwarp();
+  bool on = false;
+  int par = 0;
+  if (lane == 0) cnt.v[C_PARITY_RAYS] += 1;
+  unsigned iters = 0;
+  while (sp > 0 || nlq > 0) {
+    if (++iters > (1u << 26)) return -1;  // defensive bound: a tree walk is finite
+    if (sp > 0 && nlq + 32 <= LQ) {
+      int P = min(sp, 32 / W);
+      while (P > 0 && sp - P + P * W > stack_cap) --P;
+      if (P == 0) return -1;
+      int ni = lane / W, c = lane % W;
+      bool ok = ni < P;
+      uint32_t node = ok ? sm.stk[sp - 1 - ni].x : 0;
+      __syncwarp();
+      sp -= P;
+      uint32_t ch = kEmpty;
+      if (ok) {
+        const float *g = T.nodes + (int64_t)node * SW;
+        ch = __float_as_uint(__ldg(g + 6 * W + c));
+        if (ch != kEmpty) {
+          float lx = __ldg(g + c) + toff.x, ly = __ldg(g + W + c) + toff.y;
+          float hx = __ldg(g + 3 * W + c) + toff.x, hy = __ldg(g + 4 * W + c) + toff.y;
+          float hz = __ldg(g + 5 * W + c) + toff.z;
+          ok = lx <= vf.x && vf.x <= hx && ly <= vf.y && vf.y <= hy && vf.z <= hz;
+        } else {
+          ok = false;
+        }
+      }
+      bool leaf = ok && (ch & kLeafBit);
+      bool inner = ok && !leaf;
+      unsigned m1 = __ballot_sync(FULL, inner), m2 = __ballot_sync(FULL, leaf);
+      if (inner) sm.stk[sp + __popc(m1 & lt)].x = ch;
+      if (leaf) sm.lq[nlq + __popc(m2 & lt)].x = kLeafBit | (node * W + c);
+      sp += __popc(m1);
+      nlq += __popc(m2);
+      if (lane == 0) {
+        cnt.v[C_PARITY_NODES] += P;
+        cnt.v[C_BYTES] += (unsigned long long)P * SW * 4;
+      }
+      __syncwarp();
+    }
+    if (nlq > 0 && (sp == 0 || nlq + 32 > LQ)) {
+      // flatten leaf triangles
+      int run = 0;
+      if (lane == 0) sm.lpre[0] = 0;
+      for (int e0 = 0; e0 < nlq; e0 += 32) {
+        int e = e0 + lane;
+        int u = 0;
+        if (e < nlq) {
+          uint32_t sl = sm.lq[e].x & ~kLeafBit;
+          uint32_t d = __float_as_uint(__ldg(T.nodes + (int64_t)(sl / W) * SW + 6 * W + sl % W));
+          sm.ldesc[e].x = d;
+          u = (int)(d & 7u) + 1;
+        }
+        int inc = u;
+        for (int o = 1; o < 32; o <<= 1) {
+          int t = __shfl_up_sync(FULL, inc, o);
+          if (lane >= o) inc += t;
+        }
+        if (e < nlq) sm.lpre[e + 1] = run + inc;
+        run += __shfl_sync(FULL, inc, 31);
+      }
+      __syncwarp();
+      for (int base = 0; base < run; base += 32) {
+        int u = base + lane;
+        if (u < run) {
+          int lo = 0, hi = nlq - 1;
+          while (lo < hi) {
+            int mid = (lo + hi + 1) >> 1;
+            if (sm.lpre[mid] <= u) lo = mid; else hi = mid - 1;
+          }
+          uint32_t d = sm.ldesc[lo].x;
+          int64_t s = tbase + ((d >> 3) & 0x0FFFFFFFu) + (u - sm.lpre[lo]);
+          F3 a, b, c;
+          int own;
+          load_tri(T.trirec, s, toff, a, b, c, own);
+          I3 ai = toi(a), bi = toi(b), ci = toi(c);
+          on = on || on_triangle(v, ai, bi, ci);
+          par ^= ray_up_hit(v, ai, bi, ci) ? 1 : 0;
+          cnt.v[C_PARITY_TRIS] += 1;
+          cnt.v[C_BYTES] += 48;
+        }
+      }
+      nlq = 0;
+      __syncwarp();
+    }
+  }
+  bool on_any = __any_sync(FULL, on);
+  int parity = __popc(__ballot_sync(FULL, par != 0)) & 1;
+  return parity | (on_any ? 2 : 0);
+}
+
+// inside(Q_iq, T_it): representative vertex of Q (lexicographically smallest
+// not on T's surface) has odd +z parity against T.  A vertex outside T's
+// closed box is off T's surface and has even parity (T is closed), which
+// ends the search.  Returns 1/0, or -1 on a capacity error.
+template <int W>
+__device__ int pair_inside(const Side &Q, int iq, F3 qoff, const Side &T, int it, F3 toff,
+                           WarpMem &sm, int lane, int stack_cap, Cnt &cnt) {
+  const int64_t v0 = Q.voff[iq], nv = Q.voff[iq + 1] - v0;
+  const float *tb = T.aabb + 6 * (int64_t)it;
+  F3 lo = add(ld3(tb), toff), hi = add(ld3(tb + 3), toff);
+  for (int64_t k = 0; k < nv; ++k) {
+    int64_t vid = Q.lexorder[v0 + k];
+    F3 v = add(ld3(Q.xyz + 3 * vid), qoff);
+    if (lane == 0) cnt.v[C_BYTES] += 16;
+    if (v.x < lo.x || v.x > hi.x || v.y < lo.y || v.y > hi.y || v.z < lo.z || v.z > hi.z)
+      return 0;
+    int r = parity_query<W>(T, it, toff, v, sm, lane, stack_cap, cnt);
+    if (r < 0) return -1;
+    if (!(r & 2)) return r & 1;
+  }
+  return 0;
+}
+
+__device__ __forceinline__ void bar_group(int id, int nthreads) {
+  asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(nthreads) : "memory");
+}
+
+template <int W, bool EXACT>
+__global__ void __launch_bounds__(128) k_refine(RefineArgs P) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  __shared__ int group_flag[4];
+  __shared__ long long group_cand[4];
+  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+  const int k = P.warps_per_pair;
+  const int grp = wib / k, rank = wib % k;
+  WarpMem sm = carve<W>(smem + (size_t)wib * warp_smem_bytes<W>(P.stack_cap), P.stack_cap);
+  Cnt cnt;
+  for (int i = 0; i < C_NUM; ++i) cnt.v[i] = 0;
+  const int64_t n = *P.n_cand;
+  bool first = true;
+  for (;;) {
+    long long c;
+    if (P.single >= 0) {
+      c = first ? P.single : n;
+      first = false;
+    } else {
+      if (k > 1) {
+        if (rank == 0 && lane == 0) {
+          group_cand[grp] = (long long)atomicAdd(P.work, 1ull);
+          group_flag[grp] = 0;
+        }
+        bar_group(1 + grp, 32 * k);
+        c = group_cand[grp];
+      } else {
+        unsigned long long w = 0;
+        if (lane == 0) w = atomicAdd(P.work, 1ull);
+        c = (long long)__shfl_sync(FULL, w, 0);
+      }
+    }
+    if (c >= n) break;
+    const int ia = P.cand[2 * c], ib = P.cand[2 * c + 1];
+    if (ia < 0 || ia >= P.MA || ib < 0 || ib >= P.MB) {
+      // reported by the candidate check; never dereference a bad id
+      if (rank == 0 && lane == 0) P.flags[c] = 0;
+      continue;
+    }
+    F3 off = mkf3(0.f, 0.f, 0.f);
+    if (P.cand_off)
+      off = mkf3((float)P.cand_off[3 * c], (float)P.cand_off[3 * c + 1], (float)P.cand_off[3 * c + 2]);
+    const float *ba = P.A.aabb + 6 * (int64_t)ia, *bb = P.B.aabb + 6 * (int64_t)ib;
+    bool overlap = ba[0] <= bb[3] + off.x && bb[0] + off.x <= ba[3] && ba[1] <= bb[4] + off.y &&
+                   bb[1] + off.y <= ba[4] && ba[2] <= bb[5] + off.z && bb[2] + off.z <= ba[5];
+    volatile int *gflag = k > 1 ? &group_flag[grp] : nullptr;
+    int res = 0;
+    if (overlap)
+      res = pair_cross<W, EXACT>(P.A, P.B, ia, ib, off, sm, lane, P.stack_cap, cnt, gflag, rank, k);
+    if (res < 0) {
+      if (lane == 0) atomicCAS(P.err, 0, DERR_STACK);
+      res = 0;
+    }
+    if (k > 1) {
+      if (res == 1 && lane == 0) group_flag[grp] = 1;
+      bar_group(1 + grp, 32 * k);
+      res = group_flag[grp];
+      bar_group(1 + grp, 32 * k);
+    }
+    if (!res) {
+      // containment both ways; with several warps per pair, ranks 0 and 1
+      // take one direction each
+      int r1 = 0, r2 = 0;
+      F3 zero = mkf3(0.f, 0.f, 0.f);
+      if (rank == 0) r1 = pair_inside<W>(P.B, ib, off, P.A, ia, zero, sm, lane, P.stack_cap, cnt);
+      if ((k == 1 && r1 == 0) || (k > 1 && rank == 1))
+        r2 = pair_inside<W>(P.A, ia, zero, P.B, ib, off, sm, lane, P.stack_cap, cnt);
+      if (r1 < 0 || r2 < 0) {
+        if (lane == 0) atomicCAS(P.err, 0, DERR_STACK);
+        r1 = r2 = 0;
+      }
+      res = (r1 > 0 || r2 > 0) ? 1 : 0;
+      if (k > 1) {
+        if (res && lane == 0) group_flag[grp] = 1;
+        bar_group(1 + grp, 32 * k);
+        res = group_flag[grp];
+        bar_group(1 + grp, 32 * k);
+      }
+    }
+    if (rank == 0 && lane == 0) {
+      P.flags[c] = (uint8_t)res;
+      cnt.v[C_PAIRS] += 1;
+      cnt.v[C_HITS] += res;
+      cnt.v[C_BYTES] += 8 + 1 + 48;
+    }
+  }
+  // flush counters (warp-aggregated)
+  for (int i = 0; i < C_NUM; ++i) {
+    unsigned long long v = cnt.v[i];
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(FULL, v, o);
+    if (lane == 0 && v) atomicAdd(P.counters + i, v);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Compaction: flags -> (idA, idB) in candidate order
+// ---------------------------------------------------------------------------
+constexpr int CMP_T = 256, CMP_PER = 16, CMP_CHUNK = CMP_T * CMP_PER;
+
+__global__ void k_flag_count(const uint8_t *flags, const int64_t *n_dev, int64_t *bcount) {
+  const int64_t n = *n_dev;
+  int64_t base = blockIdx.x * (int64_t)CMP_CHUNK;
+  int c = 0;
+  for (int k = threadIdx.x; k < CMP_CHUNK; k += CMP_T) {
+    int64_t i = base + k;
+    if (i < n) c += flags[i] != 0;
+  }
+  for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(FULL, c, o);
+  __shared__ int ws[CMP_T / 32];
+  if ((threadIdx.x & 31) == 0) ws[threadIdx.x >> 5] = c;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int s = 0;
+    for (int w = 0; w < CMP_T / 32; ++w) s += ws[w];
+    bcount[blockIdx.x] = s;
+  }
+}
+
+__global__ void k_flag_emit(const uint8_t *flags, const int64_t *n_dev, const int32_t *cand,
+                            const int64_t *boff, int32_t *out) {
+  const int64_t n = *n_dev;
+  int64_t base = blockIdx.x * (int64_t)CMP_CHUNK + (int64_t)threadIdx.x * CMP_PER;
+  int c = 0;
+  uint8_t f[CMP_PER];
+  for (int k = 0; k < CMP_PER; ++k) {
+    int64_t i = base + k;
+    f[k] = (i < n) ? flags[i] : 0;
+    c += f[k] != 0;
+  }
+  // block exclusive scan of c
+  __shared__ int ws[CMP_T / 32];
+  int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  int inc = c;
+  for (int o = 1; o < 32; o <<= 1) {
+    int t = __shfl_up_sync(FULL, inc, o);
+    if (lane >= o) inc += t;
+  }
+  if (lane == 31) ws[w] = inc;
+  __syncthreads();
+  int wbase = 0;
+  for (int k = 0; k < w; ++k) wbase += ws[k];
+  int64_t pos = boff[blockIdx.x] + wbase + inc - c;
+  for (int k = 0; k < CMP_PER; ++k) {
+    if (f[k]) {
+      int64_t i = base + k;
+      out[2 * pos] = cand[2 * i];
+      out[2 * pos + 1] = cand[2 * i + 1];
+      ++pos;
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Leaf predicate on explicit inputs (tests of the filter and exact path)
+// ---------------------------------------------------------------------------
+__global__ void k_segtri_batch(const float *pq, const float *abc, int64_t n, int mode,
+                               uint8_t *res, unsigned long long *nfb) {
+  unsigned long long fb = 0;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    F3 p = ld3(pq + 6 * i), q = ld3(pq + 6 * i + 3);
+    F3 a = ld3(abc + 9 * i), b = ld3(abc + 9 * i + 3), c = ld3(abc + 9 * i + 6);
+    bool r;
+    if (mode == PJ_LEAF_EXACT) {
+      r = segtri_exact(p, q, a, b, c);
+    } else {
+      int f = segtri_filter(p, q, a, b, c);
+      if (f < 0) {
+        ++fb;
+        r = segtri_exact(p, q, a, b, c);
+      } else {
+        r = f == 1;
+      }
+    }
+    res[i] = r ? 1 : 0;
+  }
+  for (int o = 16; o > 0; o >>= 1) fb += __shfl_xor_sync(FULL, fb, o);
+  if ((threadIdx.x & 31) == 0 && fb) atomicAdd(nfb, fb);
+}
+
+pj_status run_segtri_batch(Ctx *ctx, const float *pq, const float *abc, int64_t n, int mode,
+                           uint8_t *res, int64_t *n_fallback, cudaStream_t s) {
+  pj_status st;
+  unsigned long long *d = (unsigned long long *)ws_get(ctx, "segtri", 8, &st);
+  if (!d) return st;
+  PJ_CK(cudaMemsetAsync(d, 0, 8, s));
+  if (n > 0) {
+    int nb = (int)std::min<int64_t>((n + 255) / 256, (int64_t)ctx->num_sms * 16);
+    k_segtri_batch<<<nb, 256, 0, s>>>(pq, abc, n, mode, res, d);
+    PJ_CK(cudaGetLastError());
+  }
+  unsigned long long h = 0;
+  PJ_CK(cudaMemcpyAsync(&h, d, 8, cudaMemcpyDeviceToHost, s));
+  PJ_CK(cudaStreamSynchronize(s));
+  if (n_fallback) *n_fallback = (int64_t)h;
+  return PJ_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Orchestration
+// ---------------------------------------------------------------------------
+typedef void (*RefineKernel)(RefineArgs);
+
+static RefineKernel pick_kernel(int W, bool exact) {
+  if (W == 2) return exact ? k_refine<2, true> : k_refine<2, false>;
+  if (W == 4) return exact ? k_refine<4, true> : k_refine<4, false>;
+  return exact ? k_refine<8, true> : k_refine<8, false>;
+}
+
+static int smem_per_warp(int W, int cap) {
+  if (W == 2) return warp_smem_bytes<2>(cap);
+  if (W == 4) return warp_smem_bytes<4>(cap);
+  return warp_smem_bytes<8>(cap);
+}
+
+static Side make_side(Dataset *d, Bvh &b) {
+  Side s;
+  s.nodes = b.d_nodes;
+  s.roots = b.d_roots;
+  s.trirec = b.d_trirec;
+  s.toff = d->d_toff;
+  s.voff = d->d_voff;
+  s.aabb = d->d_aabb;
+  s.xyz = d->d_xyz;
+  s.lexorder = d->d_lexorder;
+  return s;
+}
+
+pj_status run_join(Ctx *ctx, Dataset *A, Dataset *B, const int32_t *cand,
+                   const int32_t *cand_off, int64_t n_cand, int cand_on_device,
+                   int self_join, const pj_join_opts *o, cudaStream_t s, pj_pairs *out) {
+  // pick the BVH
+  std::pair<int, int> key = o->width ? std::make_pair((int)o->width, (int)o->leaf_size)
+                                     : A->last_bvh;
+  auto ia = A->bvhs.find(key), ib = B->bvhs.find(key);
+  if (ia == A->bvhs.end() || ib == B->bvhs.end())
+    return fail(ctx, PJ_ERR_INVALID_ARG, "both datasets need a BVH of the requested width / "
+                                         "leaf size (pj_build_bvh)");
+  Bvh &bA = ia->second, &bB = ib->second;
+  const int W = key.first;
+  const int k = o->warps_per_pair ? o->warps_per_pair : 1;
+  if (!(k == 1 || k == 2 || k == 4)) return fail(ctx, PJ_ERR_INVALID_ARG, "warps_per_pair must be 1, 2 or 4");
+  const bool exact = o->leaf_mode == PJ_LEAF_EXACT;
+
+  pj_status st;
+  int64_t *d_misc = (int64_t *)ws_get(ctx, "misc", 64, &st);  // [0] n_cand, [1] K, [2] work
+  if (!d_misc) return st;
+  int64_t *h_misc = (int64_t *)ctx->h_pinned;
+
+  cudaEvent_t ev[4];
+  for (auto &e : ev) cudaEventCreate(&e);
+  struct EvGuard {
+    cudaEvent_t *e;
+    ~EvGuard() {
+      for (int i = 0; i < 4; ++i) cudaEventDestroy(e[i]);
+    }
+  } eg{ev};
+  cudaEvent_t e0 = ev[0], e1 = ev[3];
+  PJ_CK(cudaMemsetAsync(ctx->d_err, 0, sizeof(int) * 4, s));
+  PJ_CK(cudaEventRecord(e0, s));
+
+  // 1. candidates
+  int32_t *d_cand = nullptr;
+  int32_t *d_off = nullptr;
+  int64_t C = 0;
+  if (n_cand < 0) {
+    // bounding-box filter join on the device
+    const int64_t MA = A->M, MB = B->M;
+    int64_t *counts = (int64_t *)ws_get(ctx, "mbb_counts", sizeof(int64_t) * (MA + 1), &st);
+    if (!counts) return st;
+    int64_t *offs = (int64_t *)ws_get(ctx, "mbb_offs", sizeof(int64_t) * (MA + 1), &st);
+    if (!offs) return st;
+    int nb = (int)((MA + MBB_T - 1) / MBB_T);
+    k_mbb<false><<<nb, MBB_T, 0, s>>>(A->d_aabb, MA, B->d_aabb, MB, self_join, counts, nullptr, nullptr);
+    ++ctx->launches;
+    PJ_CK(cudaGetLastError());
+    if ((st = scan_i64(ctx, counts, offs, MA, d_misc, s)) != PJ_OK) return st;
+    PJ_CK(cudaMemcpyAsync(h_misc, d_misc, 8, cudaMemcpyDeviceToHost, s));
+    PJ_CK(cudaStreamSynchronize(s));
+    C = h_misc[0];
+    d_cand = (int32_t *)ws_get(ctx, "cand", sizeof(int32_t) * 2 * (size_t)std::max<int64_t>(C, 1), &st);
+    if (!d_cand) return st;
+    k_mbb<true><<<nb, MBB_T, 0, s>>>(A->d_aabb, MA, B->d_aabb, MB, self_join, nullptr, offs, d_cand);
+    ++ctx->launches;
+    PJ_CK(cudaGetLastError());
+  } else {
+    C = n_cand;
+    if (cand_on_device) {
+      d_cand = const_cast<int32_t *>(cand);
+      d_off = const_cast<int32_t *>(cand_off);
+    } else {
+      d_cand = (int32_t *)ws_get(ctx, "cand", sizeof(int32_t) * 2 * (size_t)std::max<int64_t>(C, 1), &st);
+      if (!d_cand) return st;
+      if (C > 0)
+        PJ_CK(cudaMemcpyAsync(d_cand, cand, sizeof(int32_t) * 2 * C, cudaMemcpyHostToDevice, s));
+      if (cand_off) {
+        d_off = (int32_t *)ws_get(ctx, "cand_off", sizeof(int32_t) * 3 * (size_t)std::max<int64_t>(C, 1), &st);
+        if (!d_off) return st;
+        if (C > 0)
+          PJ_CK(cudaMemcpyAsync(d_off, cand_off, sizeof(int32_t) * 3 * C, cudaMemcpyHostToDevice, s));
+      }
+    }
+    h_misc[0] = C;
+    PJ_CK(cudaMemcpyAsync(d_misc, h_misc, 8, cudaMemcpyHostToDevice, s));
+    if (C > 0)
+      k_check_cand<<<std::min(blocks_for(C, 256), ctx->num_sms * 8), 256, 0, s>>>(
+          d_cand, d_off, C, A->M, B->M, B->d_aabb, ctx->d_err);
+    if (C > 0) ++ctx->launches;
+  }
+  uint8_t *d_flags = (uint8_t *)ws_get(ctx, "flags", (size_t)std::max<int64_t>(C, 1), &st);
+  if (!d_flags) return st;
+  int32_t *d_pairs = (int32_t *)ws_get(ctx, "pairs", sizeof(int32_t) * 2 * (size_t)std::max<int64_t>(C, 1), &st);
+  if (!d_pairs) return st;
+  int nchunks = (int)std::max<int64_t>(1, (C + CMP_CHUNK - 1) / CMP_CHUNK);
+  int64_t *bcount = (int64_t *)ws_get(ctx, "cmp_counts", sizeof(int64_t) * nchunks, &st);
+  if (!bcount) return st;
+  int64_t *boff = (int64_t *)ws_get(ctx, "cmp_offs", sizeof(int64_t) * nchunks, &st);
+  if (!boff) return st;
+
+  PJ_CK(cudaEventRecord(ev[1], s));
+  // 2. refinement
+  const int depth = std::max(bA.max_depth, 1) + std::max(bB.max_depth, 1);
+  int stack_cap = 1 + (W * W - 1) * depth + 32;
+  stack_cap = std::max(stack_cap, 64);
+  const int per_warp = smem_per_warp(W, stack_cap);
+  int threads = 128;
+  if (per_warp * 4 > 200 * 1024) return fail(ctx, PJ_ERR_INTERNAL, "BVH too deep for the traversal stack");
+  const int smem = per_warp * (threads / 32);
+  RefineKernel kern = pick_kernel(W, exact);
+  PJ_CK(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+  RefineArgs args;
+  args.A = make_side(A, bA);
+  args.B = make_side(B, bB);
+  args.cand = d_cand;
+  args.cand_off = d_off;
+  args.n_cand = d_misc;
+  args.flags = d_flags;
+  args.work = (unsigned long long *)(d_misc + 2);
+  args.counters = ctx->d_counters;
+  args.err = ctx->d_err;
+  args.stack_cap = stack_cap;
+  args.warps_per_pair = k;
+  args.MA = A->M;
+  args.MB = B->M;
+  args.single = -1;
+  int64_t blocks = 1;
+  if (C > 0 && o->launch_mode != PJ_LAUNCH_PER_PAIR) {
+    int occ = 0;
+    PJ_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, threads, smem));
+    if (occ < 1) return fail(ctx, PJ_ERR_INTERNAL, "refinement kernel does not fit on an SM");
+    blocks = std::min<int64_t>((int64_t)occ * ctx->num_sms, (C * k * 32 + threads - 1) / threads);
+    blocks = std::max<int64_t>(blocks, 1);
+  }
+  if (o->launch_mode == PJ_LAUNCH_PER_PAIR && k != 1)
+    return fail(ctx, PJ_ERR_INVALID_ARG, "per-pair launches use one warp per pair");
+  const bool graph = o->use_graph != 0;
+  // everything from here to the compacted pairs is a fixed sequence of
+  // stream operations (no host synchronisation), so it can be captured
+  auto device_part = [&](bool timed) -> pj_status {
+    if (C > 0) {
+      if (o->launch_mode == PJ_LAUNCH_PER_PAIR) {
+        for (int64_t c = 0; c < C; ++c) {
+          args.single = c;
+          kern<<<1, 32, per_warp, s>>>(args);
+        }
+        args.single = -1;
+        ctx->launches += C;
+      } else {
+        PJ_CK(cudaMemsetAsync(d_misc + 2, 0, 8, s));
+        kern<<<(int)blocks, threads, smem, s>>>(args);
+        ++ctx->launches;
+      }
+      PJ_CK(cudaGetLastError());
+    }
+    if (timed) PJ_CK(cudaEventRecord(ev[2], s));
+    // 3. compaction
+    k_flag_count<<<nchunks, CMP_T, 0, s>>>(d_flags, d_misc, bcount);
+    ++ctx->launches;
+    pj_status st2 = scan_i64(ctx, bcount, boff, nchunks, d_misc + 1, s);
+    if (st2 != PJ_OK) return st2;
+    k_flag_emit<<<nchunks, CMP_T, 0, s>>>(d_flags, d_misc, d_cand, boff, d_pairs);
+    ++ctx->launches;
+    PJ_CK(cudaGetLastError());
+    return PJ_OK;
+  };
+  char gk[256];
+  snprintf(gk, sizeof(gk), "%p|%p|%p|%p|%d|%d|%d|%d|%d|%lld", (void *)A, (void *)B,
+           (void *)d_cand, (void *)d_off, W, key.second, (int)exact, k, (int)o->launch_mode,
+           (long long)C);
+  bool replayed = false;
+  if (graph) {
+    auto it = ctx->graphs.find(gk);
+    if (it != ctx->graphs.end()) {
+      PJ_CK(cudaGraphLaunch(it->second, s));
+      ctx->launches += ctx->graph_kernels[gk];
+      replayed = true;
+    }
+  }
+  if (!replayed) {
+    if ((st = device_part(true)) != PJ_OK) return st;
+    if (graph) {
+      // capture the same sequence for the next call with this shape
+      cudaGraph_t g = nullptr;
+      PJ_CK(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+      const unsigned long long before = ctx->launches;
+      pj_status cst = device_part(false);
+      cudaError_t ce = cudaStreamEndCapture(s, &g);
+      ctx->graph_kernels[gk] = ctx->launches - before;
+      ctx->launches = before;  // captured, not launched
+      if (cst != PJ_OK) {
+        if (g) cudaGraphDestroy(g);
+        return cst;
+      }
+      PJ_CK(ce);
+      cudaGraphExec_t ge = nullptr;
+      cudaError_t ie = cudaGraphInstantiate(&ge, g, 0);
+      cudaGraphDestroy(g);
+      PJ_CK(ie);
+      ctx->graphs[gk] = ge;
+    }
+  }
+  PJ_CK(cudaEventRecord(e1, s));
+  PJ_CK(cudaMemcpyAsync(h_misc + 1, d_misc + 1, 8, cudaMemcpyDeviceToHost, s));
+  int herr[4];
+  PJ_CK(cudaMemcpyAsync(herr, ctx->d_err, sizeof(herr), cudaMemcpyDeviceToHost, s));
+  PJ_CK(cudaStreamSynchronize(s));
+  if (herr[1]) return fail(ctx, PJ_ERR_INVALID_ARG, "a candidate mesh id is out of range");
+  if (herr[2]) return fail(ctx, PJ_ERR_INVALID_ARG, "a translated candidate mesh leaves the 2^18 grid");
+  if (herr[0]) return fail(ctx, PJ_ERR_INTERNAL, "traversal stack capacity exceeded");
+  const int64_t K = h_misc[1];
+  float ms = 0.f;
+  cudaEventElapsedTime(&ms, e0, e1);
+  cudaEventElapsedTime(&out->mbb_ms, ev[0], ev[1]);
+  if (replayed) {
+    // one graph launch: refinement and compaction are not separated
+    cudaEventElapsedTime(&out->refine_ms, ev[1], ev[3]);
+    out->compact_ms = 0.f;
+  } else {
+    cudaEventElapsedTime(&out->refine_ms, ev[1], ev[2]);
+    cudaEventElapsedTime(&out->compact_ms, ev[2], ev[3]);
+  }
+
+  out->count = K;
+  out->n_candidates = C;
+  out->device_ms = ms;
+  size_t bytes = sizeof(int32_t) * 2 * (size_t)std::max<int64_t>(K, 1);
+  if (o->out_host) {
+    PJ_CK(cudaMallocHost((void **)&out->pairs, bytes));
+    out->on_device = 0;
+    if (K > 0) PJ_CK(cudaMemcpyAsync(out->pairs, d_pairs, sizeof(int32_t) * 2 * K, cudaMemcpyDeviceToHost, s));
+  } else {
+    PJ_CK(cudaMalloc((void **)&out->pairs, bytes));
+    out->on_device = 1;
+    if (K > 0) PJ_CK(cudaMemcpyAsync(out->pairs, d_pairs, sizeof(int32_t) * 2 * K, cudaMemcpyDeviceToDevice, s));
+  }
+  if (o->keep_flags) {
+    PJ_CK(cudaMalloc((void **)&out->flags, (size_t)std::max<int64_t>(C, 1)));
+    if (C > 0) PJ_CK(cudaMemcpyAsync(out->flags, d_flags, C, cudaMemcpyDeviceToDevice, s));
+  }
+  PJ_CK(cudaStreamSynchronize(s));
+  return PJ_OK;
+}
+
+}  // namespace pj

@@ -1,0 +1,356 @@
+"""ctypes binding of libpierce.so (include/pierce.h).
+
+Argument marshalling only: every step of the join runs in the library's CUDA
+kernels.  The functions keep the C names.  Host arrays are numpy arrays;
+device arrays may be torch CUDA tensors (their data pointers are passed).
+Loading fails loudly when the library is missing: there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+from . import _build
+
+_lib = None
+
+PJ_OK = 0
+PJ_PENDING = 9
+PJ_LEAF_FILTERED, PJ_LEAF_EXACT = 0, 1
+PJ_LAUNCH_PERSISTENT, PJ_LAUNCH_PER_PAIR = 0, 1
+
+_STATUS = {1: "PJ_ERR_INVALID_ARG", 2: "PJ_ERR_NOT_QUANTIZED", 3: "PJ_ERR_NOT_MANIFOLD",
+           4: "PJ_ERR_NO_MEMORY", 5: "PJ_ERR_BUSY", 6: "PJ_ERR_TIMEOUT", 7: "PJ_ERR_CUDA",
+           8: "PJ_ERR_INTERNAL", 9: "PJ_PENDING"}
+
+
+class PierceError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__("%s: %s" % (_STATUS.get(code, str(code)), msg))
+        self.code = code
+
+
+class pj_config(ctypes.Structure):
+    _fields_ = [("device", ctypes.c_int32), ("reserved0", ctypes.c_int32),
+                ("budget_bytes", ctypes.c_int64), ("wait_limit_us", ctypes.c_int64),
+                ("serve_streams", ctypes.c_int32), ("reserved1", ctypes.c_int32)]
+
+
+class pj_bvh_params(ctypes.Structure):
+    _fields_ = [("width", ctypes.c_int32), ("leaf_size", ctypes.c_int32)]
+
+
+class pj_join_opts(ctypes.Structure):
+    _fields_ = [("width", ctypes.c_int32), ("leaf_size", ctypes.c_int32),
+                ("warps_per_pair", ctypes.c_int32), ("leaf_mode", ctypes.c_int32),
+                ("launch_mode", ctypes.c_int32), ("use_graph", ctypes.c_int32),
+                ("out_host", ctypes.c_int32), ("keep_flags", ctypes.c_int32)]
+
+
+class pj_pairs(ctypes.Structure):
+    _fields_ = [("count", ctypes.c_int64), ("pairs", ctypes.POINTER(ctypes.c_int32)),
+                ("on_device", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("n_candidates", ctypes.c_int64), ("flags", ctypes.c_void_p),
+                ("device_ms", ctypes.c_float), ("mbb_ms", ctypes.c_float),
+                ("refine_ms", ctypes.c_float), ("compact_ms", ctypes.c_float),
+                ("impl", ctypes.c_void_p)]
+
+
+class pj_counters(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_uint64) for n in (
+        "pairs_refined", "node_pairs", "box_tests", "leaf_pairs", "edge_slab_tests",
+        "segtri_tests", "exact_fallbacks", "parity_rays", "parity_nodes",
+        "parity_tri_tests", "bytes_fetched", "pairs_hit", "kernel_launches")] + [
+        ("reserved", ctypes.c_uint64 * 3)]
+
+
+class pj_dataset_info(ctypes.Structure):
+    _fields_ = [("n_meshes", ctypes.c_int64), ("n_verts", ctypes.c_int64),
+                ("n_tris", ctypes.c_int64), ("n_edges", ctypes.c_int64),
+                ("bvh_nodes", ctypes.c_int64), ("bvh_width", ctypes.c_int32),
+                ("bvh_leaf_size", ctypes.c_int32), ("bvh_max_depth", ctypes.c_int32),
+                ("reserved", ctypes.c_int32), ("device_bytes", ctypes.c_int64)]
+
+
+_vp = ctypes.c_void_p
+_i64 = ctypes.c_int64
+_i32 = ctypes.c_int32
+
+# name -> (restype, argtypes)
+SIGNATURES = {
+    "pj_create": (_i32, [ctypes.POINTER(pj_config), ctypes.POINTER(_vp)]),
+    "pj_destroy": (_i32, [_vp]),
+    "pj_last_error": (ctypes.c_char_p, [_vp]),
+    "pj_load_meshes": (_i32, [_vp, _vp, _i64, _vp, _i64, _vp, _vp, _i64, _i32,
+                              ctypes.POINTER(_i32)]),
+    "pj_free_dataset": (_i32, [_vp, _i32]),
+    "pj_build_bvh": (_i32, [_vp, _i32, ctypes.POINTER(pj_bvh_params)]),
+    "pj_dataset_info_get": (_i32, [_vp, _i32, ctypes.POINTER(pj_dataset_info)]),
+    "pj_join_intersects": (_i32, [_vp, _i32, _i32, _vp, _i64, _i32, _vp,
+                                  ctypes.POINTER(pj_pairs)]),
+    "pj_join_intersects_ex": (_i32, [_vp, _i32, _i32, _vp, _vp, _i64, _i32, _i32,
+                                     ctypes.POINTER(pj_join_opts), _vp,
+                                     ctypes.POINTER(pj_pairs)]),
+    "pj_free_pairs": (_i32, [_vp, ctypes.POINTER(pj_pairs)]),
+    "pj_get_counters": (_i32, [_vp, ctypes.POINTER(pj_counters)]),
+    "pj_reset_counters": (_i32, [_vp]),
+    "pj_segtri_batch": (_i32, [_vp, _vp, _vp, _i64, _i32, _vp, ctypes.POINTER(_i64), _vp]),
+    "pj_export_bvh": (_i32, [_vp, _i32, _i32, _i32, _vp, _vp, _vp, ctypes.POINTER(_i64)]),
+    "pj_export_mesh_data": (_i32, [_vp, _i32, _vp, _vp, _vp]),
+}
+
+
+def lib_path() -> str:
+    return _build.LIB
+
+
+def load(build_if_missing: bool = False):
+    """Load libpierce.so (raise if it is missing; build it first on request)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = _build.LIB
+    if not os.path.exists(path):
+        if not build_if_missing:
+            raise RuntimeError("libpierce.so is not built (run __graft_entry__.build())")
+        _build.build()
+    lib = ctypes.CDLL(path)
+    for name, (res, args) in SIGNATURES.items():
+        f = getattr(lib, name)
+        f.restype = res
+        f.argtypes = args
+    _lib = lib
+    return lib
+
+
+def _ptr(x):
+    """Data pointer of a numpy array or torch tensor (None -> NULL)."""
+    if x is None:
+        return None
+    if isinstance(x, np.ndarray):
+        return x.ctypes.data
+    return int(x.data_ptr())
+
+
+def _is_device(x) -> bool:
+    return x is not None and not isinstance(x, np.ndarray) and getattr(x, "is_cuda", False)
+
+
+def _stream_ptr(stream):
+    if stream is None:
+        return None
+    if isinstance(stream, int):
+        return stream
+    return int(stream.cuda_stream)
+
+
+def _check(ctx, rc):
+    if rc != PJ_OK:
+        msg = load().pj_last_error(ctx).decode() if ctx else ""
+        raise PierceError(rc, msg)
+
+
+# ---------------------------------------------------------------------------
+# Functions with the C names
+# ---------------------------------------------------------------------------
+
+def pj_create(device: int = 0, budget_bytes: int = 0, wait_limit_us: int = 0,
+              serve_streams: int = 0):
+    cfg = pj_config(device, 0, budget_bytes, wait_limit_us, serve_streams, 0)
+    h = _vp()
+    rc = load().pj_create(ctypes.byref(cfg), ctypes.byref(h))
+    if rc != PJ_OK:
+        raise PierceError(rc, "pj_create failed")
+    return h.value
+
+
+def pj_destroy(ctx):
+    _check(None, load().pj_destroy(ctx))
+
+
+def pj_last_error(ctx) -> str:
+    return load().pj_last_error(ctx).decode()
+
+
+def pj_load_meshes(ctx, xyz, tris, mesh_vert_off, mesh_tri_off) -> int:
+    """xyz (V x 3 float32) and tris (F x 3 int32): numpy arrays (host) or torch
+    CUDA tensors (device).  Offsets: numpy int64 (host)."""
+    dev = _is_device(xyz)
+    if dev != _is_device(tris):
+        raise ValueError("xyz and tris must both be host or both be device arrays")
+    if not dev:
+        xyz = np.ascontiguousarray(xyz, dtype=np.float32)
+        tris = np.ascontiguousarray(tris, dtype=np.int32)
+    else:
+        xyz, tris = xyz.contiguous(), tris.contiguous()
+    voff = np.ascontiguousarray(mesh_vert_off, dtype=np.int64)
+    toff = np.ascontiguousarray(mesh_tri_off, dtype=np.int64)
+    nv = int(xyz.shape[0]) if xyz.ndim == 2 else int(xyz.numel() // 3 if dev else xyz.size // 3)
+    nt = int(tris.shape[0]) if tris.ndim == 2 else int(tris.numel() // 3 if dev else tris.size // 3)
+    out = _i32()
+    rc = load().pj_load_meshes(ctx, _ptr(xyz), nv, _ptr(tris), nt, _ptr(voff), _ptr(toff),
+                               len(voff) - 1, 1 if dev else 0, ctypes.byref(out))
+    _check(ctx, rc)
+    return out.value
+
+
+def pj_free_dataset(ctx, ds: int):
+    _check(ctx, load().pj_free_dataset(ctx, ds))
+
+
+def pj_build_bvh(ctx, ds: int, width: int = 4, leaf_size: int = 4):
+    p = pj_bvh_params(width, leaf_size)
+    _check(ctx, load().pj_build_bvh(ctx, ds, ctypes.byref(p)))
+
+
+def pj_dataset_info_get(ctx, ds: int) -> dict:
+    info = pj_dataset_info()
+    _check(ctx, load().pj_dataset_info_get(ctx, ds, ctypes.byref(info)))
+    return {f: getattr(info, f) for f, _ in pj_dataset_info._fields_ if f != "reserved"}
+
+
+def pj_join_intersects_ex(ctx, a: int, b: int, cand=None, cand_offsets=None, self_join=False,
+                          width=0, leaf_size=0, warps_per_pair=0, leaf_mode=PJ_LEAF_FILTERED,
+                          launch_mode=PJ_LAUNCH_PERSISTENT, use_graph=False, out_host=True,
+                          keep_flags=False, stream=None):
+    """Run the join.  Returns the filled pj_pairs (free it with pj_free_pairs).
+
+    cand / cand_offsets: None (device bounding-box filter join), numpy int32
+    arrays (host) or torch CUDA int32 tensors (device)."""
+    dev = _is_device(cand)
+    n = 0
+    if cand is not None:
+        if not dev:
+            cand = np.ascontiguousarray(cand, dtype=np.int32).reshape(-1, 2)
+            if cand_offsets is not None:
+                cand_offsets = np.ascontiguousarray(cand_offsets, dtype=np.int32).reshape(-1, 3)
+        n = int(cand.shape[0])
+    opts = pj_join_opts(width, leaf_size, warps_per_pair, leaf_mode, launch_mode,
+                        int(use_graph), int(out_host), int(keep_flags))
+    res = pj_pairs()
+    rc = load().pj_join_intersects_ex(ctx, a, b, _ptr(cand), _ptr(cand_offsets), n,
+                                      1 if dev else 0, int(self_join), ctypes.byref(opts),
+                                      _stream_ptr(stream), ctypes.byref(res))
+    _check(ctx, rc)
+    return res
+
+
+def pj_join_intersects(ctx, a: int, b: int, cand=None, self_join=False, stream=None):
+    """The plain entry point (device-resident result).  Returns pj_pairs."""
+    res = pj_pairs()
+    n = 0
+    if cand is not None:
+        cand = np.ascontiguousarray(cand, dtype=np.int32).reshape(-1, 2)
+        n = cand.shape[0]
+    rc = load().pj_join_intersects(ctx, a, b, _ptr(cand), n, int(self_join),
+                                   _stream_ptr(stream), ctypes.byref(res))
+    _check(ctx, rc)
+    return res
+
+
+def pj_free_pairs(ctx, res: pj_pairs):
+    _check(ctx, load().pj_free_pairs(ctx, ctypes.byref(res)))
+
+
+def pj_get_counters(ctx) -> dict:
+    c = pj_counters()
+    _check(ctx, load().pj_get_counters(ctx, ctypes.byref(c)))
+    return {f: int(getattr(c, f)) for f, _ in pj_counters._fields_ if f != "reserved"}
+
+
+def pj_reset_counters(ctx):
+    _check(ctx, load().pj_reset_counters(ctx))
+
+
+def pj_segtri_batch(ctx, pq, abc, res, mode=PJ_LEAF_FILTERED, stream=None) -> int:
+    """pq (n x 6), abc (n x 9) float32 and res (n uint8): torch CUDA tensors.
+    Returns the number of filter fallbacks."""
+    nfb = _i64()
+    _check(ctx, load().pj_segtri_batch(ctx, _ptr(pq), _ptr(abc), int(res.numel()), mode,
+                                       _ptr(res), ctypes.byref(nfb), _stream_ptr(stream)))
+    return nfb.value
+
+
+def pj_export_bvh(ctx, ds: int, width: int, leaf_size: int, n_tris: int, n_meshes: int):
+    """(nodes [n, 7W] int32 words, roots [M], tri_order [F]) as numpy arrays."""
+    n = _i64()
+    lib = load()
+    _check(ctx, lib.pj_export_bvh(ctx, ds, width, leaf_size, None, None, None, ctypes.byref(n)))
+    nodes = np.zeros((n.value, 7 * width), dtype=np.int32)
+    roots = np.zeros(n_meshes, dtype=np.int32)
+    order = np.zeros(n_tris, dtype=np.int32)
+    _check(ctx, lib.pj_export_bvh(ctx, ds, width, leaf_size, _ptr(nodes), _ptr(roots),
+                                  _ptr(order), ctypes.byref(n)))
+    return nodes, roots, order
+
+
+def pj_export_mesh_data(ctx, ds: int, n_meshes: int, n_tris: int):
+    aabb = np.zeros((n_meshes, 6), dtype=np.float32)
+    lex = np.zeros(n_meshes, dtype=np.int32)
+    own = np.zeros(n_tris, dtype=np.uint8)
+    _check(ctx, load().pj_export_mesh_data(ctx, ds, _ptr(aabb), _ptr(lex), _ptr(own)))
+    return aabb, lex, own
+
+
+# ---------------------------------------------------------------------------
+# Convenience wrappers
+# ---------------------------------------------------------------------------
+
+def pairs_to_numpy(res: pj_pairs) -> np.ndarray:
+    """Copy a host-resident result (out_host=True) into a numpy array."""
+    if res.on_device:
+        raise ValueError("result is on the device; join with out_host=True")
+    k = int(res.count)
+    if k == 0:
+        return np.zeros((0, 2), dtype=np.int32)
+    return np.ctypeslib.as_array(res.pairs, shape=(k, 2)).copy()
+
+
+class Context:
+    """Owns a pj_ctx; datasets are loaded from objects with xyz/tris/voff/toff."""
+
+    def __init__(self, device: int = 0, **cfg):
+        self.h = pj_create(device, **cfg)
+
+    def close(self):
+        if self.h:
+            pj_destroy(self.h)
+            self.h = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def load(self, ds, device_tensors: bool = False) -> int:
+        if device_tensors:
+            import torch
+            xyz = torch.from_numpy(np.ascontiguousarray(ds.xyz, dtype=np.float32)).cuda()
+            tris = torch.from_numpy(np.ascontiguousarray(ds.tris, dtype=np.int32)).cuda()
+            return pj_load_meshes(self.h, xyz, tris, ds.voff, ds.toff)
+        return pj_load_meshes(self.h, ds.xyz, ds.tris, ds.voff, ds.toff)
+
+    def build(self, ds: int, width: int = 4, leaf_size: int = 4):
+        pj_build_bvh(self.h, ds, width, leaf_size)
+
+    def join(self, a: int, b: int, cand=None, **kw):
+        """Sorted intersecting pairs as numpy (K x 2), plus the raw result info."""
+        kw.setdefault("out_host", True)
+        res = pj_join_intersects_ex(self.h, a, b, cand=cand, **kw)
+        try:
+            pairs = pairs_to_numpy(res)
+            info = dict(count=int(res.count), n_candidates=int(res.n_candidates),
+                        device_ms=res.device_ms, mbb_ms=res.mbb_ms, refine_ms=res.refine_ms,
+                        compact_ms=res.compact_ms)
+        finally:
+            pj_free_pairs(self.h, res)
+        return pairs, info
+
+    def counters(self) -> dict:
+        return pj_get_counters(self.h)
+
+    def reset_counters(self):
+        pj_reset_counters(self.h)

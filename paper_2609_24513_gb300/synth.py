@@ -261,12 +261,29 @@ def nuclei(seed: int, n: int = 10000, mean_r: float = 1.0 / 200, sigma: float = 
     margin = r * (1 + noise_amp) + 2.0 / QMAX
     c = lo + margin[:, None] + rng.uniform(size=(n, 3)) * (hi - lo - 2 * margin[:, None])
     R = random_rotations(rng, n)
-    meshes = []
-    for k in range(n):
-        field = _smooth_field(rng)
-        meshes.append(_placed_sphere(int(lev[k]), c[k], r[k], R[k],
-                                     noise=lambda u, f=field: noise_amp * f(u)))
-    return concat(meshes, dict(kind="nuclei", seed=seed, n=n))
+    # smooth radial field per mesh: 8 low-frequency sinusoids (see _smooth_field)
+    nt = 8
+    dirs = rng.normal(size=(n, nt, 3))
+    dirs /= np.linalg.norm(dirs, axis=2, keepdims=True)
+    w = dirs * rng.uniform(1.0, 3.0, size=(n, nt, 1))
+    phase = rng.uniform(0, 2 * np.pi, size=(n, nt))
+    amp = rng.uniform(0.5, 1.0, size=(n, nt))
+    out = [None] * n
+    w32, ph32, amp32 = w.astype(np.float32), phase.astype(np.float32), amp.astype(np.float32)
+    for L in np.unique(lev):
+        U, F = icosphere(int(L))
+        U32 = U.astype(np.float32)
+        ids = np.nonzero(lev == L)[0]
+        for k0 in range(0, len(ids), 64):
+            blk = ids[k0:k0 + 64]
+            f = np.matmul(U32[None], w32[blk].transpose(0, 2, 1)) + ph32[blk][:, None, :]
+            f = np.matmul(np.sin(f), amp32[blk][:, :, None])[..., 0] / amp32[blk].sum(axis=1)[:, None]
+            X = U[None, :, :] * (1.0 + noise_amp * f.astype(np.float64))[:, :, None]
+            X = np.matmul(X, R[blk].transpose(0, 2, 1)) * r[blk][:, None, None] + c[blk][:, None, :]
+            Q = quantize(X)
+            for j, k in enumerate(blk):
+                out[k] = (Q[j], F)
+    return concat(out, dict(kind="nuclei", seed=seed, n=n))
 
 
 def _bspline(ctrl: np.ndarray, m: int) -> np.ndarray:
@@ -340,22 +357,21 @@ def _tube(curve: np.ndarray, radius: float, rings: int, sides: int = 16):
 def _curve_ok(curve, radius):
     """Reject curves that bend tighter than 3 radii or pass within 3 radii of
     themselves away from the neighbourhood of a point."""
-    P = curve[:: max(1, len(curve) // 1500)]
-    seg = np.linalg.norm(np.diff(P, axis=0), axis=1)
+    seg = np.linalg.norm(np.diff(curve, axis=0), axis=1)
     s = np.concatenate([[0], np.cumsum(seg)])
-    d1 = np.gradient(P, s, axis=0)
+    d1 = np.gradient(curve, s, axis=0)
     d2 = np.gradient(d1, s, axis=0)
     kappa = np.linalg.norm(np.cross(d1, d2), axis=1) / np.maximum(
         np.linalg.norm(d1, axis=1) ** 3, 1e-30)
-    if np.any(kappa * 3 * radius > 1):
+    if np.any(kappa[2:-2] * 3 * radius > 1):
         return False
-    for i0 in range(0, len(P), 256):
-        blk = P[i0:i0 + 256]
-        D = np.linalg.norm(blk[:, None, :] - P[None, :, :], axis=2)
-        far = np.abs(s[i0:i0 + 256][:, None] - s[None, :]) > 8 * radius
-        if np.any(D[far] < 3 * radius):
-            return False
-    return True
+    # non-local approach: samples spaced well below the 3-radius threshold
+    step = max(1, int(len(curve) * radius / max(s[-1], 1e-12)))
+    P, sp = curve[::step], s[::step]
+    sq = (P * P).sum(axis=1)
+    D2 = sq[:, None] + sq[None, :] - 2 * P @ P.T
+    far = np.abs(sp[:, None] - sp[None, :]) > 8 * radius
+    return not np.any(D2[far] < (3 * radius) ** 2)
 
 
 def vessels(seed: int, n: int = 500, f_range=(10000, 50000), r_range=(1.0 / 300, 1.0 / 100),

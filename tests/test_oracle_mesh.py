@@ -14,6 +14,7 @@ import numpy as np
 import pytest
 
 import oracle
+from cases import HAND, lattice_case_sets
 from paper_2609_24513_gb300 import synth
 
 QMAX = synth.QMAX
@@ -213,29 +214,6 @@ def _case(ma, mb):
     return one(ma), one(mb)
 
 
-HAND = {
-    "disjoint boxes": (synth.box((100, 100, 100), (110, 110, 110)),
-                       synth.box((120, 100, 100), (130, 110, 110)), False),
-    "face to face": (synth.box((100, 100, 100), (110, 110, 110)),
-                     synth.box((110, 102, 103), (120, 108, 113)), False),
-    "shared edge": (synth.box((100, 100, 100), (110, 110, 110)),
-                    synth.box((110, 110, 100), (120, 120, 110)), False),
-    "shared vertex": (synth.box((100, 100, 100), (110, 110, 110)),
-                      synth.box((110, 110, 110), (120, 120, 120)), False),
-    "interpenetrating boxes": (synth.box((100, 100, 100), (110, 110, 110)),
-                               synth.box((105, 103, 96), (117, 108, 104)), True),
-    "nested boxes": (synth.box((100, 100, 100), (130, 130, 130)),
-                     synth.box((107, 111, 113), (117, 119, 121)), True),
-    "nested boxes sharing a face": (synth.box((100, 100, 100), (120, 120, 120)),
-                                    synth.box((100, 105, 105), (110, 115, 115)), True),
-    "vertex on a face, outside": (synth.box((100, 100, 100), (120, 120, 120)),
-                                  synth.tetra((110, 110, 120), (105, 105, 130),
-                                              (118, 106, 131), (108, 117, 129)), False),
-    "identical meshes": (synth.box((100, 100, 100), (110, 110, 110)),
-                         synth.box((100, 100, 100), (110, 110, 110)), False),
-}
-
-
 @pytest.mark.parametrize("name", list(HAND))
 def test_hand_built_cases(name):
     ma, mb, exp = HAND[name]
@@ -386,14 +364,6 @@ def test_invariants(tiny, name):
 
 # -- exhaustive lattice placements vs the convex separating-axis test (P4) -------
 
-def _shapes():
-    return {
-        "cube": synth.box((0, 0, 0), (2, 2, 2)),
-        "tetra": synth.tetra((0, 0, 0), (2, 0, 0), (0, 2, 0), (0, 0, 2)),
-        "octa": synth.octahedron((1, 1, 1), 1),
-    }
-
-
 def _sat_overlap(va, ta, vb, tb):
     """Exact: interiors of two convex polytopes intersect iff no candidate axis
     (face normals, edge x edge) weakly separates them."""
@@ -415,21 +385,7 @@ def _sat_overlap(va, ta, vb, tb):
 
 
 def test_exhaustive_lattice_vs_sat():
-    shapes = _shapes()
-    base = np.array([20, 20, 20])
-    offs = list(itertools.product(range(-3, 4), repeat=3))
-    meshes_a, meshes_b, cand, meta = [], [], [], []
-    names = list(shapes)
-    for ia, na in enumerate(names):
-        meshes_a.append(synth.translate(shapes[na], base))
-    for na in names:
-        for nb in names:
-            for o in offs:
-                meshes_b.append(synth.translate(shapes[nb], base + np.array(o)))
-                cand.append((names.index(na), len(meshes_b) - 1))
-                meta.append((na, nb, o))
-    A, B = synth.concat(meshes_a), synth.concat(meshes_b)
-    cand = np.array(cand, dtype=np.int32)
+    A, B, cand, meta = lattice_case_sets()
     f1 = oracle.join(A, B, cand, tier=1)
     f2 = oracle.join(A, B, cand, tier=2)
     assert (f1 == f2).all()
