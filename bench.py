@@ -71,7 +71,7 @@ class ClockSampler:
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", "-i", str(self.device), "--query-gpu=" + self.Q,
-                 "--format=csv,noheader,nounits", "-lms", "100"],
+                 "--format=csv,noheader,nounits", "-lms", "50"],
                 stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.t = threading.Thread(target=self._read, daemon=True)
             self.t.start()
@@ -110,9 +110,23 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def make_workload(seed: int):
+def aggregate_ranks(ms_step: float, units: int, dist, device: str):
+    """Whole-job numbers: the slowest rank's step time and the units (candidate
+    pairs) all ranks processed per step.  No collective touches the data path;
+    this is the only one, after the timed region."""
+    if dist is None:
+        return ms_step, units
+    import torch
+    t = torch.tensor([ms_step], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    u = torch.tensor([units], dtype=torch.int64, device=device)
+    dist.all_reduce(u, op=dist.ReduceOp.SUM)
+    return float(t.item()), int(u.item())
+
+
+def make_workload(seed: int, n_nuclei: int = 10000, n_vessels: int = 500):
     from paper_2609_24513_gb300 import synth
-    return synth.pathology(seed)
+    return synth.pathology(seed, n_nuclei, n_vessels)
 
 
 def profile_traffic(kernel_src: str):
@@ -156,7 +170,7 @@ def run_reference(args, rank, world):
     import oracle
     from paper_2609_24513_gb300 import synth
     oracle.build()
-    A, B = make_workload(args.seed)
+    A, B = make_workload(args.seed, args.nuclei, args.vessels)
     cand = oracle.mbb_candidates(A, B)
     rng = np.random.default_rng(args.seed)
     per_step = max(1.0, args.ref_step_s)
@@ -195,7 +209,7 @@ def run_ours(args, rank, world, local_rank):
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
     t0 = time.perf_counter()
-    A, B = make_workload(args.seed + 1000 * rank)     # weak scaling: one workload per rank
+    A, B = make_workload(args.seed + 1000 * rank, args.nuclei, args.vessels)  # one per rank
     gen_s = time.perf_counter() - t0
     ctx = pierce.Context(local_rank)
     stream = torch.cuda.current_stream()
@@ -240,12 +254,8 @@ def run_ours(args, rank, world, local_rank):
         dist.barrier()
     clk = clocks.stop()
     cnt = ctx.counters()
-    ms_step = total_ms / args.steps
-    if dist:
-        t = torch.tensor([ms_step], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms_step = float(t.item())
-    value = world * C / (ms_step / 1000.0)
+    ms_step, C_all = aggregate_ranks(total_ms / args.steps, C, dist, "cuda")
+    value = C_all / (ms_step / 1000.0)
     segtri_s = cnt["segtri_tests"] / (total_ms / 1000.0)
     launches = cnt["kernel_launches"]
     # dominant kernel: the refinement launch
@@ -255,26 +265,10 @@ def run_ours(args, rank, world, local_rank):
     achieved = bytes_launch / (refine_avg / 1000.0) / 1e9
     traffic = profile_traffic(os.path.join(ROOT, "paper_2609_24513_gb300", "csrc", "pj_join.cu"))
 
-    # end to end: candidates from pinned host memory, pairs back to the host
+    line_e2e = None
     cand_host = _candidates_host(ctx, ha, hb, C)
-    pinned = torch.from_numpy(cand_host).pin_memory()
-    cand_np = pinned.numpy()
-    e2e_t, e2e_k = 0.0, 0
-    for i in range(args.warmup + args.steps):
-        flush.zero_()
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        r = pierce.pj_join_intersects_ex(ctx.h, ha, hb, cand=cand_np, width=args.width,
-                                         leaf_size=args.leaf, warps_per_pair=args.warps,
-                                         out_host=True, stream=stream)
-        pairs = pierce.pairs_to_numpy(r)
-        pierce.pj_free_pairs(ctx.h, r)
-        el = time.perf_counter() - t0
-        if i >= args.warmup:
-            e2e_t += el
-            e2e_k = len(pairs)
-    e2e_value = world * len(cand_np) / (e2e_t / args.steps)
-
+    if not args.no_e2e:
+        line_e2e = _end_to_end(ctx, ha, hb, cand_host, args, flush, stream, dist, pierce)
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
@@ -294,9 +288,7 @@ def run_ours(args, rank, world, local_rank):
                          "kernel": "k_refine", "refine_ms": refine_avg,
                          "peak_source": peak_kind,
                          "bytes_per_launch": bytes_launch},
-            "e2e": {"value": e2e_value, "unit": UNIT,
-                    "h2d_bytes_per_step": int(cand_np.nbytes),
-                    "d2h_bytes_per_step": int(8 * e2e_k + 8)},
+            "e2e": line_e2e,
             "clocks": clk}
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(A, B, cand_host, args.cpu_seconds, args.seed)
@@ -305,6 +297,33 @@ def run_ours(args, rank, world, local_rank):
         dist.destroy_process_group()
     if rank == 0:
         print(json.dumps(line), flush=True)
+
+
+def _end_to_end(ctx, ha, hb, cand_host, args, flush, stream, dist, pierce):
+    """The same metric through the public call with host buffers: the
+    candidate list comes from pinned host memory each step and the result
+    pairs go back to host memory; wall-clock timed with a synchronize on both
+    sides of every step."""
+    import torch
+    pinned = torch.from_numpy(cand_host).pin_memory()
+    cand_np = pinned.numpy()
+    e2e_t, e2e_k = 0.0, 0
+    for i in range(args.warmup + args.steps):
+        flush.zero_()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        r = pierce.pj_join_intersects_ex(ctx.h, ha, hb, cand=cand_np, width=args.width,
+                                         leaf_size=args.leaf, warps_per_pair=args.warps,
+                                         out_host=True, stream=stream)
+        pairs = pierce.pairs_to_numpy(r)
+        pierce.pj_free_pairs(ctx.h, r)
+        el = time.perf_counter() - t0
+        if i >= args.warmup:
+            e2e_t += el
+            e2e_k = len(pairs)
+    e2e_ms, e2e_units = aggregate_ranks(1000.0 * e2e_t / args.steps, len(cand_np), dist, "cuda")
+    return {"value": e2e_units / (e2e_ms / 1000.0), "unit": UNIT,
+            "h2d_bytes_per_step": int(cand_np.nbytes), "d2h_bytes_per_step": int(8 * e2e_k + 8)}
 
 
 def _candidates_host(ctx, ha, hb, n):
@@ -341,7 +360,7 @@ def _nt(ctx, h):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--seed", type=int, default=2001)
@@ -352,6 +371,9 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--ref-step-s", type=float, default=10.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--nuclei", type=int, default=10000)
+    ap.add_argument("--vessels", type=int, default=500)
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

@@ -245,10 +245,11 @@ pj_status pj_segtri_batch(pj_ctx *ctx, const float *pq, const float *abc,
 
 /* Copy a dataset's BVH (built with width W, leaf size L) to host buffers for
  * inspection.  Pass NULL buffers to query the sizes first.
- *   nodes      n_nodes x (7 W) float/int32 words per node: lo x/y/z[W],
- *              hi x/y/z[W], child[W] (child: -1 empty; >= 0 wide node;
- *              bit 31 set: leaf with first sorted triangle (bits 3-30) and
- *              count - 1 (bits 0-2))
+ *   nodes      n_nodes x 8 (W + 1) 32-bit words: W + 1 slots of 8 words; slot
+ *              0 = the node's own box (lo x y z, hi x y z, 0, 0), slot k + 1 =
+ *              child k (lo x y z, hi x y z as float, child word, 0).  Child
+ *              word: -1 empty; < 2^30 wide node; bit 31 set: leaf with first
+ *              sorted triangle (bits 3-30) and count - 1 (bits 0-2)
  *   roots      n_meshes int32 root node per mesh
  *   tri_order  n_tris int32: mesh-local triangle id at each sorted position
  * *n_nodes receives the node count. */

@@ -278,12 +278,25 @@ static void tri_box(const int64_t *a, const int64_t *b, const int64_t *c,
 }
 
 /* Does some edge of S pierce some triangle of T?  tier 2 restricts the tests
- * to boxes meeting the clip box [clo, chi]. */
+ * to edges and triangles whose boxes meet the clip box [clo, chi] and each
+ * other (the triangles meeting the clip box are listed once per call). */
 static int pierce_one_way(const mesh_t *S, const mesh_t *T, int tier,
                           const int64_t *clo, const int64_t *chi,
                           int64_t *ntests) {
-  for (int64_t f = 0; f < S->nf; ++f) {
-    for (int k = 0; k < 3; ++k) {
+  int64_t *list = NULL, nlist = T->nf;
+  if (tier == 2) {
+    list = (int64_t *)malloc(sizeof(int64_t) * (size_t)(T->nf > 0 ? T->nf : 1));
+    if (!list) return ORC_ERR_NOMEM;
+    nlist = 0;
+    for (int64_t g = 0; g < T->nf; ++g) {
+      int64_t tlo[3], thi[3];
+      tri_box(VTX(T, T->t[3 * g]), VTX(T, T->t[3 * g + 1]), VTX(T, T->t[3 * g + 2]), tlo, thi);
+      if (boxes_meet(tlo, thi, clo, chi)) list[nlist++] = g;
+    }
+  }
+  int found = 0;
+  for (int64_t f = 0; f < S->nf && !found; ++f) {
+    for (int k = 0; k < 3 && !found; ++k) {
       const int64_t *p = VTX(S, S->t[3 * f + k]);
       const int64_t *q = VTX(S, S->t[3 * f + (k + 1) % 3]);
       int64_t slo[3], shi[3];
@@ -291,22 +304,23 @@ static int pierce_one_way(const mesh_t *S, const mesh_t *T, int tier,
         seg_box(p, q, slo, shi);
         if (!boxes_meet(slo, shi, clo, chi)) continue;
       }
-      for (int64_t g = 0; g < T->nf; ++g) {
+      for (int64_t h = 0; h < nlist; ++h) {
+        int64_t g = tier == 2 ? list[h] : h;
         const int64_t *a = VTX(T, T->t[3 * g]);
         const int64_t *b = VTX(T, T->t[3 * g + 1]);
         const int64_t *c = VTX(T, T->t[3 * g + 2]);
         if (tier == 2) {
           int64_t tlo[3], thi[3];
           tri_box(a, b, c, tlo, thi);
-          if (!boxes_meet(tlo, thi, clo, chi)) continue;
           if (!boxes_meet(tlo, thi, slo, shi)) continue;
         }
         ++*ntests;
-        if (orc_segtri_strict(p, q, a, b, c)) return 1;
+        if (orc_segtri_strict(p, q, a, b, c)) { found = 1; break; }
       }
     }
   }
-  return 0;
+  free(list);
+  return found;
 }
 
 static int cross_meshes(const mesh_t *A, const mesh_t *B, int tier,
@@ -317,7 +331,8 @@ static int cross_meshes(const mesh_t *A, const mesh_t *B, int tier,
     chi[d] = A->hi[d] < B->hi[d] ? A->hi[d] : B->hi[d];
     if (tier == 2 && clo[d] > chi[d]) return 0;
   }
-  if (pierce_one_way(A, B, tier, clo, chi, ntests)) return 1;
+  int r = pierce_one_way(A, B, tier, clo, chi, ntests);
+  if (r != 0) return r;
   return pierce_one_way(B, A, tier, clo, chi, ntests);
 }
 
@@ -396,7 +411,7 @@ static int pair_eval(const orc_dataset *DA, int64_t i, const orc_dataset *DB,
   if (!stats) stats = dummy;
   int res = 0;
   /* what: 1 = cross, 2 = inside(B,A), 4 = inside(A,B); any set bit -> OR */
-  if ((what & 1) && cross_meshes(&A, &B, tier, &stats[0])) res = 1;
+  if (what & 1) res = cross_meshes(&A, &B, tier, &stats[0]);
   if (!res && (what & 2)) {
     rc = inside_meshes(&B, &A, &stats[1]);
     if (rc < 0) res = rc; else res = rc;

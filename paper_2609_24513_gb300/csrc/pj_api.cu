@@ -615,12 +615,7 @@ pj_status pj_export_bvh(pj_ctx *h, pj_dataset id, int32_t W, int32_t L, int32_t 
   cudaSetDevice(ctx->device);
   *n_nodes = b.n_nodes;
   int sw = node_stride_words(W);
-  if (nodes) {
-    std::vector<int32_t> tmp((size_t)b.n_nodes * sw);
-    PJ_CK(cudaMemcpy(tmp.data(), b.d_nodes, 4 * tmp.size(), cudaMemcpyDeviceToHost));
-    for (int64_t k = 0; k < b.n_nodes; ++k)
-      memcpy(nodes + k * 7 * W, tmp.data() + k * sw, 4 * 7 * W);
-  }
+  if (nodes) PJ_CK(cudaMemcpy(nodes, b.d_nodes, 4 * (size_t)b.n_nodes * sw, cudaMemcpyDeviceToHost));
   if (roots) PJ_CK(cudaMemcpy(roots, b.d_roots, 4 * d->M, cudaMemcpyDeviceToHost));
   if (tri_order) {
     PJ_CK(cudaMemcpy(tri_order, b.d_tri_order, 4 * d->F, cudaMemcpyDeviceToHost));

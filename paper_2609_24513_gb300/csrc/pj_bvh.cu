@@ -228,38 +228,46 @@ __global__ void k_collapse(const QEntry *qin, const unsigned int *qin_n,
       }
     }
     float *node = nodes + (int64_t)q.wide * sw;
-    uint32_t *child = reinterpret_cast<uint32_t *>(node + 6 * W);
+    {
+      const float *b = box_of(q.bin);
+      for (int d = 0; d < 6; ++d) node[d] = b[d];
+      node[6] = 0.f;
+      node[7] = 0.f;
+    }
     for (int k = 0; k < W; ++k) {
+      float *slot = node + 8 * (k + 1);
+      uint32_t *child = reinterpret_cast<uint32_t *>(slot + 6);
+      slot[7] = 0.f;
       if (k >= nf) {
         for (int d = 0; d < 3; ++d) {
-          node[d * W + k] = 3e38f;
-          node[(3 + d) * W + k] = -3e38f;
+          slot[d] = 3e38f;
+          slot[3 + d] = -3e38f;
         }
-        child[k] = kEmpty;
+        *child = kEmpty;
         continue;
       }
       int32_t r = fr[k];
       const float *b = box_of(r);
-      for (int d = 0; d < 6; ++d) node[d * W + k] = b[d];
+      for (int d = 0; d < 6; ++d) slot[d] = b[d];
       int c = count_of(r);
       if (c <= L) {
         int first = r < 0 ? (-r - 1) : T.first[ib + r];
-        child[k] = kLeafBit | ((uint32_t)first << 3) | (uint32_t)(c - 1);
+        *child = kLeafBit | ((uint32_t)first << 3) | (uint32_t)(c - 1);
       } else {
         unsigned int id = atomicAdd(node_ctr, 1u);
         if ((int64_t)id >= node_cap) {
           atomicExch(err, 1);
-          child[k] = kEmpty;
+          *child = kEmpty;
           continue;
         }
-        child[k] = id;
-        unsigned int slot = atomicAdd(qout_n, 1u);
+        *child = id;
+        unsigned int qs = atomicAdd(qout_n, 1u);
         QEntry o;
         o.bin = r;
         o.mesh = q.mesh;
         o.wide = (int32_t)id;
         o.depth = q.depth + 1;
-        qout[slot] = o;
+        qout[qs] = o;
       }
     }
     atomicMax(max_depth, q.depth);
@@ -424,6 +432,8 @@ pj_status build_bvh(Ctx *ctx, Dataset *ds, int W, int L, cudaStream_t s) {
   PJ_CK(cudaMemcpyAsync(hflag, dflag, 8, cudaMemcpyDeviceToHost, s));
   PJ_CK(cudaStreamSynchronize(s));
   if (hflag[1]) return fail(ctx, PJ_ERR_INTERNAL, "BVH node capacity exceeded");
+  if ((int64_t)n_nodes * W >= (1ll << 30))
+    return fail(ctx, PJ_ERR_INVALID_ARG, "dataset too large for 30-bit BVH slot ids");
   bvh.n_nodes = n_nodes;
   bvh.max_depth = hflag[0];
   PJ_CK(cudaMalloc(&bvh.d_nodes, sizeof(float) * (size_t)n_nodes * sw));

@@ -17,19 +17,21 @@ namespace pj {
 // ---------------------------------------------------------------------------
 // Encodings
 // ---------------------------------------------------------------------------
-// A wide node of width W is 8 * ceil(7W / 8) 32-bit words (so that nodes
-// start on 32-byte boundaries): lo_x[W] lo_y[W] lo_z[W] hi_x[W] hi_y[W]
-// hi_z[W] child[W] (padding).  A child word is
+// A wide node of width W is W + 1 slots of 8 32-bit words (32 bytes), so
+// that one child is two aligned 16-byte loads:
+//   slot 0 (header): lo_x lo_y lo_z hi_x hi_y hi_z 0 0   (the node's own box)
+//   slot k + 1:      lo_x lo_y lo_z hi_x hi_y hi_z child 0 (child k)
+// A child word is
 //   0xFFFFFFFF                 empty slot (its box is inverted: lo > hi)
-//   < 2^31                     index of a wide node (global in the dataset)
+//   < 2^30                     index of a wide node (global in the dataset)
 //   bit 31 | first << 3 | n-1  leaf: n in [1, 8] triangles starting at the
 //                              mesh-local sorted position `first` (< 2^28)
 // A traversal item is a 32-bit word: an internal wide node index, or
-// bit 31 | (node * W + slot) for the leaf held in `slot` of `node`.
+// bit 31 | (node * W + k) for the leaf held in child k of `node`.
 constexpr uint32_t kEmpty = 0xFFFFFFFFu;
 constexpr uint32_t kLeafBit = 0x80000000u;
 
-__host__ __device__ inline int node_stride_words(int W) { return ((7 * W + 7) / 8) * 8; }
+__host__ __device__ inline int node_stride_words(int W) { return 8 * (W + 1); }
 
 // Triangle record in BVH-leaf order: three float4
 //   r0 = (ax, ay, az, bx)  r1 = (by, bz, cx, cy)  r2 = (cz, owner bits, local id, 0)

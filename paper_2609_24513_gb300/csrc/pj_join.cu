@@ -218,6 +218,7 @@ struct RefineArgs {
   unsigned long long *counters;
   int *err;
   int stack_cap;             // task entries per warp
+  int max_pop;               // tasks popped per traversal step (1 = plain DFS)
   int warps_per_pair;        // 1, 2 or 4
   int64_t MA, MB;            // mesh counts (candidate ids are checked)
   long long single;          // >= 0: process only this candidate
@@ -227,13 +228,21 @@ struct Cnt {
   unsigned long long v[C_NUM];
 };
 
+// Traversal items (32-bit):
+//   internal node: node index (bits 0-29), bit 30 = expand this side next
+//   leaf:          bit 31 | slot id = node * W + child (bits 0-29)
+constexpr uint32_t kExpand = 0x40000000u;
+constexpr uint32_t kIdx = 0x3FFFFFFFu;
+
 template <int W>
 struct Cfg {
-  static constexpr int SW = ((7 * W + 7) / 8) * 8;  // node stride in words
-  static constexpr int LQ = W * W + 32;            // leaf-pair queue entries
+  static constexpr int SW = 8 * (W + 1);  // node stride in words
+  static constexpr int LQ = 128;          // leaf-pair queue entries
+  static constexpr int TQ = 32;           // tasks popped per step
   // per-warp shared memory besides the task stack
   static constexpr int extra_bytes = LQ * 8 /*queue*/ + LQ * 8 /*descriptors*/ +
-                                     (LQ + 1) * 4 /*prefix*/ + 2 * SW * 4 /*staged nodes*/;
+                                     (LQ + 1) * 4 /*unit prefix*/ + TQ * 8 /*popped*/ +
+                                     (TQ + 1) * 4 /*test prefix*/;
 };
 
 template <int W>
@@ -245,8 +254,9 @@ struct WarpMem {
   uint2 *stk;
   uint2 *lq;
   uint2 *ldesc;
+  uint2 *tq;
   int *lpre;
-  float *stage;
+  int *tpre;
 };
 
 template <int W>
@@ -255,12 +265,54 @@ __device__ __forceinline__ WarpMem carve(unsigned char *base, int stack_cap) {
   m.stk = reinterpret_cast<uint2 *>(base);
   m.lq = m.stk + stack_cap;
   m.ldesc = m.lq + Cfg<W>::LQ;
-  m.stage = reinterpret_cast<float *>(m.ldesc + Cfg<W>::LQ);
-  m.lpre = reinterpret_cast<int *>(m.stage + 2 * Cfg<W>::SW);
+  m.tq = m.ldesc + Cfg<W>::LQ;
+  m.lpre = reinterpret_cast<int *>(m.tq + Cfg<W>::TQ);
+  m.tpre = m.lpre + Cfg<W>::LQ + 1;
   return m;
 }
 
 __device__ __forceinline__ F3 ld3(const float *p) { return mkf3(p[0], p[1], p[2]); }
+
+struct Box {
+  F3 lo, hi;
+};
+
+// slot k of a node (k = -1: the node's own box): box and child word
+template <int W>
+__device__ __forceinline__ void load_slot(const float *nodes, uint32_t node, int k, F3 off,
+                                          Box &b, uint32_t &child) {
+  const float4 *p = reinterpret_cast<const float4 *>(nodes + (int64_t)node * Cfg<W>::SW +
+                                                     8 * (k + 1));
+  float4 u = __ldg(p), v = __ldg(p + 1);
+  b.lo = add(mkf3(u.x, u.y, u.z), off);
+  b.hi = add(mkf3(u.w, v.x, v.y), off);
+  child = __float_as_uint(v.z);
+}
+
+__device__ __forceinline__ bool overlap(const Box &a, const Box &b) {
+  return a.lo.x <= b.hi.x && b.lo.x <= a.hi.x && a.lo.y <= b.hi.y && b.lo.y <= a.hi.y &&
+         a.lo.z <= b.hi.z && b.lo.z <= a.hi.z;
+}
+
+__device__ __forceinline__ float extent(const Box &b) {
+  return fmaxf(fmaxf(b.hi.x - b.lo.x, b.hi.y - b.lo.y), b.hi.z - b.lo.z);
+}
+
+// Build a task from two items (flags stripped) and their boxes: a leaf never
+// expands; of two internal nodes, the one more than twice as large expands
+// alone, otherwise both do (simultaneous descent).
+__device__ __forceinline__ uint2 make_task(uint32_t a, const Box &ba, uint32_t b,
+                                          const Box &bb) {
+  const bool la = a & kLeafBit, lb = b & kLeafBit;
+  const float ea = extent(ba), eb = extent(bb);
+  const bool xa = !la && (lb || !(eb > 2.f * ea));
+  const bool xb = !lb && (la || !(ea > 2.f * eb));
+  return make_uint2(a | (xa ? kExpand : 0u), b | (xb ? kExpand : 0u));
+}
+
+__device__ __forceinline__ int task_tests(uint2 t, int W) {
+  return ((t.x & kExpand) ? W : 1) * ((t.y & kExpand) ? W : 1);
+}
 
 __device__ __forceinline__ void load_tri(const float4 *rec, int64_t s, F3 off, F3 &a,
                                          F3 &b, F3 &c, int &own) {
@@ -271,84 +323,84 @@ __device__ __forceinline__ void load_tri(const float4 *rec, int64_t s, F3 off, F
   own = __float_as_int(r2.y);
 }
 
+// warp-wide inclusive scan of small ints
+__device__ __forceinline__ int warp_scan_incl(int v, int lane) {
+  for (int o = 1; o < 32; o <<= 1) {
+    int t = __shfl_up_sync(FULL, v, o);
+    if (lane >= o) v += t;
+  }
+  return v;
+}
+
 // Leaf-pair work: one unit = (leaf pair, direction, source triangle).
 template <int W, bool EXACT>
 __device__ bool leaf_units(const Side &A, const Side &B, int64_t tA, int64_t tB, F3 off,
                            WarpMem &sm, int nlq, int lane, Cnt &cnt) {
-  constexpr int SW = Cfg<W>::SW;
-  // descriptors and unit counts
-  for (int e = lane; e < nlq; e += 32) {
-    uint2 q = sm.lq[e];
-    uint32_t sa = q.x & ~kLeafBit, sb = q.y & ~kLeafBit;
-    uint32_t da = __float_as_uint(__ldg(A.nodes + (int64_t)(sa / W) * SW + 6 * W + sa % W));
-    uint32_t db = __float_as_uint(__ldg(B.nodes + (int64_t)(sb / W) * SW + 6 * W + sb % W));
-    sm.ldesc[e] = make_uint2(da, db);
-  }
-  __syncwarp();
-  // prefix over entries (sequential chunks of 32)
+  const F3 zero = mkf3(0.f, 0.f, 0.f);
+  // descriptors (child words of the two leaf slots) and unit counts
   int run = 0;
   if (lane == 0) sm.lpre[0] = 0;
   for (int e0 = 0; e0 < nlq; e0 += 32) {
     int e = e0 + lane;
     int u = 0;
     if (e < nlq) {
-      uint2 d = sm.ldesc[e];
-      u = (int)(d.x & 7u) + 1 + (int)(d.y & 7u) + 1;
+      uint2 q = sm.lq[e];
+      uint32_t sa = q.x & kIdx, sb = q.y & kIdx;
+      const float *pa = A.nodes + (int64_t)(sa / W) * Cfg<W>::SW + 8 * (sa % W + 1);
+      const float *pb = B.nodes + (int64_t)(sb / W) * Cfg<W>::SW + 8 * (sb % W + 1);
+      uint32_t da = __float_as_uint(__ldg(pa + 6)), db = __float_as_uint(__ldg(pb + 6));
+      sm.ldesc[e] = make_uint2(da, db);
+      u = (int)(da & 7u) + 1 + (int)(db & 7u) + 1;
     }
-    int inc = u;
-    for (int o = 1; o < 32; o <<= 1) {
-      int t = __shfl_up_sync(FULL, inc, o);
-      if (lane >= o) inc += t;
-    }
+    int inc = warp_scan_incl(u, lane);
     if (e < nlq) sm.lpre[e + 1] = run + inc;
     run += __shfl_sync(FULL, inc, 31);
   }
   __syncwarp();
   const int U = run;
-  cnt.v[C_LEAF_PAIRS] += (lane == 0) ? nlq : 0;
-  cnt.v[C_BYTES] += (lane == 0) ? 8ull * nlq : 0;
+  if (lane == 0) {
+    cnt.v[C_LEAF_PAIRS] += nlq;
+    cnt.v[C_BYTES] += 8ull * nlq;
+  }
   bool hit = false;
   for (int base = 0; base < U; base += 32) {
     int u = base + lane;
     if (u < U && !hit) {
-      // entry: largest e with lpre[e] <= u
       int lo = 0, hi = nlq - 1;
       while (lo < hi) {
         int mid = (lo + hi + 1) >> 1;
         if (sm.lpre[mid] <= u) lo = mid; else hi = mid - 1;
       }
-      int e = lo;
-      int k = u - sm.lpre[e];
-      uint2 q = sm.lq[e];
-      uint2 d = sm.ldesc[e];
-      int nA = (int)(d.x & 7u) + 1;
-      bool dirA = k < nA;  // source triangle from A, target leaf in B
+      const int e = lo;
+      const int k = u - sm.lpre[e];
+      const uint2 q = sm.lq[e];
+      const uint2 d = sm.ldesc[e];
+      const int nA = (int)(d.x & 7u) + 1;
+      const bool dirA = k < nA;  // source triangle from A, target leaf in B
       const Side &S = dirA ? A : B;
       const Side &T = dirA ? B : A;
-      uint32_t sdesc = dirA ? d.x : d.y, tdesc = dirA ? d.y : d.x;
-      uint32_t tslot = (dirA ? q.y : q.x) & ~kLeafBit;
-      int64_t sbase = dirA ? tA : tB, tbase = dirA ? tB : tA;
-      F3 soff = dirA ? mkf3(0.f, 0.f, 0.f) : off;
-      F3 toff = dirA ? off : mkf3(0.f, 0.f, 0.f);
-      int si = dirA ? k : k - nA;
-      int64_t s_rec = sbase + ((sdesc >> 3) & 0x0FFFFFFFu) + si;
-      int64_t t_first = tbase + ((tdesc >> 3) & 0x0FFFFFFFu);
-      int t_n = (int)(tdesc & 7u) + 1;
-      // target leaf box from its parent node
-      const float *tn = T.nodes + (int64_t)(tslot / W) * SW;
-      int ts = tslot % W;
-      F3 tlo = add(mkf3(__ldg(tn + ts), __ldg(tn + W + ts), __ldg(tn + 2 * W + ts)), toff);
-      F3 thi = add(mkf3(__ldg(tn + 3 * W + ts), __ldg(tn + 4 * W + ts), __ldg(tn + 5 * W + ts)), toff);
+      const uint32_t sdesc = dirA ? d.x : d.y, tdesc = dirA ? d.y : d.x;
+      const uint32_t tslot = (dirA ? q.y : q.x) & kIdx;
+      const int64_t sbase = dirA ? tA : tB, tbase = dirA ? tB : tA;
+      const F3 soff = dirA ? zero : off;
+      const F3 toff = dirA ? off : zero;
+      const int si = dirA ? k : k - nA;
+      const int64_t s_rec = sbase + ((sdesc >> 3) & 0x0FFFFFFFu) + si;
+      const int64_t t_first = tbase + ((tdesc >> 3) & 0x0FFFFFFFu);
+      const int t_n = (int)(tdesc & 7u) + 1;
+      Box tb;
+      uint32_t tdummy;
+      load_slot<W>(T.nodes, tslot / W, (int)(tslot % W), toff, tb, tdummy);
       F3 v[3];
       int own;
       load_tri(S.trirec, s_rec, soff, v[0], v[1], v[2], own);
-      cnt.v[C_BYTES] += 48 + 28;
+      cnt.v[C_BYTES] += 48 + 32;
       for (int ek = 0; ek < 3 && !hit; ++ek) {
         if (!((own >> ek) & 1)) continue;
         F3 p = v[ek], qv = v[ek == 2 ? 0 : ek + 1];
         Seg sg = make_seg(p, qv);
         cnt.v[C_SLAB_TESTS] += 1;
-        if (!slab_hit(sg, tlo, thi)) continue;
+        if (!slab_hit(sg, tb.lo, tb.hi)) continue;
         F3 elo = mkf3(fminf(p.x, qv.x), fminf(p.y, qv.y), fminf(p.z, qv.z));
         F3 ehi = mkf3(fmaxf(p.x, qv.x), fmaxf(p.y, qv.y), fmaxf(p.z, qv.z));
         for (int t = 0; t < t_n; ++t) {
@@ -386,19 +438,29 @@ __device__ bool leaf_units(const Side &A, const Side &B, int64_t tA, int64_t tB,
   return false;
 }
 
-// Crossing test of one pair by simultaneous descent of both BVHs.
-// Returns 1 on a crossing, 0 if none, -1 on a capacity error.
+// Crossing test of one pair by descending both BVHs (larger node first,
+// simultaneously when comparable).  Each step pops up to 32 tasks and spreads
+// their child-box tests over the lanes.  Returns 1 on a crossing, 0 if none,
+// -1 if the task stack would overflow.
 template <int W, bool EXACT>
 __device__ int pair_cross(const Side &A, const Side &B, int ia, int ib, F3 off,
-                          WarpMem &sm, int lane, int stack_cap, Cnt &cnt,
+                          WarpMem &sm, int lane, int stack_cap, int max_pop, Cnt &cnt,
                           volatile int *group_hit, int rank, int nrank) {
-  constexpr int SW = Cfg<W>::SW, LQ = Cfg<W>::LQ;
+  constexpr int LQ = Cfg<W>::LQ;
   const int64_t tA = A.toff[ia], tB = B.toff[ib];
-  int sp = 1, nlq = 0;
-  if (lane == 0) sm.stk[0] = make_uint2((uint32_t)A.roots[ia], (uint32_t)B.roots[ib]);
-  __syncwarp();
-  float *sA = sm.stage, *sB = sm.stage + SW;
   const unsigned lt = (1u << lane) - 1u;
+  const F3 zero = mkf3(0.f, 0.f, 0.f);
+  {
+    const uint32_t ra = (uint32_t)A.roots[ia], rb = (uint32_t)B.roots[ib];
+    Box ba, bb;
+    ba.lo = ld3(A.aabb + 6 * (int64_t)ia);
+    ba.hi = ld3(A.aabb + 6 * (int64_t)ia + 3);
+    bb.lo = add(ld3(B.aabb + 6 * (int64_t)ib), off);
+    bb.hi = add(ld3(B.aabb + 6 * (int64_t)ib + 3), off);
+    if (lane == 0) sm.stk[0] = make_task(ra, ba, rb, bb);
+  }
+  int sp = 1, nlq = 0;
+  __syncwarp();
   bool split_done = nrank <= 1;
   unsigned iters = 0;
   while (sp > 0 || nlq > 0) {
@@ -407,51 +469,87 @@ __device__ int pair_cross(const Side &A, const Side &B, int ia, int ib, F3 off,
       int gh = __shfl_sync(FULL, *group_hit, 0);
       if (gh) return 1;
     }
-    if (sp > 0 && nlq + W * W <= LQ) {
-      if (sp - 1 + W * W > stack_cap) return -1;
-      uint2 t = sm.stk[sp - 1];
-      --sp;
-      __syncwarp();
-      const uint32_t a = t.x, b = t.y;
-      const bool aLeaf = a & kLeafBit, bLeaf = b & kLeafBit;
-      const uint32_t an = aLeaf ? (a & ~kLeafBit) / W : a;
-      const uint32_t bn = bLeaf ? (b & ~kLeafBit) / W : b;
-      const int as = aLeaf ? (int)((a & ~kLeafBit) % W) : 0;
-      const int bs = bLeaf ? (int)((b & ~kLeafBit) % W) : 0;
-      const float *ga = A.nodes + (int64_t)an * SW, *gb = B.nodes + (int64_t)bn * SW;
-      for (int k = lane; k < SW; k += 32) {
-        sA[k] = __ldg(ga + k);
-        sB[k] = __ldg(gb + k);
+    if (sp > 0 && nlq + 64 <= LQ) {
+      // pop up to max_pop tasks whose tests add up to at most 32 (at least one)
+      const int e = sp - 1 - lane;
+      const bool valid = lane < max_pop && e >= 0;
+      const uint2 t = valid ? sm.stk[e] : make_uint2(0u, 0u);
+      const int nt = valid ? task_tests(t, W) : 0;
+      const int incl = warp_scan_incl(nt, lane);
+      int npop = __popc(__ballot_sync(FULL, valid && incl <= 32));
+      if (npop == 0) npop = 1;
+      int T = __shfl_sync(FULL, incl, npop - 1);
+      // the pushes must fit: shrink the batch, down to one task
+      while (npop > 1 && sp - npop + T > stack_cap) {
+        --npop;
+        T = __shfl_sync(FULL, incl, npop - 1);
+      }
+      if (sp - npop + T > stack_cap) return -1;
+      if (lane < npop) {
+        sm.tq[lane] = t;
+        sm.tpre[lane] = incl - nt;
       }
       __syncwarp();
-      const int nA = aLeaf ? 1 : W, nB = bLeaf ? 1 : W, tot = nA * nB;
-      for (int base = 0; base < tot; base += 32) {
-        int tt = base + lane;
-        bool ok = tt < tot;
-        int i = ok ? tt / nB : 0;
-        int j = ok ? tt - i * nB : 0;
-        int sa = aLeaf ? as : i, sb = bLeaf ? bs : j;
-        uint32_t ca = __float_as_uint(sA[6 * W + sa]), cb = __float_as_uint(sB[6 * W + sb]);
-        ok = ok && ca != kEmpty && cb != kEmpty;
-        if (ok) {
-          ok = sA[sa] <= sB[3 * W + sb] + off.x && sB[sb] + off.x <= sA[3 * W + sa] &&
-               sA[W + sa] <= sB[4 * W + sb] + off.y && sB[W + sb] + off.y <= sA[4 * W + sa] &&
-               sA[2 * W + sa] <= sB[5 * W + sb] + off.z && sB[2 * W + sb] + off.z <= sA[5 * W + sa];
+      sp -= npop;
+      for (int base = 0; base < T; base += 32) {
+        const int u = base + lane;
+        const bool act = u < T;
+        int k = 0;
+        if (act) {
+          int lo = 0, hi = npop - 1;
+          while (lo < hi) {
+            int mid = (lo + hi + 1) >> 1;
+            if (sm.tpre[mid] <= u) lo = mid; else hi = mid - 1;
+          }
+          k = lo;
         }
-        uint32_t na = aLeaf ? a : ((ca & kLeafBit) ? (kLeafBit | (an * W + sa)) : ca);
-        uint32_t nb = bLeaf ? b : ((cb & kLeafBit) ? (kLeafBit | (bn * W + sb)) : cb);
-        bool both = ok && (na & kLeafBit) && (nb & kLeafBit);
-        bool push = ok && !both;
-        unsigned m1 = __ballot_sync(FULL, push), m2 = __ballot_sync(FULL, both);
-        if (push) sm.stk[sp + __popc(m1 & lt)] = make_uint2(na, nb);
+        const uint2 tk = act ? sm.tq[k] : make_uint2(0u, 0u);
+        const int r = act ? u - sm.tpre[k] : 0;
+        const bool xa = tk.x & kExpand, xb = tk.y & kExpand;
+        const int nB = xb ? W : 1;
+        const int i = r / nB, j = r - (r / nB) * nB;
+        bool ok = act;
+        Box ba, bb;
+        uint32_t na = 0, nb = 0;
+        if (act) {
+          uint32_t ca, cb;
+          const uint32_t ia2 = tk.x & kIdx, ib2 = tk.y & kIdx;
+          if (xa) {
+            load_slot<W>(A.nodes, ia2, i, zero, ba, ca);
+            ok = ok && ca != kEmpty;
+            na = (ca & kLeafBit) ? (kLeafBit | (ia2 * W + i)) : ca;
+          } else if (tk.x & kLeafBit) {
+            load_slot<W>(A.nodes, ia2 / W, (int)(ia2 % W), zero, ba, ca);
+            na = tk.x;
+          } else {
+            load_slot<W>(A.nodes, ia2, -1, zero, ba, ca);
+            na = tk.x & ~kExpand;
+          }
+          if (xb) {
+            load_slot<W>(B.nodes, ib2, j, off, bb, cb);
+            ok = ok && cb != kEmpty;
+            nb = (cb & kLeafBit) ? (kLeafBit | (ib2 * W + j)) : cb;
+          } else if (tk.y & kLeafBit) {
+            load_slot<W>(B.nodes, ib2 / W, (int)(ib2 % W), off, bb, cb);
+            nb = tk.y;
+          } else {
+            load_slot<W>(B.nodes, ib2, -1, off, bb, cb);
+            nb = tk.y & ~kExpand;
+          }
+          ok = ok && overlap(ba, bb);
+        }
+        const bool both = ok && (na & kLeafBit) && (nb & kLeafBit);
+        const bool push = ok && !both;
+        const unsigned m1 = __ballot_sync(FULL, push), m2 = __ballot_sync(FULL, both);
+        if (push) sm.stk[sp + __popc(m1 & lt)] = make_task(na, ba, nb, bb);
         if (both) sm.lq[nlq + __popc(m2 & lt)] = make_uint2(na, nb);
         sp += __popc(m1);
         nlq += __popc(m2);
+        if (act) cnt.v[C_BYTES] += 64;
       }
       if (lane == 0) {
-        cnt.v[C_NODE_PAIRS] += 1;
-        cnt.v[C_BOX_TESTS] += tot;
-        cnt.v[C_BYTES] += 2 * SW * 4;
+        cnt.v[C_NODE_PAIRS] += npop;
+        cnt.v[C_BOX_TESTS] += T;
       }
       __syncwarp();
       if (!split_done) {
@@ -460,9 +558,9 @@ __device__ int pair_cross(const Side &A, const Side &B, int ia, int ib, F3 off,
         split_done = true;
         int nsp = 0, nl = 0;
         for (int e0 = 0; e0 < sp; e0 += 32) {
-          int e = e0 + lane;
-          bool keep = e < sp && (e % nrank) == rank;
-          uint2 v = keep ? sm.stk[e] : make_uint2(0, 0);
+          int ee = e0 + lane;
+          bool keep = ee < sp && (ee % nrank) == rank;
+          uint2 v = keep ? sm.stk[ee] : make_uint2(0, 0);
           unsigned m = __ballot_sync(FULL, keep);
           __syncwarp();
           if (keep) sm.stk[nsp + __popc(m & lt)] = v;
@@ -470,9 +568,9 @@ __device__ int pair_cross(const Side &A, const Side &B, int ia, int ib, F3 off,
           __syncwarp();
         }
         for (int e0 = 0; e0 < nlq; e0 += 32) {
-          int e = e0 + lane;
-          bool keep = e < nlq && ((sp + e) % nrank) == rank;
-          uint2 v = keep ? sm.lq[e] : make_uint2(0, 0);
+          int ee = e0 + lane;
+          bool keep = ee < nlq && ((sp + ee) % nrank) == rank;
+          uint2 v = keep ? sm.lq[ee] : make_uint2(0, 0);
           unsigned m = __ballot_sync(FULL, keep);
           __syncwarp();
           if (keep) sm.lq[nl + __popc(m & lt)] = v;
@@ -483,7 +581,7 @@ __device__ int pair_cross(const Side &A, const Side &B, int ia, int ib, F3 off,
         nlq = nl;
       }
     }
-    if (nlq > 0 && (sp == 0 || nlq + W * W > LQ || nlq >= 32)) {
+    if (nlq > 0 && (sp == 0 || nlq + 64 > LQ || nlq >= 32)) {
       bool h = leaf_units<W, EXACT>(A, B, tA, tB, off, sm, nlq, lane, cnt);
       nlq = 0;
       __syncwarp();
@@ -499,7 +597,7 @@ __device__ int pair_cross(const Side &A, const Side &B, int ia, int ib, F3 off,
 template <int W>
 __device__ int parity_query(const Side &T, int it, F3 toff, F3 vf, WarpMem &sm,
                             int lane, int stack_cap, Cnt &cnt) {
-  constexpr int SW = Cfg<W>::SW, LQ = Cfg<W>::LQ;
+  constexpr int LQ = Cfg<W>::LQ;
   const int64_t tbase = T.toff[it];
   const I3 v = toi(vf);
   const unsigned lt = (1u << lane) - 1u;
@@ -516,55 +614,39 @@ __device__ int parity_query(const Side &T, int it, F3 toff, F3 vf, WarpMem &sm,
       int P = min(sp, 32 / W);
       while (P > 0 && sp - P + P * W > stack_cap) --P;
       if (P == 0) return -1;
-      int ni = lane / W, c = lane % W;
+      const int ni = lane / W, c = lane % W;
       bool ok = ni < P;
-      uint32_t node = ok ? sm.stk[sp - 1 - ni].x : 0;
+      const uint32_t node = ok ? sm.stk[sp - 1 - ni].x : 0u;
       __syncwarp();
       sp -= P;
       uint32_t ch = kEmpty;
       if (ok) {
-        const float *g = T.nodes + (int64_t)node * SW;
-        ch = __float_as_uint(__ldg(g + 6 * W + c));
-        if (ch != kEmpty) {
-          float lx = __ldg(g + c) + toff.x, ly = __ldg(g + W + c) + toff.y;
-          float hx = __ldg(g + 3 * W + c) + toff.x, hy = __ldg(g + 4 * W + c) + toff.y;
-          float hz = __ldg(g + 5 * W + c) + toff.z;
-          ok = lx <= vf.x && vf.x <= hx && ly <= vf.y && vf.y <= hy && vf.z <= hz;
-        } else {
-          ok = false;
-        }
+        Box b;
+        load_slot<W>(T.nodes, node, c, toff, b, ch);
+        ok = ch != kEmpty && b.lo.x <= vf.x && vf.x <= b.hi.x && b.lo.y <= vf.y &&
+             vf.y <= b.hi.y && vf.z <= b.hi.z;
       }
-      bool leaf = ok && (ch & kLeafBit);
-      bool inner = ok && !leaf;
-      unsigned m1 = __ballot_sync(FULL, inner), m2 = __ballot_sync(FULL, leaf);
+      const bool leaf = ok && (ch & kLeafBit);
+      const bool inner = ok && !leaf;
+      const unsigned m1 = __ballot_sync(FULL, inner), m2 = __ballot_sync(FULL, leaf);
       if (inner) sm.stk[sp + __popc(m1 & lt)].x = ch;
-      if (leaf) sm.lq[nlq + __popc(m2 & lt)].x = kLeafBit | (node * W + c);
+      if (leaf) sm.lq[nlq + __popc(m2 & lt)] = make_uint2(node * W + c, ch);
       sp += __popc(m1);
       nlq += __popc(m2);
       if (lane == 0) {
         cnt.v[C_PARITY_NODES] += P;
-        cnt.v[C_BYTES] += (unsigned long long)P * SW * 4;
+        cnt.v[C_BYTES] += (unsigned long long)P * W * 32;
       }
       __syncwarp();
     }
     if (nlq > 0 && (sp == 0 || nlq + 32 > LQ)) {
-      // flatten leaf triangles
+      // flatten the queued leaves' triangles over the lanes
       int run = 0;
       if (lane == 0) sm.lpre[0] = 0;
       for (int e0 = 0; e0 < nlq; e0 += 32) {
         int e = e0 + lane;
-        int u = 0;
-        if (e < nlq) {
-          uint32_t sl = sm.lq[e].x & ~kLeafBit;
-          uint32_t d = __float_as_uint(__ldg(T.nodes + (int64_t)(sl / W) * SW + 6 * W + sl % W));
-          sm.ldesc[e].x = d;
-          u = (int)(d & 7u) + 1;
-        }
-        int inc = u;
-        for (int o = 1; o < 32; o <<= 1) {
-          int t = __shfl_up_sync(FULL, inc, o);
-          if (lane >= o) inc += t;
-        }
+        int u = e < nlq ? (int)(sm.lq[e].y & 7u) + 1 : 0;
+        int inc = warp_scan_incl(u, lane);
         if (e < nlq) sm.lpre[e + 1] = run + inc;
         run += __shfl_sync(FULL, inc, 31);
       }
@@ -577,8 +659,8 @@ __device__ int parity_query(const Side &T, int it, F3 toff, F3 vf, WarpMem &sm,
             int mid = (lo + hi + 1) >> 1;
             if (sm.lpre[mid] <= u) lo = mid; else hi = mid - 1;
           }
-          uint32_t d = sm.ldesc[lo].x;
-          int64_t s = tbase + ((d >> 3) & 0x0FFFFFFFu) + (u - sm.lpre[lo]);
+          const uint32_t d = sm.lq[lo].y;
+          const int64_t s = tbase + ((d >> 3) & 0x0FFFFFFFu) + (u - sm.lpre[lo]);
           F3 a, b, c;
           int own;
           load_tri(T.trirec, s, toff, a, b, c, own);
@@ -626,7 +708,7 @@ __device__ __forceinline__ void bar_group(int id, int nthreads) {
 }
 
 template <int W, bool EXACT>
-__global__ void __launch_bounds__(128) k_refine(RefineArgs P) {
+__global__ void __launch_bounds__(128, 4) k_refine(RefineArgs P) {
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ int group_flag[4];
   __shared__ long long group_cand[4];
@@ -673,7 +755,8 @@ __global__ void __launch_bounds__(128) k_refine(RefineArgs P) {
     volatile int *gflag = k > 1 ? &group_flag[grp] : nullptr;
     int res = 0;
     if (overlap)
-      res = pair_cross<W, EXACT>(P.A, P.B, ia, ib, off, sm, lane, P.stack_cap, cnt, gflag, rank, k);
+      res = pair_cross<W, EXACT>(P.A, P.B, ia, ib, off, sm, lane, P.stack_cap, P.max_pop, cnt,
+                                 gflag, rank, k);
     if (res < 0) {
       if (lane == 0) atomicCAS(P.err, 0, DERR_STACK);
       res = 0;
@@ -947,8 +1030,9 @@ pj_status run_join(Ctx *ctx, Dataset *A, Dataset *B, const int32_t *cand,
   PJ_CK(cudaEventRecord(ev[1], s));
   // 2. refinement
   const int depth = std::max(bA.max_depth, 1) + std::max(bB.max_depth, 1);
-  int stack_cap = 1 + (W * W - 1) * depth + 32;
-  stack_cap = std::max(stack_cap, 64);
+  // plain depth-first order needs at most 1 + (W^2 - 1) * depth entries; the
+  // batched pops get 256 more and fall back to plain DFS if that is not enough
+  int stack_cap = 1 + (W * W - 1) * depth + 256;
   const int per_warp = smem_per_warp(W, stack_cap);
   int threads = 128;
   if (per_warp * 4 > 200 * 1024) return fail(ctx, PJ_ERR_INTERNAL, "BVH too deep for the traversal stack");
@@ -966,6 +1050,7 @@ pj_status run_join(Ctx *ctx, Dataset *A, Dataset *B, const int32_t *cand,
   args.counters = ctx->d_counters;
   args.err = ctx->d_err;
   args.stack_cap = stack_cap;
+  args.max_pop = 32;
   args.warps_per_pair = k;
   args.MA = A->M;
   args.MB = B->M;
@@ -1053,6 +1138,18 @@ pj_status run_join(Ctx *ctx, Dataset *A, Dataset *B, const int32_t *cand,
   PJ_CK(cudaStreamSynchronize(s));
   if (herr[1]) return fail(ctx, PJ_ERR_INVALID_ARG, "a candidate mesh id is out of range");
   if (herr[2]) return fail(ctx, PJ_ERR_INVALID_ARG, "a translated candidate mesh leaves the 2^18 grid");
+  if (herr[0] == DERR_STACK) {
+    // batched pops outgrew the stack: redo every pair in plain depth-first
+    // order, whose stack bound holds by construction
+    args.max_pop = 1;
+    PJ_CK(cudaMemsetAsync(ctx->d_err, 0, sizeof(int) * 4, s));
+    if ((st = device_part(true)) != PJ_OK) return st;
+    PJ_CK(cudaEventRecord(e1, s));
+    PJ_CK(cudaMemcpyAsync(h_misc + 1, d_misc + 1, 8, cudaMemcpyDeviceToHost, s));
+    PJ_CK(cudaMemcpyAsync(herr, ctx->d_err, sizeof(herr), cudaMemcpyDeviceToHost, s));
+    PJ_CK(cudaStreamSynchronize(s));
+    replayed = false;
+  }
   if (herr[0]) return fail(ctx, PJ_ERR_INTERNAL, "traversal stack capacity exceeded");
   const int64_t K = h_misc[1];
   float ms = 0.f;

@@ -274,11 +274,11 @@ def pj_segtri_batch(ctx, pq, abc, res, mode=PJ_LEAF_FILTERED, stream=None) -> in
 
 
 def pj_export_bvh(ctx, ds: int, width: int, leaf_size: int, n_tris: int, n_meshes: int):
-    """(nodes [n, 7W] int32 words, roots [M], tri_order [F]) as numpy arrays."""
+    """(nodes [n, W + 1, 8] int32 words, roots [M], tri_order [F]) as numpy arrays."""
     n = _i64()
     lib = load()
     _check(ctx, lib.pj_export_bvh(ctx, ds, width, leaf_size, None, None, None, ctypes.byref(n)))
-    nodes = np.zeros((n.value, 7 * width), dtype=np.int32)
+    nodes = np.zeros((n.value, width + 1, 8), dtype=np.int32)
     roots = np.zeros(n_meshes, dtype=np.int32)
     order = np.zeros(n_tris, dtype=np.int32)
     _check(ctx, lib.pj_export_bvh(ctx, ds, width, leaf_size, _ptr(nodes), _ptr(roots),

@@ -131,7 +131,7 @@ def test_instanced_candidates(ctx):
         va, _ = A.mesh(int(i))
         vb, _ = B.mesh(int(j))
         # shift B_j so that its centre lands near A_i's centre (kept on the grid)
-        d = np.rint(va.mean(axis=0) - vb.mean(axis=0) + rng.normal(0, 12000, size=3))
+        d = np.rint(va.mean(axis=0) - vb.mean(axis=0) + rng.normal(0, 30000, size=3))
         d = np.clip(d, -vb.min(axis=0), synth.QMAX - vb.max(axis=0))
         cand.append((i, j))
         offs.append(d)
@@ -213,9 +213,17 @@ def test_mesh_data_and_bvh_structure(ctx):
     assert info["n_edges"] == len(ds.tris) * 3 // 2
     for W, L in ((2, 1), (4, 4), (8, 8), (4, 1)):
         nodes, roots, order = pierce.pj_export_bvh(ctx.h, h, W, L, len(ds.tris), ds.nmesh)
-        lo = nodes[:, :3 * W].view(np.float32).reshape(-1, 3, W)
-        hi = nodes[:, 3 * W:6 * W].view(np.float32).reshape(-1, 3, W)
-        child = nodes[:, 6 * W:7 * W].view(np.uint32)
+        f = nodes.view(np.float32)
+        own_lo, own_hi = f[:, 0, 0:3], f[:, 0, 3:6]
+        lo = f[:, 1:, 0:3].transpose(0, 2, 1)          # [node, axis, child]
+        hi = f[:, 1:, 3:6].transpose(0, 2, 1)
+        child = nodes[:, 1:, 6].view(np.uint32)
+        live = child != 0xFFFFFFFF
+        # a node's own box is the union of its live children's boxes
+        for n in range(len(nodes)):
+            m = live[n]
+            assert np.array_equal(own_lo[n], lo[n][:, m].min(axis=1))
+            assert np.array_equal(own_hi[n], hi[n][:, m].max(axis=1))
         for k in range(ds.nmesh):
             v, t = ds.mesh(k)
             ordk = order[ds.toff[k]:ds.toff[k + 1]]
