@@ -212,7 +212,8 @@ def run_ours(args, rank, world, local_rank):
     A, B = make_workload(args.seed + 1000 * rank, args.nuclei, args.vessels)  # one per rank
     gen_s = time.perf_counter() - t0
     ctx = pierce.Context(local_rank)
-    stream = torch.cuda.current_stream()
+    stream = torch.cuda.Stream()                     # every step and event on one stream
+    torch.cuda.set_stream(stream)
     t0 = time.perf_counter()
     ha, hb = ctx.load(A), ctx.load(B)
     load_s = time.perf_counter() - t0

@@ -89,6 +89,11 @@ typedef struct {
   int32_t use_graph;        /* replay the device part as a captured CUDA graph */
   int32_t out_host;         /* 1: result pairs in library-owned host memory   */
   int32_t keep_flags;       /* 1: also return the per-candidate result bytes  */
+  int32_t record_cycles;    /* 1: also return each candidate's SM clock cycles
+                               (instrumentation of per-pair cost)            */
+  int32_t spill_budget;     /* traversal steps a warp spends on one pair in the
+                               first pass before handing the rest of it to
+                               later passes (0: 64; < 0: never)             */
 } pj_join_opts;
 
 /* Result of a join.  Owned by the library until pj_free_pairs. */
@@ -105,6 +110,9 @@ typedef struct {
   float mbb_ms;             /* of which: bounding-box filter join             */
   float refine_ms;          /* of which: refinement (crossing + parity)       */
   float compact_ms;         /* of which: compaction                           */
+  uint32_t *cycles;         /* device, C values (only with record_cycles):
+                               clock64 cycles the refinement spent on each
+                               candidate (saturated at 2^32 - 1)              */
   void *impl;
 } pj_pairs;
 
@@ -123,7 +131,9 @@ typedef struct {
   uint64_t bytes_fetched;       /* algorithmic bytes: nodes, triangles, vertices */
   uint64_t pairs_hit;           /* pairs found intersecting                     */
   uint64_t kernel_launches;     /* kernels launched by joins (host count)       */
-  uint64_t reserved[3];
+  uint64_t tasks_spilled;       /* traversal tasks handed to a later pass        */
+  uint64_t tasks_resumed;       /* spilled tasks taken up by a later pass        */
+  uint64_t reserved;
 } pj_counters;
 
 /* Dataset summary. */

@@ -551,6 +551,7 @@ pj_status pj_free_pairs(pj_ctx *h, pj_pairs *res) {
     if (res->on_device) cudaFree(res->pairs); else cudaFreeHost(res->pairs);
   }
   if (res->flags) cudaFree(res->flags);
+  if (res->cycles) cudaFree(res->cycles);
   memset(res, 0, sizeof(*res));
   return PJ_OK;
 }
@@ -577,6 +578,8 @@ pj_status pj_get_counters(pj_ctx *h, pj_counters *out) {
   out->bytes_fetched = c[C_BYTES];
   out->pairs_hit = c[C_HITS];
   out->kernel_launches = ctx->launches;
+  out->tasks_spilled = c[C_SPILLED];
+  out->tasks_resumed = c[C_TASKS];
   return PJ_OK;
 }
 

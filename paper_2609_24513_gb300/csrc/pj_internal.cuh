@@ -69,7 +69,7 @@ struct Dataset {
 enum {
   C_PAIRS = 0, C_NODE_PAIRS, C_BOX_TESTS, C_LEAF_PAIRS, C_SLAB_TESTS,
   C_SEGTRI, C_FALLBACK, C_PARITY_RAYS, C_PARITY_NODES, C_PARITY_TRIS,
-  C_BYTES, C_HITS, C_NUM = 16
+  C_BYTES, C_HITS, C_SPILLED, C_TASKS, C_NUM = 16
 };
 
 struct Workspace {

@@ -222,10 +222,31 @@ struct RefineArgs {
   int warps_per_pair;        // 1, 2 or 4
   int64_t MA, MB;            // mesh counts (candidate ids are checked)
   long long single;          // >= 0: process only this candidate
+  unsigned int *cycles;      // per-candidate SM cycles, or null
+  // pass 1 spill queue and budget; later passes read q_in
+  uint4 *q_out;
+  unsigned int *q_out_n;
+  unsigned int q_cap;
+  int budget;
+  const uint4 *q_in;
+  const unsigned int *q_in_n;
+  unsigned int *q_in_pos;
 };
 
 struct Cnt {
   unsigned long long v[C_NUM];
+};
+
+// Work handed from one refinement pass to the next: when a pair exceeds its
+// step budget its remaining traversal tasks go to a queue of
+// (candidate, itemA, itemB) entries that the next pass spreads over warps.
+struct Spill {
+  uint4 *q;                  // queue to append to (null: never spill)
+  unsigned int *q_n;         // its fill counter
+  unsigned int q_cap;
+  int budget;                // traversal steps before spilling (0: unbounded)
+  const volatile uint8_t *flag;  // this pair's result, polled for early exit
+  uint32_t cand;
 };
 
 // Traversal items (32-bit):
@@ -445,12 +466,13 @@ __device__ bool leaf_units(const Side &A, const Side &B, int64_t tA, int64_t tB,
 template <int W, bool EXACT>
 __device__ int pair_cross(const Side &A, const Side &B, int ia, int ib, F3 off,
                           WarpMem &sm, int lane, int stack_cap, int max_pop, Cnt &cnt,
-                          volatile int *group_hit, int rank, int nrank) {
+                          volatile int *group_hit, int rank, int nrank, const Spill &spill,
+                          bool from_root, uint2 start) {
   constexpr int LQ = Cfg<W>::LQ;
   const int64_t tA = A.toff[ia], tB = B.toff[ib];
   const unsigned lt = (1u << lane) - 1u;
   const F3 zero = mkf3(0.f, 0.f, 0.f);
-  {
+  if (from_root) {
     const uint32_t ra = (uint32_t)A.roots[ia], rb = (uint32_t)B.roots[ib];
     Box ba, bb;
     ba.lo = ld3(A.aabb + 6 * (int64_t)ia);
@@ -458,6 +480,8 @@ __device__ int pair_cross(const Side &A, const Side &B, int ia, int ib, F3 off,
     bb.lo = add(ld3(B.aabb + 6 * (int64_t)ib), off);
     bb.hi = add(ld3(B.aabb + 6 * (int64_t)ib + 3), off);
     if (lane == 0) sm.stk[0] = make_task(ra, ba, rb, bb);
+  } else if (lane == 0) {
+    sm.stk[0] = start;
   }
   int sp = 1, nlq = 0;
   __syncwarp();
@@ -468,6 +492,31 @@ __device__ int pair_cross(const Side &A, const Side &B, int ia, int ib, F3 off,
     if (group_hit) {
       int gh = __shfl_sync(FULL, *group_hit, 0);
       if (gh) return 1;
+    }
+    if (spill.flag && (iters & 15u) == 0) {
+      // another warp may already have found a crossing of this pair
+      int f = lane == 0 ? (int)*spill.flag : 0;
+      if (__shfl_sync(FULL, f, 0)) return 1;
+    }
+    if (spill.budget > 0 && iters > (unsigned)spill.budget && sp > 0) {
+      // over budget: finish the queued leaf pairs, then hand the remaining
+      // tasks to the next pass, where other warps take them
+      if (nlq > 0) {
+        bool h = leaf_units<W, EXACT>(A, B, tA, tB, off, sm, nlq, lane, cnt);
+        nlq = 0;
+        __syncwarp();
+        if (h) return 1;
+      }
+      unsigned base = 0;
+      if (lane == 0) base = atomicAdd(spill.q_n, (unsigned)sp);
+      base = __shfl_sync(FULL, base, 0);
+      if ((uint64_t)base + (uint64_t)sp > (uint64_t)spill.q_cap) return -3;
+      for (int e = lane; e < sp; e += 32) {
+        uint2 t = sm.stk[e];
+        spill.q[base + e] = make_uint4(spill.cand, t.x, t.y, 0u);
+      }
+      if (lane == 0) cnt.v[C_SPILLED] += sp;
+      return -2;
     }
     if (sp > 0 && nlq + 64 <= LQ) {
       // pop up to max_pop tasks whose tests add up to at most 32 (at least one)
@@ -596,7 +645,7 @@ __device__ int pair_cross(const Side &A, const Side &B, int ia, int ib, F3 off,
 // or -1 on a capacity error.
 template <int W>
 __device__ int parity_query(const Side &T, int it, F3 toff, F3 vf, WarpMem &sm,
-                            int lane, int stack_cap, Cnt &cnt) {
+                            int lane, int stack_cap, int max_pop, Cnt &cnt) {
   constexpr int LQ = Cfg<W>::LQ;
   const int64_t tbase = T.toff[it];
   const I3 v = toi(vf);
@@ -611,7 +660,7 @@ __device__ int parity_query(const Side &T, int it, F3 toff, F3 vf, WarpMem &sm,
   while (sp > 0 || nlq > 0) {
     if (++iters > (1u << 26)) return -1;  // defensive bound: a tree walk is finite
     if (sp > 0 && nlq + 32 <= LQ) {
-      int P = min(sp, 32 / W);
+      int P = min(min(sp, 32 / W), max_pop);
       while (P > 0 && sp - P + P * W > stack_cap) --P;
       if (P == 0) return -1;
       const int ni = lane / W, c = lane % W;
@@ -686,7 +735,7 @@ __device__ int parity_query(const Side &T, int it, F3 toff, F3 vf, WarpMem &sm,
 // ends the search.  Returns 1/0, or -1 on a capacity error.
 template <int W>
 __device__ int pair_inside(const Side &Q, int iq, F3 qoff, const Side &T, int it, F3 toff,
-                           WarpMem &sm, int lane, int stack_cap, Cnt &cnt) {
+                           WarpMem &sm, int lane, int stack_cap, int max_pop, Cnt &cnt) {
   const int64_t v0 = Q.voff[iq], nv = Q.voff[iq + 1] - v0;
   const float *tb = T.aabb + 6 * (int64_t)it;
   F3 lo = add(ld3(tb), toff), hi = add(ld3(tb + 3), toff);
@@ -696,7 +745,7 @@ __device__ int pair_inside(const Side &Q, int iq, F3 qoff, const Side &T, int it
     if (lane == 0) cnt.v[C_BYTES] += 16;
     if (v.x < lo.x || v.x > hi.x || v.y < lo.y || v.y > hi.y || v.z < lo.z || v.z > hi.z)
       return 0;
-    int r = parity_query<W>(T, it, toff, v, sm, lane, stack_cap, cnt);
+    int r = parity_query<W>(T, it, toff, v, sm, lane, stack_cap, max_pop, cnt);
     if (r < 0) return -1;
     if (!(r & 2)) return r & 1;
   }
@@ -740,6 +789,7 @@ __global__ void __launch_bounds__(128, 4) k_refine(RefineArgs P) {
       }
     }
     if (c >= n) break;
+    const long long t_start = clock64();
     const int ia = P.cand[2 * c], ib = P.cand[2 * c + 1];
     if (ia < 0 || ia >= P.MA || ib < 0 || ib >= P.MB) {
       // reported by the candidate check; never dereference a bad id
@@ -753,12 +803,21 @@ __global__ void __launch_bounds__(128, 4) k_refine(RefineArgs P) {
     bool overlap = ba[0] <= bb[3] + off.x && bb[0] + off.x <= ba[3] && ba[1] <= bb[4] + off.y &&
                    bb[1] + off.y <= ba[4] && ba[2] <= bb[5] + off.z && bb[2] + off.z <= ba[5];
     volatile int *gflag = k > 1 ? &group_flag[grp] : nullptr;
+    Spill spill;
+    spill.q = P.q_out;
+    spill.q_n = P.q_out_n;
+    spill.q_cap = P.q_cap;
+    spill.budget = (k == 1 && P.q_out) ? P.budget : 0;
+    spill.flag = nullptr;
+    spill.cand = (uint32_t)c;
     int res = 0;
     if (overlap)
       res = pair_cross<W, EXACT>(P.A, P.B, ia, ib, off, sm, lane, P.stack_cap, P.max_pop, cnt,
-                                 gflag, rank, k);
-    if (res < 0) {
-      if (lane == 0) atomicCAS(P.err, 0, DERR_STACK);
+                                 gflag, rank, k, spill, true, make_uint2(0u, 0u));
+    if (res == -2) {
+      res = 0;  // the crossing test continues in the next pass
+    } else if (res < 0) {
+      if (lane == 0) atomicCAS(P.err, 0, res == -3 ? DERR_QUEUE : DERR_STACK);
       res = 0;
     }
     if (k > 1) {
@@ -772,9 +831,10 @@ __global__ void __launch_bounds__(128, 4) k_refine(RefineArgs P) {
       // take one direction each
       int r1 = 0, r2 = 0;
       F3 zero = mkf3(0.f, 0.f, 0.f);
-      if (rank == 0) r1 = pair_inside<W>(P.B, ib, off, P.A, ia, zero, sm, lane, P.stack_cap, cnt);
+      if (rank == 0)
+        r1 = pair_inside<W>(P.B, ib, off, P.A, ia, zero, sm, lane, P.stack_cap, P.max_pop, cnt);
       if ((k == 1 && r1 == 0) || (k > 1 && rank == 1))
-        r2 = pair_inside<W>(P.A, ia, zero, P.B, ib, off, sm, lane, P.stack_cap, cnt);
+        r2 = pair_inside<W>(P.A, ia, zero, P.B, ib, off, sm, lane, P.stack_cap, P.max_pop, cnt);
       if (r1 < 0 || r2 < 0) {
         if (lane == 0) atomicCAS(P.err, 0, DERR_STACK);
         r1 = r2 = 0;
@@ -788,6 +848,10 @@ __global__ void __launch_bounds__(128, 4) k_refine(RefineArgs P) {
       }
     }
     if (rank == 0 && lane == 0) {
+      if (P.cycles) {
+        long long dt = clock64() - t_start;
+        P.cycles[c] = dt > 0xFFFFFFFFll ? 0xFFFFFFFFu : (unsigned int)dt;
+      }
       P.flags[c] = (uint8_t)res;
       cnt.v[C_PAIRS] += 1;
       cnt.v[C_HITS] += res;
@@ -795,6 +859,56 @@ __global__ void __launch_bounds__(128, 4) k_refine(RefineArgs P) {
     }
   }
   // flush counters (warp-aggregated)
+  for (int i = 0; i < C_NUM; ++i) {
+    unsigned long long v = cnt.v[i];
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(FULL, v, o);
+    if (lane == 0 && v) atomicAdd(P.counters + i, v);
+  }
+}
+
+// Later passes: warps pop spilled (candidate, itemA, itemB) tasks and continue
+// the crossing test from there.  A crossing sets the candidate's flag (the
+// first pass already stored the containment result; a crossing can only add
+// to it).  Pairs already known to intersect are skipped.
+template <int W, bool EXACT>
+__global__ void __launch_bounds__(128, 4) k_refine_tasks(RefineArgs P) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+  WarpMem sm = carve<W>(smem + (size_t)wib * warp_smem_bytes<W>(P.stack_cap), P.stack_cap);
+  Cnt cnt;
+  for (int i = 0; i < C_NUM; ++i) cnt.v[i] = 0;
+  const unsigned int n = min(*P.q_in_n, P.q_cap);
+  for (;;) {
+    unsigned int t = 0;
+    if (lane == 0) t = atomicAdd(P.q_in_pos, 1u);
+    t = __shfl_sync(FULL, t, 0);
+    if (t >= n) break;
+    const uint4 e = P.q_in[t];
+    const uint32_t c = e.x;
+    volatile uint8_t *flag = P.flags + c;
+    int done = lane == 0 ? (int)*flag : 0;
+    if (__shfl_sync(FULL, done, 0)) continue;
+    const int ia = P.cand[2 * (int64_t)c], ib = P.cand[2 * (int64_t)c + 1];
+    F3 off = mkf3(0.f, 0.f, 0.f);
+    if (P.cand_off)
+      off = mkf3((float)P.cand_off[3 * (int64_t)c], (float)P.cand_off[3 * (int64_t)c + 1],
+                 (float)P.cand_off[3 * (int64_t)c + 2]);
+    Spill spill;
+    spill.q = P.q_out;
+    spill.q_n = P.q_out_n;
+    spill.q_cap = P.q_cap;
+    spill.budget = P.q_out ? P.budget : 0;
+    spill.flag = flag;
+    spill.cand = c;
+    int res = pair_cross<W, EXACT>(P.A, P.B, ia, ib, off, sm, lane, P.stack_cap, P.max_pop, cnt,
+                                   nullptr, 0, 1, spill, false, make_uint2(e.y, e.z));
+    if (res == 1) {
+      if (lane == 0) *flag = 1;
+    } else if (res < -2 || res == -1) {
+      if (lane == 0) atomicCAS(P.err, 0, res == -3 ? DERR_QUEUE : DERR_STACK);
+    }
+    if (lane == 0) cnt.v[C_TASKS] += 1;
+  }
   for (int i = 0; i < C_NUM; ++i) {
     unsigned long long v = cnt.v[i];
     for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(FULL, v, o);
@@ -917,6 +1031,12 @@ static RefineKernel pick_kernel(int W, bool exact) {
   return exact ? k_refine<8, true> : k_refine<8, false>;
 }
 
+static RefineKernel pick_task_kernel(int W, bool exact) {
+  if (W == 2) return exact ? k_refine_tasks<2, true> : k_refine_tasks<2, false>;
+  if (W == 4) return exact ? k_refine_tasks<4, true> : k_refine_tasks<4, false>;
+  return exact ? k_refine_tasks<8, true> : k_refine_tasks<8, false>;
+}
+
 static int smem_per_warp(int W, int cap) {
   if (W == 2) return warp_smem_bytes<2>(cap);
   if (W == 4) return warp_smem_bytes<4>(cap);
@@ -966,6 +1086,13 @@ pj_status run_join(Ctx *ctx, Dataset *A, Dataset *B, const int32_t *cand,
     }
   } eg{ev};
   cudaEvent_t e0 = ev[0], e1 = ev[3];
+  // the legacy default stream cannot be captured into a graph: order the
+  // work on the context's stream after everything already queued on it
+  if (o->use_graph && (s == cudaStreamLegacy || s == cudaStreamPerThread)) {
+    PJ_CK(cudaEventRecord(ev[0], s));
+    PJ_CK(cudaStreamWaitEvent(ctx->stream, ev[0], 0));
+    s = ctx->stream;
+  }
   PJ_CK(cudaMemsetAsync(ctx->d_err, 0, sizeof(int) * 4, s));
   PJ_CK(cudaEventRecord(e0, s));
 
@@ -1038,12 +1165,27 @@ pj_status run_join(Ctx *ctx, Dataset *A, Dataset *B, const int32_t *cand,
   if (per_warp * 4 > 200 * 1024) return fail(ctx, PJ_ERR_INTERNAL, "BVH too deep for the traversal stack");
   const int smem = per_warp * (threads / 32);
   RefineKernel kern = pick_kernel(W, exact);
+  RefineKernel kern_tasks = pick_task_kernel(W, exact);
   PJ_CK(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+  PJ_CK(cudaFuncSetAttribute(kern_tasks, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+  // spill queues between the refinement passes
+  const unsigned int q_cap = 1u << 22;
+  uint4 *q1 = (uint4 *)ws_get(ctx, "spill1", sizeof(uint4) * (size_t)q_cap, &st);
+  if (!q1) return st;
+  uint4 *q2 = (uint4 *)ws_get(ctx, "spill2", sizeof(uint4) * (size_t)q_cap, &st);
+  if (!q2) return st;
+  unsigned int *qctr = reinterpret_cast<unsigned int *>(d_misc + 3);  // q1 n/pos, q2 n/pos
+  unsigned int *d_cycles = nullptr;
+  if (o->record_cycles) {
+    d_cycles = (unsigned int *)ws_get(ctx, "cycles", sizeof(unsigned int) * (size_t)std::max<int64_t>(C, 1), &st);
+    if (!d_cycles) return st;
+  }
   RefineArgs args;
   args.A = make_side(A, bA);
   args.B = make_side(B, bB);
   args.cand = d_cand;
   args.cand_off = d_off;
+  args.cycles = d_cycles;
   args.n_cand = d_misc;
   args.flags = d_flags;
   args.work = (unsigned long long *)(d_misc + 2);
@@ -1055,6 +1197,16 @@ pj_status run_join(Ctx *ctx, Dataset *A, Dataset *B, const int32_t *cand,
   args.MA = A->M;
   args.MB = B->M;
   args.single = -1;
+  const bool per_pair = o->launch_mode == PJ_LAUNCH_PER_PAIR;
+  // pass 1 spills a pair after this many traversal steps; pass 2 after more;
+  // pass 3 finishes everything
+  int budget1 = o->spill_budget > 0 ? o->spill_budget : (o->spill_budget < 0 ? 0 : 64);
+  if (per_pair) budget1 = 0;
+  const int budget2 = budget1 > 0 ? 8 * budget1 : 0;
+  args.q_cap = q_cap;
+  args.q_in = nullptr;
+  args.q_in_n = nullptr;
+  args.q_in_pos = nullptr;
   int64_t blocks = 1;
   if (C > 0 && o->launch_mode != PJ_LAUNCH_PER_PAIR) {
     int occ = 0;
@@ -1071,6 +1223,9 @@ pj_status run_join(Ctx *ctx, Dataset *A, Dataset *B, const int32_t *cand,
   auto device_part = [&](bool timed) -> pj_status {
     if (C > 0) {
       if (o->launch_mode == PJ_LAUNCH_PER_PAIR) {
+        args.q_out = nullptr;
+        args.q_out_n = nullptr;
+        args.budget = 0;
         for (int64_t c = 0; c < C; ++c) {
           args.single = c;
           kern<<<1, 32, per_warp, s>>>(args);
@@ -1078,9 +1233,29 @@ pj_status run_join(Ctx *ctx, Dataset *A, Dataset *B, const int32_t *cand,
         args.single = -1;
         ctx->launches += C;
       } else {
-        PJ_CK(cudaMemsetAsync(d_misc + 2, 0, 8, s));
-        kern<<<(int)blocks, threads, smem, s>>>(args);
-        ++ctx->launches;
+        PJ_CK(cudaMemsetAsync(d_misc + 2, 0, 24, s));  // work counter, queue counters
+        RefineArgs a1 = args;
+        a1.q_out = budget1 > 0 ? q1 : nullptr;
+        a1.q_out_n = qctr;
+        a1.budget = budget1;
+        kern<<<(int)blocks, threads, smem, s>>>(a1);
+        RefineArgs a2 = args;
+        a2.q_in = q1;
+        a2.q_in_n = qctr;
+        a2.q_in_pos = qctr + 1;
+        a2.q_out = q2;
+        a2.q_out_n = qctr + 2;
+        a2.budget = budget2;
+        kern_tasks<<<(int)blocks, threads, smem, s>>>(a2);
+        RefineArgs a3 = args;
+        a3.q_in = q2;
+        a3.q_in_n = qctr + 2;
+        a3.q_in_pos = qctr + 3;
+        a3.q_out = nullptr;
+        a3.q_out_n = nullptr;
+        a3.budget = 0;
+        kern_tasks<<<(int)blocks, threads, smem, s>>>(a3);
+        ctx->launches += 3;
       }
       PJ_CK(cudaGetLastError());
     }
@@ -1096,9 +1271,9 @@ pj_status run_join(Ctx *ctx, Dataset *A, Dataset *B, const int32_t *cand,
     return PJ_OK;
   };
   char gk[256];
-  snprintf(gk, sizeof(gk), "%p|%p|%p|%p|%d|%d|%d|%d|%d|%lld", (void *)A, (void *)B,
-           (void *)d_cand, (void *)d_off, W, key.second, (int)exact, k, (int)o->launch_mode,
-           (long long)C);
+  snprintf(gk, sizeof(gk), "%p|%p|%p|%p|%p|%d|%d|%d|%d|%d|%lld|%d|%d", (void *)A, (void *)B,
+           (void *)d_cand, (void *)d_off, (void *)d_cycles, W, key.second, (int)exact, k,
+           (int)o->launch_mode, (long long)C, budget1, args.max_pop);
   bool replayed = false;
   if (graph) {
     auto it = ctx->graphs.find(gk);
@@ -1138,10 +1313,12 @@ pj_status run_join(Ctx *ctx, Dataset *A, Dataset *B, const int32_t *cand,
   PJ_CK(cudaStreamSynchronize(s));
   if (herr[1]) return fail(ctx, PJ_ERR_INVALID_ARG, "a candidate mesh id is out of range");
   if (herr[2]) return fail(ctx, PJ_ERR_INVALID_ARG, "a translated candidate mesh leaves the 2^18 grid");
-  if (herr[0] == DERR_STACK) {
-    // batched pops outgrew the stack: redo every pair in plain depth-first
-    // order, whose stack bound holds by construction
+  if (herr[0] == DERR_STACK || herr[0] == DERR_QUEUE) {
+    // batched pops outgrew the stack, or a spill queue filled up: redo every
+    // pair in plain depth-first order (whose stack bound holds by
+    // construction) and in one pass
     args.max_pop = 1;
+    budget1 = 0;
     PJ_CK(cudaMemsetAsync(ctx->d_err, 0, sizeof(int) * 4, s));
     if ((st = device_part(true)) != PJ_OK) return st;
     PJ_CK(cudaEventRecord(e1, s));
@@ -1181,8 +1358,14 @@ pj_status run_join(Ctx *ctx, Dataset *A, Dataset *B, const int32_t *cand,
     PJ_CK(cudaMalloc((void **)&out->flags, (size_t)std::max<int64_t>(C, 1)));
     if (C > 0) PJ_CK(cudaMemcpyAsync(out->flags, d_flags, C, cudaMemcpyDeviceToDevice, s));
   }
+  if (d_cycles) {
+    PJ_CK(cudaMalloc((void **)&out->cycles, sizeof(unsigned int) * (size_t)std::max<int64_t>(C, 1)));
+    if (C > 0)
+      PJ_CK(cudaMemcpyAsync(out->cycles, d_cycles, sizeof(unsigned int) * C, cudaMemcpyDeviceToDevice, s));
+  }
   PJ_CK(cudaStreamSynchronize(s));
   return PJ_OK;
 }
+
 
 }  // namespace pj

@@ -46,7 +46,8 @@ class pj_join_opts(ctypes.Structure):
     _fields_ = [("width", ctypes.c_int32), ("leaf_size", ctypes.c_int32),
                 ("warps_per_pair", ctypes.c_int32), ("leaf_mode", ctypes.c_int32),
                 ("launch_mode", ctypes.c_int32), ("use_graph", ctypes.c_int32),
-                ("out_host", ctypes.c_int32), ("keep_flags", ctypes.c_int32)]
+                ("out_host", ctypes.c_int32), ("keep_flags", ctypes.c_int32),
+                ("record_cycles", ctypes.c_int32), ("spill_budget", ctypes.c_int32)]
 
 
 class pj_pairs(ctypes.Structure):
@@ -55,15 +56,15 @@ class pj_pairs(ctypes.Structure):
                 ("n_candidates", ctypes.c_int64), ("flags", ctypes.c_void_p),
                 ("device_ms", ctypes.c_float), ("mbb_ms", ctypes.c_float),
                 ("refine_ms", ctypes.c_float), ("compact_ms", ctypes.c_float),
-                ("impl", ctypes.c_void_p)]
+                ("cycles", ctypes.c_void_p), ("impl", ctypes.c_void_p)]
 
 
 class pj_counters(ctypes.Structure):
     _fields_ = [(n, ctypes.c_uint64) for n in (
         "pairs_refined", "node_pairs", "box_tests", "leaf_pairs", "edge_slab_tests",
         "segtri_tests", "exact_fallbacks", "parity_rays", "parity_nodes",
-        "parity_tri_tests", "bytes_fetched", "pairs_hit", "kernel_launches")] + [
-        ("reserved", ctypes.c_uint64 * 3)]
+        "parity_tri_tests", "bytes_fetched", "pairs_hit", "kernel_launches",
+        "tasks_spilled", "tasks_resumed")] + [("reserved", ctypes.c_uint64)]
 
 
 class pj_dataset_info(ctypes.Structure):
@@ -138,12 +139,17 @@ def _is_device(x) -> bool:
     return x is not None and not isinstance(x, np.ndarray) and getattr(x, "is_cuda", False)
 
 
+_CUDA_STREAM_LEGACY = 1  # cudaStreamLegacy: the legacy default stream
+
+
 def _stream_ptr(stream):
+    """cudaStream_t for the C ABI.  None -> NULL (the context's own stream).
+    A torch stream whose handle is 0 is the legacy default stream, which the
+    ABI would read as NULL, so it is passed as cudaStreamLegacy."""
     if stream is None:
         return None
-    if isinstance(stream, int):
-        return stream
-    return int(stream.cuda_stream)
+    h = stream if isinstance(stream, int) else int(stream.cuda_stream)
+    return h if h != 0 else _CUDA_STREAM_LEGACY
 
 
 def _check(ctx, rc):
@@ -214,7 +220,7 @@ def pj_dataset_info_get(ctx, ds: int) -> dict:
 def pj_join_intersects_ex(ctx, a: int, b: int, cand=None, cand_offsets=None, self_join=False,
                           width=0, leaf_size=0, warps_per_pair=0, leaf_mode=PJ_LEAF_FILTERED,
                           launch_mode=PJ_LAUNCH_PERSISTENT, use_graph=False, out_host=True,
-                          keep_flags=False, stream=None):
+                          keep_flags=False, record_cycles=False, spill_budget=0, stream=None):
     """Run the join.  Returns the filled pj_pairs (free it with pj_free_pairs).
 
     cand / cand_offsets: None (device bounding-box filter join), numpy int32
@@ -228,7 +234,8 @@ def pj_join_intersects_ex(ctx, a: int, b: int, cand=None, cand_offsets=None, sel
                 cand_offsets = np.ascontiguousarray(cand_offsets, dtype=np.int32).reshape(-1, 3)
         n = int(cand.shape[0])
     opts = pj_join_opts(width, leaf_size, warps_per_pair, leaf_mode, launch_mode,
-                        int(use_graph), int(out_host), int(keep_flags))
+                        int(use_graph), int(out_host), int(keep_flags), int(record_cycles),
+                        int(spill_budget))
     res = pj_pairs()
     rc = load().pj_join_intersects_ex(ctx, a, b, _ptr(cand), _ptr(cand_offsets), n,
                                       1 if dev else 0, int(self_join), ctypes.byref(opts),
@@ -297,6 +304,26 @@ def pj_export_mesh_data(ctx, ds: int, n_meshes: int, n_tris: int):
 # ---------------------------------------------------------------------------
 # Convenience wrappers
 # ---------------------------------------------------------------------------
+
+class _DeviceView:
+    """A raw device buffer exposed through __cuda_array_interface__."""
+
+    def __init__(self, ptr: int, n: int, typestr: str):
+        self.__cuda_array_interface__ = {"shape": (n,), "typestr": typestr,
+                                         "data": (int(ptr), False), "version": 3}
+
+
+def device_to_numpy(ptr, n: int, dtype) -> np.ndarray:
+    """Copy n elements of a library-owned device buffer to a numpy array."""
+    import torch
+    dt = np.dtype(dtype)
+    if n == 0 or not ptr:
+        return np.zeros(0, dtype=dt)
+    code = {np.dtype(np.uint8): "|u1", np.dtype(np.int32): "<i4", np.dtype(np.uint32): "<i4",
+            np.dtype(np.int64): "<i8"}[dt]
+    t = torch.as_tensor(_DeviceView(ptr, n, code), device="cuda")
+    return t.cpu().numpy().view(dt)
+
 
 def pairs_to_numpy(res: pj_pairs) -> np.ndarray:
     """Copy a host-resident result (out_host=True) into a numpy array."""

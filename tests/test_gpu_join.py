@@ -51,7 +51,8 @@ def test_tiny_spheres_all_bvh_shapes(ctx, tiny, W, L):
         assert np.array_equal(got, exp)
 
 
-@pytest.mark.parametrize("mode", ["exact", "warps2", "warps4", "per_pair", "explicit", "graph"])
+@pytest.mark.parametrize("mode", ["exact", "warps2", "warps4", "per_pair", "explicit", "graph",
+                                  "spill1", "spill3", "nospill"])
 def test_tiny_spheres_modes(ctx, tiny, mode):
     for A, B, ha, hb, exp in tiny:
         kw = {}
@@ -70,6 +71,13 @@ def test_tiny_spheres_modes(ctx, tiny, mode):
                             dtype=np.int32)
         elif mode == "graph":
             kw["use_graph"] = True
+        elif mode == "spill1":
+            kw["spill_budget"] = 1      # every pair continues in the later passes
+            kw["use_graph"] = True
+        elif mode == "spill3":
+            kw["spill_budget"] = 3
+        elif mode == "nospill":
+            kw["spill_budget"] = -1
         got, _ = ctx.join(ha, hb, cand=cand, width=4, leaf_size=4, **kw)
         if mode == "explicit":
             got = got[np.lexsort((got[:, 1], got[:, 0]))]
