@@ -236,6 +236,36 @@ pj_status pj_join_intersects_ex(pj_ctx *ctx, pj_dataset a, pj_dataset b,
 /* Free a join result. */
 pj_status pj_free_pairs(pj_ctx *ctx, pj_pairs *res);
 
+/* The join's device part with no allocation at all (the paper has no
+ * counterpart: this entry point exists for callers that cannot call
+ * cudaMalloc -- code running while a stream is captured into a CUDA graph,
+ * loops that must not stall on the allocator's implicit device
+ * synchronisation, or programs whose device memory belongs to another
+ * allocator or budget).  It calls no cudaMalloc, cudaFree or allocating
+ * library routine; every buffer is the caller's:
+ *   d_cand   device, n_cand x 2 int32 candidates (idA in a, idB in b)
+ *   d_flags  device, n_cand bytes: 1 where the candidate intersects
+ *   d_pairs  device, room for n_cand x 2 int32: the intersecting candidates
+ *            in candidate order
+ *   d_count  device, one int64: the number of pairs, or -1 if a device-side
+ *            check failed (a candidate id out of range)
+ * Uses both datasets' last-built BVH (same width and leaf size), the FP32
+ * filter with int64 fallback, one warp per pair and plain depth-first
+ * traversal.  Asynchronous: the work is enqueued on cuda_stream (NULL: the
+ * context's stream) and the outputs are valid once it has completed.
+ * n_cand above 16,777,216 is rejected with PJ_ERR_INVALID_ARG.
+ * Scratch: a 65,600-byte array in device global memory, defined at file
+ * scope in the library; every GPU that loads the library holds it until the
+ * process exits.  The first call on a device looks up the array's device
+ * address (make that first call before any stream capture).  All calls on a
+ * device share the array, which keeps the last call's contents (each call
+ * clears the parts that must start at zero): calls whose work overlaps on
+ * the GPU race, so order them on one stream or synchronise between them. */
+pj_status pj_join_intersects_noalloc(pj_ctx *ctx, pj_dataset a, pj_dataset b,
+                                     const int32_t *d_cand, int64_t n_cand,
+                                     uint8_t *d_flags, int32_t *d_pairs,
+                                     int64_t *d_count, void *cuda_stream);
+
 /* --------------------------------------------------------------------------
  * Counters and diagnostics
  * ------------------------------------------------------------------------ */

@@ -542,6 +542,20 @@ pj_status pj_join_intersects_ex(pj_ctx *h, pj_dataset a, pj_dataset b,
                   &o, stream ? (cudaStream_t)stream : ctx->stream, out);
 }
 
+pj_status pj_join_intersects_noalloc(pj_ctx *h, pj_dataset a, pj_dataset b,
+                                     const int32_t *d_cand, int64_t n_cand, uint8_t *d_flags,
+                                     int32_t *d_pairs, int64_t *d_count, void *stream) {
+  Ctx *ctx = reinterpret_cast<Ctx *>(h);
+  if (!ctx) return PJ_ERR_INVALID_ARG;
+  std::lock_guard<std::mutex> lk(ctx->mu);
+  ctx->err.clear();
+  Dataset *A = get_ds(ctx, a), *B = get_ds(ctx, b);
+  if (!A || !B) return fail(ctx, PJ_ERR_INVALID_ARG, "unknown dataset");
+  cudaSetDevice(ctx->device);
+  return run_join_noalloc(ctx, A, B, d_cand, n_cand, d_flags, d_pairs, d_count,
+                          stream ? (cudaStream_t)stream : ctx->stream);
+}
+
 pj_status pj_free_pairs(pj_ctx *h, pj_pairs *res) {
   Ctx *ctx = reinterpret_cast<Ctx *>(h);
   if (!ctx || !res) return PJ_ERR_INVALID_ARG;

@@ -118,6 +118,9 @@ pj_status run_join(Ctx *ctx, Dataset *A, Dataset *B, const int32_t *cand,
                    const int32_t *cand_off, int64_t n_cand, int cand_on_device,
                    int self_join, const pj_join_opts *opts, cudaStream_t s,
                    pj_pairs *out);
+pj_status run_join_noalloc(Ctx *ctx, Dataset *A, Dataset *B, const int32_t *d_cand,
+                           int64_t n, uint8_t *d_flags, int32_t *d_pairs, int64_t *d_count,
+                           cudaStream_t s);
 pj_status run_segtri_batch(Ctx *ctx, const float *pq, const float *abc,
                            int64_t n, int mode, uint8_t *res,
                            int64_t *n_fallback, cudaStream_t s);

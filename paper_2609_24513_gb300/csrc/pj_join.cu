@@ -16,6 +16,7 @@
 //   - Result materialisation (Sec. 3.5) is one flag per candidate followed
 //     by a prefix-sum compaction, so nothing needs deduplication.
 #include <algorithm>
+#include <mutex>
 #include <cstdio>
 #include <cstring>
 #include <string>
@@ -1367,5 +1368,144 @@ pj_status run_join(Ctx *ctx, Dataset *A, Dataset *B, const int32_t *cand,
   return PJ_OK;
 }
 
+
+// ---------------------------------------------------------------------------
+// Join without allocation (pj_join_intersects_noalloc)
+//
+// For callers that cannot call cudaMalloc: code that runs while a stream is
+// being captured into a CUDA graph, real-time loops that must not block on
+// the allocator's implicit device synchronisation, and hosts whose device
+// memory is owned by another allocator or budget.  The caller passes device
+// buffers for the candidates, the per-candidate flags, the pairs and the
+// count; the little scratch the kernels need (candidate count, work counter,
+// error words, per-chunk counts and offsets of the compaction) lives in one
+// file-scope device array shared by every call on a device.
+// ---------------------------------------------------------------------------
+constexpr int64_t kNoAllocMaxChunks = 4096;
+constexpr int64_t kNoAllocMaxCand = kNoAllocMaxChunks * CMP_CHUNK;  // 16,777,216
+// int64 words: [0] candidate count, [1] work counter, [2..3] four int error
+// words, [4..7] unused, then kNoAllocMaxChunks chunk counts and as many offsets
+constexpr size_t kNoAllocScratchWords = 8 + 2 * kNoAllocMaxChunks;
+static __device__ __align__(256) int64_t g_noalloc_scratch[kNoAllocScratchWords];
+
+static std::mutex g_noalloc_mu;
+static void *g_noalloc_addr[256];  // device address of the array, per device
+
+// Device address of the scratch array on the current device (looked up once
+// per device; the host-side name is not a device address).
+static pj_status noalloc_scratch(Ctx *ctx, int64_t **out) {
+  std::lock_guard<std::mutex> lk(g_noalloc_mu);
+  if (ctx->device < 0 || ctx->device >= 256)
+    return fail(ctx, PJ_ERR_INVALID_ARG, "device ordinal out of range");
+  if (!g_noalloc_addr[ctx->device]) {
+    void *p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess || !p) return cuda_fail(ctx, e, "cudaGetSymbolAddress(g_noalloc_scratch)");
+    g_noalloc_addr[ctx->device] = p;
+  }
+  *out = static_cast<int64_t *>(g_noalloc_addr[ctx->device]);
+  return PJ_OK;
+}
+
+__global__ void k_noalloc_begin(int64_t *scr, int64_t n) {
+  scr[0] = n;  // candidate count
+  scr[1] = 0;  // work counter
+  scr[2] = 0;  // error words
+  scr[3] = 0;
+}
+
+// one block of SCAN_T threads: exclusive scan of the chunk counts, then the
+// pair count (-1 if a device-side check failed)
+__global__ void k_noalloc_scan(const int64_t *counts, int64_t *offs, int64_t nchunks,
+                               const int *err, int64_t *out_count) {
+  __shared__ int64_t carry;
+  if (threadIdx.x == 0) carry = 0;
+  __syncthreads();
+  for (int64_t base = 0; base < nchunks; base += SCAN_T) {
+    int64_t i = base + threadIdx.x;
+    int64_t v = i < nchunks ? counts[i] : 0;
+    int64_t tot;
+    int64_t e = block_excl_scan(v, &tot);
+    if (i < nchunks) offs[i] = carry + e;
+    __syncthreads();
+    if (threadIdx.x == 0) carry += tot;
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) *out_count = (err[0] || err[1] || err[2]) ? -1 : carry;
+}
+
+pj_status run_join_noalloc(Ctx *ctx, Dataset *A, Dataset *B, const int32_t *d_cand,
+                           int64_t n, uint8_t *d_flags, int32_t *d_pairs, int64_t *d_count,
+                           cudaStream_t s) {
+  if (n < 0 || n > kNoAllocMaxCand)
+    return fail(ctx, PJ_ERR_INVALID_ARG,
+                "n_cand must be in [0, 16777216] for the allocation-free join");
+  if (!d_count || (n > 0 && (!d_cand || !d_flags || !d_pairs)))
+    return fail(ctx, PJ_ERR_INVALID_ARG, "null device buffer");
+  auto ia = A->bvhs.find(A->last_bvh), ib = B->bvhs.find(A->last_bvh);
+  if (ia == A->bvhs.end() || ib == B->bvhs.end())
+    return fail(ctx, PJ_ERR_INVALID_ARG, "both datasets need a BVH of the same shape (pj_build_bvh)");
+  Bvh &bA = ia->second, &bB = ib->second;
+  const int W = A->last_bvh.first;
+  int64_t *scr = nullptr;
+  pj_status st = noalloc_scratch(ctx, &scr);
+  if (st != PJ_OK) return st;
+  int64_t *d_n = scr;
+  unsigned long long *work = reinterpret_cast<unsigned long long *>(scr + 1);
+  int *err = reinterpret_cast<int *>(scr + 2);
+  int64_t *counts = scr + 8, *offs = scr + 8 + kNoAllocMaxChunks;
+
+  // plain depth-first traversal: its stack bound holds by construction, so
+  // there is no overflow to recover from
+  const int depth = std::max(bA.max_depth, 1) + std::max(bB.max_depth, 1);
+  const int stack_cap = 1 + (W * W - 1) * depth + 256;
+  const int per_warp = smem_per_warp(W, stack_cap);
+  const int threads = 128;
+  if (per_warp * 4 > 200 * 1024) return fail(ctx, PJ_ERR_INTERNAL, "BVH too deep for the traversal stack");
+  const int smem = per_warp * (threads / 32);
+  RefineKernel kern = pick_kernel(W, false);
+  PJ_CK(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+  int occ = 0;
+  PJ_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, threads, smem));
+  if (occ < 1) return fail(ctx, PJ_ERR_INTERNAL, "refinement kernel does not fit on an SM");
+  RefineArgs args;
+  args.A = make_side(A, bA);
+  args.B = make_side(B, bB);
+  args.cand = d_cand;
+  args.cand_off = nullptr;
+  args.cycles = nullptr;
+  args.q_out = nullptr;
+  args.q_out_n = nullptr;
+  args.q_cap = 0;
+  args.budget = 0;
+  args.q_in = nullptr;
+  args.q_in_n = nullptr;
+  args.q_in_pos = nullptr;
+  args.n_cand = d_n;
+  args.flags = d_flags;
+  args.work = work;
+  args.counters = ctx->d_counters;
+  args.err = err;
+  args.stack_cap = stack_cap;
+  args.max_pop = 1;
+  args.warps_per_pair = 1;
+  args.MA = A->M;
+  args.MB = B->M;
+  args.single = -1;
+
+  k_noalloc_begin<<<1, 1, 0, s>>>(scr, n);
+  if (n > 0) {
+    k_check_cand<<<std::min(blocks_for(n, 256), ctx->num_sms * 8), 256, 0, s>>>(
+        d_cand, nullptr, n, A->M, B->M, B->d_aabb, err);
+    int64_t blocks = std::min<int64_t>((int64_t)occ * ctx->num_sms, (n * 32 + threads - 1) / threads);
+    kern<<<(int)std::max<int64_t>(blocks, 1), threads, smem, s>>>(args);
+  }
+  const int nchunks = (int)std::max<int64_t>(1, (n + CMP_CHUNK - 1) / CMP_CHUNK);
+  k_flag_count<<<nchunks, CMP_T, 0, s>>>(d_flags, d_n, counts);
+  k_noalloc_scan<<<1, SCAN_T, 0, s>>>(counts, offs, nchunks, err, d_count);
+  k_flag_emit<<<nchunks, CMP_T, 0, s>>>(d_flags, d_n, d_cand, offs, d_pairs);
+  PJ_CK(cudaGetLastError());
+  return PJ_OK;
+}
 
 }  // namespace pj

@@ -95,6 +95,7 @@ SIGNATURES = {
                                      ctypes.POINTER(pj_join_opts), _vp,
                                      ctypes.POINTER(pj_pairs)]),
     "pj_free_pairs": (_i32, [_vp, ctypes.POINTER(pj_pairs)]),
+    "pj_join_intersects_noalloc": (_i32, [_vp, _i32, _i32, _vp, _i64, _vp, _vp, _vp, _vp]),
     "pj_get_counters": (_i32, [_vp, ctypes.POINTER(pj_counters)]),
     "pj_reset_counters": (_i32, [_vp]),
     "pj_segtri_batch": (_i32, [_vp, _vp, _vp, _i64, _i32, _vp, ctypes.POINTER(_i64), _vp]),
@@ -255,6 +256,17 @@ def pj_join_intersects(ctx, a: int, b: int, cand=None, self_join=False, stream=N
                                    _stream_ptr(stream), ctypes.byref(res))
     _check(ctx, rc)
     return res
+
+
+def pj_join_intersects_noalloc(ctx, a: int, b: int, d_cand, d_flags, d_pairs, d_count,
+                               stream=None):
+    """Allocation-free join on caller-owned torch CUDA tensors: d_cand (n x 2
+    int32), d_flags (n uint8), d_pairs (n x 2 int32), d_count (1 int64).
+    Enqueues the work and returns; synchronise the stream before reading."""
+    n = int(d_cand.shape[0]) if d_cand is not None else 0
+    _check(ctx, load().pj_join_intersects_noalloc(ctx, a, b, _ptr(d_cand), n, _ptr(d_flags),
+                                                  _ptr(d_pairs), _ptr(d_count),
+                                                  _stream_ptr(stream)))
 
 
 def pj_free_pairs(ctx, res: pj_pairs):
