@@ -91,9 +91,10 @@ typedef struct {
   int32_t keep_flags;       /* 1: also return the per-candidate result bytes  */
   int32_t record_cycles;    /* 1: also return each candidate's SM clock cycles
                                (instrumentation of per-pair cost)            */
-  int32_t spill_budget;     /* traversal steps a warp spends on one pair in the
+  int32_t spill_budget;     /* SM clock cycles a warp spends on one pair in the
                                first pass before handing the rest of it to
-                               later passes (0: 64; < 0: never)             */
+                               later passes (0: 40,000; < 0: never); the
+                               second pass allows 8 times as many            */
 } pj_join_opts;
 
 /* Result of a join.  Owned by the library until pj_free_pairs. */

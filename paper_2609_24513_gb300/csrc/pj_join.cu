@@ -228,7 +228,7 @@ struct RefineArgs {
   uint4 *q_out;
   unsigned int *q_out_n;
   unsigned int q_cap;
-  int budget;
+  long long budget;          // SM cycles a warp spends on a pair or task before spilling
   const uint4 *q_in;
   const unsigned int *q_in_n;
   unsigned int *q_in_pos;
@@ -245,7 +245,7 @@ struct Spill {
   uint4 *q;                  // queue to append to (null: never spill)
   unsigned int *q_n;         // its fill counter
   unsigned int q_cap;
-  int budget;                // traversal steps before spilling (0: unbounded)
+  long long budget;          // SM cycles before spilling (0: unbounded)
   const volatile uint8_t *flag;  // this pair's result, polled for early exit
   uint32_t cand;
 };
@@ -488,6 +488,7 @@ __device__ int pair_cross(const Side &A, const Side &B, int ia, int ib, F3 off,
   __syncwarp();
   bool split_done = nrank <= 1;
   unsigned iters = 0;
+  const long long t_begin = clock64();
   while (sp > 0 || nlq > 0) {
     if (++iters > (1u << 26)) return -1;  // defensive bound: a tree walk is finite
     if (group_hit) {
@@ -499,7 +500,7 @@ __device__ int pair_cross(const Side &A, const Side &B, int ia, int ib, F3 off,
       int f = lane == 0 ? (int)*spill.flag : 0;
       if (__shfl_sync(FULL, f, 0)) return 1;
     }
-    if (spill.budget > 0 && iters > (unsigned)spill.budget && sp > 0) {
+    if (spill.budget > 0 && sp > 0 && clock64() - t_begin > spill.budget) {
       // over budget: finish the queued leaf pairs, then hand the remaining
       // tasks to the next pass, where other warps take them
       if (nlq > 0) {
@@ -855,7 +856,6 @@ __global__ void __launch_bounds__(128, 4) k_refine(RefineArgs P) {
       }
       P.flags[c] = (uint8_t)res;
       cnt.v[C_PAIRS] += 1;
-      cnt.v[C_HITS] += res;
       cnt.v[C_BYTES] += 8 + 1 + 48;
     }
   }
@@ -922,7 +922,8 @@ __global__ void __launch_bounds__(128, 4) k_refine_tasks(RefineArgs P) {
 // ---------------------------------------------------------------------------
 constexpr int CMP_T = 256, CMP_PER = 16, CMP_CHUNK = CMP_T * CMP_PER;
 
-__global__ void k_flag_count(const uint8_t *flags, const int64_t *n_dev, int64_t *bcount) {
+__global__ void k_flag_count(const uint8_t *flags, const int64_t *n_dev, int64_t *bcount,
+                             unsigned long long *hits) {
   const int64_t n = *n_dev;
   int64_t base = blockIdx.x * (int64_t)CMP_CHUNK;
   int c = 0;
@@ -938,6 +939,7 @@ __global__ void k_flag_count(const uint8_t *flags, const int64_t *n_dev, int64_t
     int s = 0;
     for (int w = 0; w < CMP_T / 32; ++w) s += ws[w];
     bcount[blockIdx.x] = s;
+    if (hits && s) atomicAdd(hits, (unsigned long long)s);
   }
 }
 
@@ -1201,9 +1203,9 @@ pj_status run_join(Ctx *ctx, Dataset *A, Dataset *B, const int32_t *cand,
   const bool per_pair = o->launch_mode == PJ_LAUNCH_PER_PAIR;
   // pass 1 spills a pair after this many traversal steps; pass 2 after more;
   // pass 3 finishes everything
-  int budget1 = o->spill_budget > 0 ? o->spill_budget : (o->spill_budget < 0 ? 0 : 64);
+  long long budget1 = o->spill_budget > 0 ? o->spill_budget : (o->spill_budget < 0 ? 0 : 40000);
   if (per_pair) budget1 = 0;
-  const int budget2 = budget1 > 0 ? 8 * budget1 : 0;
+  const long long budget2 = budget1 > 0 ? 8 * budget1 : 0;
   args.q_cap = q_cap;
   args.q_in = nullptr;
   args.q_in_n = nullptr;
@@ -1262,7 +1264,7 @@ pj_status run_join(Ctx *ctx, Dataset *A, Dataset *B, const int32_t *cand,
     }
     if (timed) PJ_CK(cudaEventRecord(ev[2], s));
     // 3. compaction
-    k_flag_count<<<nchunks, CMP_T, 0, s>>>(d_flags, d_misc, bcount);
+    k_flag_count<<<nchunks, CMP_T, 0, s>>>(d_flags, d_misc, bcount, ctx->d_counters + C_HITS);
     ++ctx->launches;
     pj_status st2 = scan_i64(ctx, bcount, boff, nchunks, d_misc + 1, s);
     if (st2 != PJ_OK) return st2;
@@ -1274,7 +1276,7 @@ pj_status run_join(Ctx *ctx, Dataset *A, Dataset *B, const int32_t *cand,
   char gk[256];
   snprintf(gk, sizeof(gk), "%p|%p|%p|%p|%p|%d|%d|%d|%d|%d|%lld|%d|%d", (void *)A, (void *)B,
            (void *)d_cand, (void *)d_off, (void *)d_cycles, W, key.second, (int)exact, k,
-           (int)o->launch_mode, (long long)C, budget1, args.max_pop);
+           (int)o->launch_mode, (long long)C, (int)budget1, args.max_pop);
   bool replayed = false;
   if (graph) {
     auto it = ctx->graphs.find(gk);
@@ -1501,7 +1503,7 @@ pj_status run_join_noalloc(Ctx *ctx, Dataset *A, Dataset *B, const int32_t *d_ca
     kern<<<(int)std::max<int64_t>(blocks, 1), threads, smem, s>>>(args);
   }
   const int nchunks = (int)std::max<int64_t>(1, (n + CMP_CHUNK - 1) / CMP_CHUNK);
-  k_flag_count<<<nchunks, CMP_T, 0, s>>>(d_flags, d_n, counts);
+  k_flag_count<<<nchunks, CMP_T, 0, s>>>(d_flags, d_n, counts, ctx->d_counters + C_HITS);
   k_noalloc_scan<<<1, SCAN_T, 0, s>>>(counts, offs, nchunks, err, d_count);
   k_flag_emit<<<nchunks, CMP_T, 0, s>>>(d_flags, d_n, d_cand, offs, d_pairs);
   PJ_CK(cudaGetLastError());
