@@ -95,6 +95,10 @@ typedef struct {
                                first pass before handing the rest of it to
                                later passes (0: 40,000; < 0: never); the
                                second pass allows 8 times as many            */
+  int32_t wave_levels;      /* BVH levels descended breadth-first, one thread
+                               per child test, before the per-warp passes
+                               (0: 8; < 0: none)                             */
+  int32_t reserved;
 } pj_join_opts;
 
 /* Result of a join.  Owned by the library until pj_free_pairs. */

@@ -247,6 +247,35 @@ __device__ __forceinline__ bool ray_up_hit(I3 v, I3 a, I3 b, I3 c) {
   return o != 0 && sgn64(o) == -s;  // v strictly below the plane
 }
 
+// Parity ray from v along axis `ax` (0, 1, 2) in direction `dir` (+1 / -1).
+// With (u, w, ax) a cyclic triple, v is perturbed to v + e u_hat + e^2 w_hat;
+// the projected area orient2d_(u,w)(a,b,c) is the ax-component of the normal,
+// and the plane point v + h e_ax has h = -orient3d(a,b,c,v) / n_ax, which must
+// have the sign of dir.  For ax = 2, dir = +1 this is ray_up_hit.
+//
+// For a closed mod-2 cycle (every edge in exactly two triangles) and v off
+// the surface, the parity of the hits is the mod-2 winding number of the
+// surface around v, whichever axis and direction the ray takes: the perturbed
+// origins all lie in v's component of the complement, and each perturbed ray
+// crosses the surface only transversally through triangle interiors.
+__device__ __forceinline__ int cget(I3 v, int k) { return k == 0 ? v.x : (k == 1 ? v.y : v.z); }
+
+__device__ __forceinline__ bool ray_axis_hit(I3 v, I3 a, I3 b, I3 c, int ax, int dir) {
+  const int u = ax == 2 ? 0 : ax + 1, w = ax == 0 ? 2 : ax - 1;
+  I3 a2, b2, c2, v2;  // (u, w) coordinates in x, y
+  a2.x = cget(a, u); a2.y = cget(a, w); a2.z = 0;
+  b2.x = cget(b, u); b2.y = cget(b, w); b2.z = 0;
+  c2.x = cget(c, u); c2.y = cget(c, w); c2.z = 0;
+  v2.x = cget(v, u); v2.y = cget(v, w); v2.z = 0;
+  long long s2 = o2xy(a2, b2, c2);
+  if (s2 == 0) return false;
+  int s = s2 > 0 ? 1 : -1;
+  if (side_eps(a2, b2, v2) != s || side_eps(b2, c2, v2) != s || side_eps(c2, a2, v2) != s)
+    return false;
+  long long o = orient64(a, b, c, v);
+  return o != 0 && sgn64(o) == -dir * s;
+}
+
 // 2-D closed point-in-triangle in the projection dropping axis `drop`
 __device__ __forceinline__ bool in_tri_2d(I3 v, I3 a, I3 b, I3 c, int drop) {
   int ax, ay, bx, by, cx, cy, vx, vy;

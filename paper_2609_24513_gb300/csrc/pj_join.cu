@@ -135,41 +135,38 @@ pj_status scan_i64(Ctx *ctx, const int64_t *d_in, int64_t *d_out, int64_t n,
 // ---------------------------------------------------------------------------
 constexpr int MBB_T = 256;
 
+// One warp per A mesh; lanes sweep the B boxes 32 at a time.  The count pass
+// and the emit pass make the same tests, and the emit pass writes each warp's
+// hits in j order (ballot prefix), so candidates come out sorted by (i, j).
 template <bool EMIT>
-__global__ void k_mbb(const float *aabbA, int64_t MA, const float *aabbB, int64_t MB,
-                      int self_join, int64_t *counts, const int64_t *offsets,
-                      int32_t *cand) {
-  __shared__ float sb[6][MBB_T];
-  int64_t i = blockIdx.x * (int64_t)MBB_T + threadIdx.x;
-  float a[6];
-  bool live = i < MA;
-  for (int d = 0; d < 6; ++d) a[d] = live ? aabbA[6 * i + d] : 0.f;
-  int64_t cnt = 0, pos = (EMIT && live) ? offsets[i] : 0;
-  int64_t j0 = self_join ? blockIdx.x * (int64_t)MBB_T : 0;  // tiles below are all j < i
-  for (int64_t t0 = j0; t0 < MB; t0 += MBB_T) {
-    __syncthreads();
-    int64_t j = t0 + threadIdx.x;
-    for (int d = 0; d < 6; ++d) sb[d][threadIdx.x] = j < MB ? aabbB[6 * j + d] : 0.f;
-    __syncthreads();
-    if (!live) continue;
-    int lim = (int)std::min<int64_t>(MBB_T, MB - t0);
-    for (int k = 0; k < lim; ++k) {
-      int64_t jj = t0 + k;
-      if (self_join && jj <= i) continue;
-      bool ov = a[0] <= sb[3][k] && sb[0][k] <= a[3] && a[1] <= sb[4][k] &&
-                sb[1][k] <= a[4] && a[2] <= sb[5][k] && sb[2][k] <= a[5];
-      if (ov) {
-        if (EMIT) {
-          cand[2 * pos] = (int32_t)i;
-          cand[2 * pos + 1] = (int32_t)jj;
-          ++pos;
-        } else {
-          ++cnt;
-        }
+__global__ void __launch_bounds__(MBB_T) k_mbb(const float *aabbA, int64_t MA,
+                                              const float *aabbB, int64_t MB, int self_join,
+                                              int64_t *counts, const int64_t *offsets,
+                                              int32_t *cand) {
+  const int lane = threadIdx.x & 31;
+  const int64_t warps = (int64_t)gridDim.x * (MBB_T / 32);
+  for (int64_t i = blockIdx.x * (int64_t)(MBB_T / 32) + (threadIdx.x >> 5); i < MA; i += warps) {
+    const float *a = aabbA + 6 * i;
+    const float ax0 = a[0], ay0 = a[1], az0 = a[2], ax1 = a[3], ay1 = a[4], az1 = a[5];
+    int64_t cnt = 0, pos = EMIT ? offsets[i] : 0;
+    for (int64_t j0 = self_join ? ((i + 1) & ~31ll) : 0; j0 < MB; j0 += 32) {
+      const int64_t j = j0 + lane;
+      bool ov = false;
+      if (j < MB && (!self_join || j > i)) {
+        const float *b = aabbB + 6 * j;
+        ov = ax0 <= b[3] && b[0] <= ax1 && ay0 <= b[4] && b[1] <= ay1 && az0 <= b[5] && b[2] <= az1;
       }
+      const unsigned m = __ballot_sync(0xffffffffu, ov);
+      if (EMIT && ov) {
+        const int64_t p = pos + __popc(m & ((1u << lane) - 1u));
+        cand[2 * p] = (int32_t)i;
+        cand[2 * p + 1] = (int32_t)j;
+      }
+      if (EMIT) pos += __popc(m);
+      else cnt += __popc(m);
     }
+    if (!EMIT && lane == 0) counts[i] = cnt;
   }
-  if (!EMIT && live) counts[i] = cnt;
 }
 
 // ---------------------------------------------------------------------------
@@ -232,6 +229,7 @@ struct RefineArgs {
   const uint4 *q_in;
   const unsigned int *q_in_n;
   unsigned int *q_in_pos;
+  unsigned int q_in_cap;
 };
 
 struct Cnt {
@@ -318,6 +316,35 @@ __device__ __forceinline__ bool overlap(const Box &a, const Box &b) {
 
 __device__ __forceinline__ float extent(const Box &b) {
   return fmaxf(fmaxf(b.hi.x - b.lo.x, b.hi.y - b.lo.y), b.hi.z - b.lo.z);
+}
+
+// The parity ray leaves along the axis and direction with the shortest way out
+// of the target's box (see ray_axis_hit: the parity does not depend on it).
+__device__ __forceinline__ void ray_axis_choice(F3 v, F3 lo, F3 hi, int &ax, int &dir) {
+  float best = hi.z - v.z;
+  ax = 2;
+  dir = 1;
+  const float d[6] = {hi.x - v.x, v.x - lo.x, hi.y - v.y, v.y - lo.y, hi.z - v.z, v.z - lo.z};
+  for (int k = 0; k < 6; ++k)
+    if (d[k] < best) {
+      best = d[k];
+      ax = k >> 1;
+      dir = (k & 1) ? -1 : 1;
+    }
+}
+
+// does the ray (ax, dir) from v meet the closed box?
+__device__ __forceinline__ bool ray_axis_box(F3 v, const Box &b, int ax, int dir) {
+  const float vu = ax == 0 ? v.y : (ax == 1 ? v.z : v.x);
+  const float vw = ax == 0 ? v.z : (ax == 1 ? v.x : v.y);
+  const float lu = ax == 0 ? b.lo.y : (ax == 1 ? b.lo.z : b.lo.x);
+  const float hu = ax == 0 ? b.hi.y : (ax == 1 ? b.hi.z : b.hi.x);
+  const float lw = ax == 0 ? b.lo.z : (ax == 1 ? b.lo.x : b.lo.y);
+  const float hw = ax == 0 ? b.hi.z : (ax == 1 ? b.hi.x : b.hi.y);
+  const float va = ax == 0 ? v.x : (ax == 1 ? v.y : v.z);
+  const float la = ax == 0 ? b.lo.x : (ax == 1 ? b.lo.y : b.lo.z);
+  const float ha = ax == 0 ? b.hi.x : (ax == 1 ? b.hi.y : b.hi.z);
+  return lu <= vu && vu <= hu && lw <= vw && vw <= hw && (dir > 0 ? va <= ha : la <= va);
 }
 
 // Build a task from two items (flags stripped) and their boxes: a leaf never
@@ -646,7 +673,7 @@ __device__ int pair_cross(const Side &A, const Side &B, int ia, int ib, F3 off,
 // (translated by toff).  Returns bit 0 = parity, bit 1 = v on the surface,
 // or -1 on a capacity error.
 template <int W>
-__device__ int parity_query(const Side &T, int it, F3 toff, F3 vf, WarpMem &sm,
+__device__ int parity_query(const Side &T, int it, F3 toff, F3 vf, int ax, int dir, WarpMem &sm,
                             int lane, int stack_cap, int max_pop, Cnt &cnt) {
   constexpr int LQ = Cfg<W>::LQ;
   const int64_t tbase = T.toff[it];
@@ -674,8 +701,7 @@ __device__ int parity_query(const Side &T, int it, F3 toff, F3 vf, WarpMem &sm,
       if (ok) {
         Box b;
         load_slot<W>(T.nodes, node, c, toff, b, ch);
-        ok = ch != kEmpty && b.lo.x <= vf.x && vf.x <= b.hi.x && b.lo.y <= vf.y &&
-             vf.y <= b.hi.y && vf.z <= b.hi.z;
+        ok = ch != kEmpty && ray_axis_box(vf, b, ax, dir);
       }
       const bool leaf = ok && (ch & kLeafBit);
       const bool inner = ok && !leaf;
@@ -717,7 +743,7 @@ __device__ int parity_query(const Side &T, int it, F3 toff, F3 vf, WarpMem &sm,
           load_tri(T.trirec, s, toff, a, b, c, own);
           I3 ai = toi(a), bi = toi(b), ci = toi(c);
           on = on || on_triangle(v, ai, bi, ci);
-          par ^= ray_up_hit(v, ai, bi, ci) ? 1 : 0;
+          par ^= ray_axis_hit(v, ai, bi, ci, ax, dir) ? 1 : 0;
           cnt.v[C_PARITY_TRIS] += 1;
           cnt.v[C_BYTES] += 48;
         }
@@ -747,7 +773,9 @@ __device__ int pair_inside(const Side &Q, int iq, F3 qoff, const Side &T, int it
     if (lane == 0) cnt.v[C_BYTES] += 16;
     if (v.x < lo.x || v.x > hi.x || v.y < lo.y || v.y > hi.y || v.z < lo.z || v.z > hi.z)
       return 0;
-    int r = parity_query<W>(T, it, toff, v, sm, lane, stack_cap, max_pop, cnt);
+    int ax, dir;
+    ray_axis_choice(v, lo, hi, ax, dir);
+    int r = parity_query<W>(T, it, toff, v, ax, dir, sm, lane, stack_cap, max_pop, cnt);
     if (r < 0) return -1;
     if (!(r & 2)) return r & 1;
   }
@@ -867,6 +895,392 @@ __global__ void __launch_bounds__(128, 4) k_refine(RefineArgs P) {
   }
 }
 
+// ---------------------------------------------------------------------------
+// Wavefront front end.  Most candidate pairs are decided in the top few
+// levels of the two BVHs (boxes stop overlapping, or the parity ray finds
+// little); handing each of them a whole warp leaves most lanes idle on memory
+// latency.  The front end therefore runs the first levels breadth-first with
+// one thread per child test, the parity rays with one thread per (pair,
+// direction) and the leaf-pair tests with one thread per source triangle;
+// whatever is left after those levels goes to the warp-DFS passes as queued
+// (candidate, itemA, itemB) tasks.
+// ---------------------------------------------------------------------------
+struct WaveArgs {
+  Side A, B;
+  const int32_t *cand;
+  const int32_t *cand_off;
+  const int64_t *n_cand;
+  uint8_t *flags;
+  unsigned long long *counters;
+  int *err;
+  unsigned int q_cap;
+  int64_t MA, MB;
+};
+
+__device__ __forceinline__ F3 cand_offset(const WaveArgs &P, int64_t c) {
+  if (!P.cand_off) return mkf3(0.f, 0.f, 0.f);
+  return mkf3((float)P.cand_off[3 * c], (float)P.cand_off[3 * c + 1], (float)P.cand_off[3 * c + 2]);
+}
+
+// warp-aggregated append of `cnt` entries; returns this lane's first index
+__device__ __forceinline__ unsigned warp_append(unsigned *ctr, unsigned cnt, int lane) {
+  unsigned incl = cnt;
+  for (int o = 1; o < 32; o <<= 1) {
+    unsigned t = __shfl_up_sync(FULL, incl, o);
+    if (lane >= o) incl += t;
+  }
+  unsigned total = __shfl_sync(FULL, incl, 31);
+  unsigned base = 0;
+  if (lane == 31 && total) base = atomicAdd(ctr, total);
+  base = __shfl_sync(FULL, base, 31);
+  return base + incl - cnt;
+}
+
+__device__ __forceinline__ void flush_counters(unsigned long long *dst, const unsigned long long *v,
+                                               int lane, int n) {
+  for (int i = 0; i < n; ++i) {
+    unsigned long long x = v[i];
+    for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(FULL, x, o);
+    if (lane == 0 && x) atomicAdd(dst + i, x);
+  }
+}
+
+// root task of every candidate whose mesh boxes meet
+__global__ void k_wave_init(WaveArgs P, uint4 *q, unsigned *q_n) {
+  const int lane = threadIdx.x & 31;
+  const int64_t n = *P.n_cand;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g - lane < n; g += stride) {
+    bool push = false;
+    uint2 t = make_uint2(0u, 0u);
+    if (g < n) {
+      const int ia = P.cand[2 * g], ib = P.cand[2 * g + 1];
+      if (ia >= 0 && ia < P.MA && ib >= 0 && ib < P.MB) {
+        const F3 off = cand_offset(P, g);
+        Box ba, bb;
+        ba.lo = ld3(P.A.aabb + 6 * (int64_t)ia);
+        ba.hi = ld3(P.A.aabb + 6 * (int64_t)ia + 3);
+        bb.lo = add(ld3(P.B.aabb + 6 * (int64_t)ib), off);
+        bb.hi = add(ld3(P.B.aabb + 6 * (int64_t)ib + 3), off);
+        if (overlap(ba, bb)) {
+          t = make_task((uint32_t)P.A.roots[ia], ba, (uint32_t)P.B.roots[ib], bb);
+          push = true;
+        }
+      }
+    }
+    unsigned pos = warp_append(q_n, push ? 1u : 0u, lane);
+    if (push && pos < P.q_cap) q[pos] = make_uint4((uint32_t)g, t.x, t.y, 0u);
+    if (push && pos >= P.q_cap) atomicCAS(P.err, 0, DERR_QUEUE);
+    if (lane == 0) {
+      const int64_t m = n - (g - lane);
+      atomicAdd(P.counters + C_PAIRS, (unsigned long long)(m < 32 ? m : 32));
+    }
+  }
+}
+
+// box of an item (an internal node's own box, or a leaf's slot box)
+template <int W>
+__device__ __forceinline__ void item_box(const float *nodes, uint32_t item, F3 off, Box &b) {
+  uint32_t dummy;
+  const uint32_t idx = item & kIdx;
+  if (item & kLeafBit) load_slot<W>(nodes, idx / W, (int)(idx % W), off, b, dummy);
+  else load_slot<W>(nodes, idx, -1, off, b, dummy);
+}
+
+// One breadth-first level: W threads per task; thread i tests child i of
+// the expanding side (against every child of the other side when both
+// expand).  Surviving children become tasks of the next level, or leaf
+// pairs.
+template <int W>
+__global__ void __launch_bounds__(256) k_wave_expand(WaveArgs P, const uint4 *qin,
+                                                     const unsigned *qin_n, uint4 *qout,
+                                                     unsigned *qout_n, uint4 *lq, unsigned *lq_n) {
+  const int lane = threadIdx.x & 31;
+  const int64_t n = (int64_t)min(*qin_n, P.q_cap) * W;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  const F3 zero = mkf3(0.f, 0.f, 0.f);
+  unsigned long long cnt[3] = {0, 0, 0};  // node pairs, box tests, bytes
+  for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g - lane < n; g += stride) {
+    unsigned task_mask = 0, leaf_mask = 0;
+    uint4 e = make_uint4(0u, 0u, 0u, 0u);
+    int i = 0;
+    bool xa = false, xb = false;
+    F3 off = zero;
+    Box ba;
+    uint32_t na = 0;
+    bool live = false;
+    if (g < n) {
+      e = qin[g / W];
+      i = (int)(g % W);
+      live = P.flags[e.x] == 0;
+      xa = e.y & kExpand;
+      xb = e.z & kExpand;
+      // with one side expanding only its W children are tested
+      if (!(xa && xb) && !xa && !xb) live = false;
+    }
+    if (live) {
+      off = cand_offset(P, e.x);
+      if (xa) {
+        uint32_t ca;
+        load_slot<W>(P.A.nodes, e.y & kIdx, i, zero, ba, ca);
+        if (ca == kEmpty) live = false;
+        na = (ca & kLeafBit) ? (kLeafBit | ((e.y & kIdx) * W + i)) : ca;
+      } else {
+        item_box<W>(P.A.nodes, e.y, zero, ba);
+        na = e.y & ~kExpand;
+      }
+      if (i == 0) cnt[0] += 1;
+      cnt[2] += 32;
+    }
+    if (live) {
+      if (xb) {
+        const int j0 = xa ? 0 : i, j1 = xa ? W : i + 1;
+        for (int j = j0; j < j1; ++j) {
+          Box bb;
+          uint32_t cb;
+          load_slot<W>(P.B.nodes, e.z & kIdx, j, off, bb, cb);
+          cnt[1] += 1;
+          cnt[2] += 32;
+          if (cb == kEmpty || !overlap(ba, bb)) continue;
+          const bool lb = cb & kLeafBit;
+          if ((na & kLeafBit) && lb) leaf_mask |= 1u << j;
+          else task_mask |= 1u << j;
+        }
+      } else {
+        Box bb;
+        item_box<W>(P.B.nodes, e.z, off, bb);
+        cnt[1] += 1;
+        cnt[2] += 32;
+        if (overlap(ba, bb)) {
+          if ((na & kLeafBit) && (e.z & kLeafBit)) leaf_mask = 1u;
+          else task_mask = 1u;
+        }
+      }
+    }
+    // write the outputs (the B-side children are reloaded: L1 hits)
+    unsigned tpos = warp_append(qout_n, __popc(task_mask), lane);
+    unsigned lpos = warp_append(lq_n, __popc(leaf_mask), lane);
+    unsigned bits = task_mask | leaf_mask;
+    while (bits) {
+      const int j = __ffs(bits) - 1;
+      bits &= bits - 1;
+      Box bb;
+      uint32_t nb;
+      if (xb) {
+        uint32_t cb;
+        const int jj = xa ? j : i;
+        load_slot<W>(P.B.nodes, e.z & kIdx, jj, off, bb, cb);
+        nb = (cb & kLeafBit) ? (kLeafBit | ((e.z & kIdx) * W + jj)) : cb;
+      } else {
+        item_box<W>(P.B.nodes, e.z, off, bb);
+        nb = e.z & ~kExpand;
+      }
+      if ((task_mask >> j) & 1u) {
+        if (tpos < P.q_cap) {
+          uint2 t = make_task(na, ba, nb, bb);
+          qout[tpos] = make_uint4(e.x, t.x, t.y, 0u);
+        } else {
+          atomicCAS(P.err, 0, DERR_QUEUE);
+        }
+        ++tpos;
+      } else {
+        if (lpos < P.q_cap) lq[lpos] = make_uint4(e.x, na, nb, 0u);
+        else atomicCAS(P.err, 0, DERR_QUEUE);
+        ++lpos;
+      }
+    }
+  }
+  unsigned long long v[C_NUM] = {};
+  v[C_NODE_PAIRS] = cnt[0];
+  v[C_BOX_TESTS] = cnt[1];
+  v[C_BYTES] = cnt[2];
+  flush_counters(P.counters, v, lane, C_NUM);
+}
+
+// Leaf pairs: 16 threads per pair (8 source triangles of each side); each
+// thread slab-tests its triangle's owned edges against the other leaf's box
+// and tests them exactly against the other leaf's triangles.
+template <int W, bool EXACT>
+__global__ void __launch_bounds__(256) k_wave_leaf(WaveArgs P, const uint4 *lq, const unsigned *lq_n) {
+  const int lane = threadIdx.x & 31;
+  const int64_t n = (int64_t)min(*lq_n, P.q_cap) * 16;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  const F3 zero = mkf3(0.f, 0.f, 0.f);
+  unsigned long long c_slab = 0, c_st = 0, c_fb = 0, c_bytes = 0, c_lp = 0;
+  for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < n; g += stride) {
+    const uint4 e = lq[g >> 4];
+    const int u = (int)(g & 15);
+    if (P.flags[e.x]) continue;
+    const bool dirA = u < 8;
+    const int k = u & 7;
+    const uint32_t sslot = (dirA ? e.y : e.z) & kIdx, tslot = (dirA ? e.z : e.y) & kIdx;
+    const Side &S = dirA ? P.A : P.B;
+    const Side &T = dirA ? P.B : P.A;
+    Box sbox, tb;
+    uint32_t sdesc, tdesc;
+    load_slot<W>(S.nodes, sslot / W, (int)(sslot % W), zero, sbox, sdesc);
+    if (k > (int)(sdesc & 7u)) continue;
+    const int ia = P.cand[2 * (int64_t)e.x], ib = P.cand[2 * (int64_t)e.x + 1];
+    const F3 off = cand_offset(P, e.x);
+    const F3 soff = dirA ? zero : off, toff = dirA ? off : zero;
+    load_slot<W>(T.nodes, tslot / W, (int)(tslot % W), toff, tb, tdesc);
+    if (u == 0) c_lp += 1;
+    const int64_t sbase = S.toff[dirA ? ia : ib], tbase = T.toff[dirA ? ib : ia];
+    const int64_t s_rec = sbase + ((sdesc >> 3) & 0x0FFFFFFFu) + k;
+    const int64_t t_first = tbase + ((tdesc >> 3) & 0x0FFFFFFFu);
+    const int t_n = (int)(tdesc & 7u) + 1;
+    F3 v[3];
+    int own;
+    load_tri(S.trirec, s_rec, soff, v[0], v[1], v[2], own);
+    c_bytes += 48 + 64;
+    bool hit = false;
+    for (int ek = 0; ek < 3 && !hit; ++ek) {
+      if (!((own >> ek) & 1)) continue;
+      const F3 p = v[ek], qv = v[ek == 2 ? 0 : ek + 1];
+      Seg sg = make_seg(p, qv);
+      c_slab += 1;
+      if (!slab_hit(sg, tb.lo, tb.hi)) continue;
+      const F3 elo = mkf3(fminf(p.x, qv.x), fminf(p.y, qv.y), fminf(p.z, qv.z));
+      const F3 ehi = mkf3(fmaxf(p.x, qv.x), fmaxf(p.y, qv.y), fmaxf(p.z, qv.z));
+      for (int t = 0; t < t_n; ++t) {
+        F3 a, b, c;
+        int town;
+        load_tri(T.trirec, t_first + t, toff, a, b, c, town);
+        c_bytes += 48;
+        const float lx = fminf(a.x, fminf(b.x, c.x)), hx = fmaxf(a.x, fmaxf(b.x, c.x));
+        const float ly = fminf(a.y, fminf(b.y, c.y)), hy = fmaxf(a.y, fmaxf(b.y, c.y));
+        const float lz = fminf(a.z, fminf(b.z, c.z)), hz = fmaxf(a.z, fmaxf(b.z, c.z));
+        if (lx > ehi.x || elo.x > hx || ly > ehi.y || elo.y > hy || lz > ehi.z || elo.z > hz)
+          continue;
+        c_st += 1;
+        bool r;
+        if (EXACT) {
+          r = segtri_exact(p, qv, a, b, c);
+        } else {
+          const int f = segtri_filter(p, qv, a, b, c);
+          if (f < 0) {
+            c_fb += 1;
+            r = segtri_exact(p, qv, a, b, c);
+          } else {
+            r = f == 1;
+          }
+        }
+        if (r) {
+          hit = true;
+          break;
+        }
+      }
+    }
+    if (hit) P.flags[e.x] = 1;
+  }
+  unsigned long long v[C_NUM] = {};
+  v[C_LEAF_PAIRS] = c_lp;
+  v[C_SLAB_TESTS] = c_slab;
+  v[C_SEGTRI] = c_st;
+  v[C_FALLBACK] = c_fb;
+  v[C_BYTES] = c_bytes;
+  // threads of a warp may have left the loop at different times: reconverge
+  __syncwarp();
+  flush_counters(P.counters, v, lane, C_NUM);
+}
+
+// Parity rays, one thread per (pair, direction): inside(B, A) for even
+// threads, inside(A, B) for odd ones.  Depth-first with a per-thread stack
+// (bounded by 1 + (W - 1) * depth).
+template <int W>
+__device__ int thread_parity(const Side &T, int it, F3 toff, F3 vf, int ax, int dir, uint32_t *stk,
+                             int cap, unsigned long long &nodes, unsigned long long &tris) {
+  const int64_t tbase = T.toff[it];
+  const I3 v = toi(vf);
+  int sp = 0;
+  stk[sp++] = (uint32_t)T.roots[it];
+  bool on = false;
+  int par = 0;
+  unsigned iters = 0;
+  while (sp > 0) {
+    if (++iters > (1u << 24)) return -1;
+    const uint32_t node = stk[--sp];
+    nodes += 1;
+    for (int c = 0; c < W; ++c) {
+      Box b;
+      uint32_t ch;
+      load_slot<W>(T.nodes, node, c, toff, b, ch);
+      if (ch == kEmpty) continue;
+      if (!ray_axis_box(vf, b, ax, dir)) continue;
+      if (ch & kLeafBit) {
+        const int64_t first = tbase + ((ch >> 3) & 0x0FFFFFFFu);
+        const int cntl = (int)(ch & 7u) + 1;
+        for (int t = 0; t < cntl; ++t) {
+          F3 a, bb, cc;
+          int own;
+          load_tri(T.trirec, first + t, toff, a, bb, cc, own);
+          const I3 ai = toi(a), bi = toi(bb), ci = toi(cc);
+          on = on || on_triangle(v, ai, bi, ci);
+          par ^= ray_axis_hit(v, ai, bi, ci, ax, dir) ? 1 : 0;
+          tris += 1;
+        }
+      } else {
+        if (sp >= cap) return -1;
+        stk[sp++] = ch;
+      }
+    }
+  }
+  return par | (on ? 2 : 0);
+}
+
+template <int W>
+__global__ void __launch_bounds__(128) k_wave_parity(WaveArgs P) {
+  constexpr int CAP = 1 + (W - 1) * 64;
+  uint32_t stk[CAP];
+  const int lane = threadIdx.x & 31;
+  const int64_t n = *P.n_cand * 2;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  const F3 zero = mkf3(0.f, 0.f, 0.f);
+  unsigned long long rays = 0, nodes = 0, tris = 0, bytes = 0;
+  for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < n; g += stride) {
+    const int64_t c = g >> 1;
+    const bool bInA = (g & 1) == 0;
+    const int ia = P.cand[2 * c], ib = P.cand[2 * c + 1];
+    if (ia < 0 || ia >= P.MA || ib < 0 || ib >= P.MB) continue;
+    const F3 off = cand_offset(P, c);
+    const Side &Q = bInA ? P.B : P.A;
+    const Side &T = bInA ? P.A : P.B;
+    const int iq = bInA ? ib : ia, it = bInA ? ia : ib;
+    const F3 qoff = bInA ? off : zero, toff = bInA ? zero : off;
+    const int64_t v0 = Q.voff[iq], nv = Q.voff[iq + 1] - v0;
+    const F3 lo = add(ld3(T.aabb + 6 * (int64_t)it), toff), hi = add(ld3(T.aabb + 6 * (int64_t)it + 3), toff);
+    int res = 0;
+    for (int64_t k = 0; k < nv; ++k) {
+      const int64_t vid = Q.lexorder[v0 + k];
+      const F3 v = add(ld3(Q.xyz + 3 * vid), qoff);
+      bytes += 16;
+      if (v.x < lo.x || v.x > hi.x || v.y < lo.y || v.y > hi.y || v.z < lo.z || v.z > hi.z) break;
+      rays += 1;
+      const unsigned long long n0 = nodes, t0 = tris;
+      int ax, dir;
+      ray_axis_choice(v, lo, hi, ax, dir);
+      const int r = thread_parity<W>(T, it, toff, v, ax, dir, stk, CAP, nodes, tris);
+      bytes += (nodes - n0) * W * 32 + (tris - t0) * 48;
+      if (r < 0) {
+        atomicCAS(P.err, 0, DERR_STACK);
+        break;
+      }
+      if (!(r & 2)) {
+        res = r & 1;
+        break;
+      }
+    }
+    if (res) P.flags[c] = 1;
+  }
+  unsigned long long v[C_NUM] = {};
+  v[C_PARITY_RAYS] = rays;
+  v[C_PARITY_NODES] = nodes;
+  v[C_PARITY_TRIS] = tris;
+  v[C_BYTES] = bytes;
+  __syncwarp();
+  flush_counters(P.counters, v, lane, C_NUM);
+}
+
 // Later passes: warps pop spilled (candidate, itemA, itemB) tasks and continue
 // the crossing test from there.  A crossing sets the candidate's flag (the
 // first pass already stored the containment result; a crossing can only add
@@ -878,7 +1292,7 @@ __global__ void __launch_bounds__(128, 4) k_refine_tasks(RefineArgs P) {
   WarpMem sm = carve<W>(smem + (size_t)wib * warp_smem_bytes<W>(P.stack_cap), P.stack_cap);
   Cnt cnt;
   for (int i = 0; i < C_NUM; ++i) cnt.v[i] = 0;
-  const unsigned int n = min(*P.q_in_n, P.q_cap);
+  const unsigned int n = min(*P.q_in_n, P.q_in_cap);
   for (;;) {
     unsigned int t = 0;
     if (lane == 0) t = atomicAdd(P.q_in_pos, 1u);
@@ -1040,6 +1454,27 @@ static RefineKernel pick_task_kernel(int W, bool exact) {
   return exact ? k_refine_tasks<8, true> : k_refine_tasks<8, false>;
 }
 
+typedef void (*WaveExpandKernel)(WaveArgs, const uint4 *, const unsigned *, uint4 *,
+                                 unsigned *, uint4 *, unsigned *);
+typedef void (*WaveLeafKernel)(WaveArgs, const uint4 *, const unsigned *);
+typedef void (*WaveParityKernel)(WaveArgs);
+
+static WaveExpandKernel pick_wave_expand(int W) {
+  if (W == 2) return k_wave_expand<2>;
+  if (W == 4) return k_wave_expand<4>;
+  return k_wave_expand<8>;
+}
+static WaveLeafKernel pick_wave_leaf(int W, bool exact) {
+  if (W == 2) return exact ? k_wave_leaf<2, true> : k_wave_leaf<2, false>;
+  if (W == 4) return exact ? k_wave_leaf<4, true> : k_wave_leaf<4, false>;
+  return exact ? k_wave_leaf<8, true> : k_wave_leaf<8, false>;
+}
+static WaveParityKernel pick_wave_parity(int W) {
+  if (W == 2) return k_wave_parity<2>;
+  if (W == 4) return k_wave_parity<4>;
+  return k_wave_parity<8>;
+}
+
 static int smem_per_warp(int W, int cap) {
   if (W == 2) return warp_smem_bytes<2>(cap);
   if (W == 4) return warp_smem_bytes<4>(cap);
@@ -1076,7 +1511,8 @@ pj_status run_join(Ctx *ctx, Dataset *A, Dataset *B, const int32_t *cand,
   const bool exact = o->leaf_mode == PJ_LEAF_EXACT;
 
   pj_status st;
-  int64_t *d_misc = (int64_t *)ws_get(ctx, "misc", 64, &st);  // [0] n_cand, [1] K, [2] work
+  // [0] n_cand, [1] K, [2] work counter, [3..4] spill queue counters, [5..7] wave counters
+  int64_t *d_misc = (int64_t *)ws_get(ctx, "misc", 64, &st);
   if (!d_misc) return st;
   int64_t *h_misc = (int64_t *)ctx->h_pinned;
 
@@ -1110,7 +1546,7 @@ pj_status run_join(Ctx *ctx, Dataset *A, Dataset *B, const int32_t *cand,
     if (!counts) return st;
     int64_t *offs = (int64_t *)ws_get(ctx, "mbb_offs", sizeof(int64_t) * (MA + 1), &st);
     if (!offs) return st;
-    int nb = (int)((MA + MBB_T - 1) / MBB_T);
+    int nb = (int)std::min<int64_t>((MA + (MBB_T / 32) - 1) / (MBB_T / 32), (int64_t)ctx->num_sms * 64);
     k_mbb<false><<<nb, MBB_T, 0, s>>>(A->d_aabb, MA, B->d_aabb, MB, self_join, counts, nullptr, nullptr);
     ++ctx->launches;
     PJ_CK(cudaGetLastError());
@@ -1178,6 +1614,29 @@ pj_status run_join(Ctx *ctx, Dataset *A, Dataset *B, const int32_t *cand,
   uint4 *q2 = (uint4 *)ws_get(ctx, "spill2", sizeof(uint4) * (size_t)q_cap, &st);
   if (!q2) return st;
   unsigned int *qctr = reinterpret_cast<unsigned int *>(d_misc + 3);  // q1 n/pos, q2 n/pos
+  // wavefront front end: breadth-first levels before the warp passes (a
+  // per-thread parity stack needs the BVH depth to stay within 64 levels)
+  int wave_levels = o->wave_levels > 0 ? o->wave_levels : (o->wave_levels < 0 ? 0 : 8);
+  if (std::max(bA.max_depth, bB.max_depth) > 64) wave_levels = 0;
+  const unsigned int wq_cap = 1u << 23;
+  uint4 *wqa = nullptr, *wqb = nullptr, *wlq = nullptr;
+  unsigned int *wctr = reinterpret_cast<unsigned int *>(d_misc + 5);  // qa n/pos, qb n/pos, lq n
+  int wave_grid[3] = {1, 1, 1};  // expand/init, leaf, parity: one resident wave
+  if (wave_levels > 0 && o->launch_mode != PJ_LAUNCH_PER_PAIR) {
+    int occ = 0;
+    PJ_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, pick_wave_expand(W), 256, 0));
+    wave_grid[0] = std::max(1, occ) * ctx->num_sms;
+    PJ_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, pick_wave_leaf(W, exact), 256, 0));
+    wave_grid[1] = std::max(1, occ) * ctx->num_sms;
+    PJ_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, pick_wave_parity(W), 128, 0));
+    wave_grid[2] = std::max(1, occ) * ctx->num_sms;
+    wqa = (uint4 *)ws_get(ctx, "wave_a", sizeof(uint4) * (size_t)wq_cap, &st);
+    if (!wqa) return st;
+    wqb = (uint4 *)ws_get(ctx, "wave_b", sizeof(uint4) * (size_t)wq_cap, &st);
+    if (!wqb) return st;
+    wlq = (uint4 *)ws_get(ctx, "wave_leaf", sizeof(uint4) * (size_t)wq_cap, &st);
+    if (!wlq) return st;
+  }
   unsigned int *d_cycles = nullptr;
   if (o->record_cycles) {
     d_cycles = (unsigned int *)ws_get(ctx, "cycles", sizeof(unsigned int) * (size_t)std::max<int64_t>(C, 1), &st);
@@ -1207,6 +1666,7 @@ pj_status run_join(Ctx *ctx, Dataset *A, Dataset *B, const int32_t *cand,
   if (per_pair) budget1 = 0;
   const long long budget2 = budget1 > 0 ? 8 * budget1 : 0;
   args.q_cap = q_cap;
+  args.q_in_cap = q_cap;
   args.q_in = nullptr;
   args.q_in_n = nullptr;
   args.q_in_pos = nullptr;
@@ -1235,6 +1695,64 @@ pj_status run_join(Ctx *ctx, Dataset *A, Dataset *B, const int32_t *cand,
         }
         args.single = -1;
         ctx->launches += C;
+      } else if (wave_levels > 0) {
+        // wavefront front end, then the warp passes over what is left
+        PJ_CK(cudaMemsetAsync(d_misc + 2, 0, 48, s));  // work, spill and wave counters
+        PJ_CK(cudaMemsetAsync(d_flags, 0, (size_t)C, s));
+        WaveArgs wa;
+        wa.A = args.A;
+        wa.B = args.B;
+        wa.cand = d_cand;
+        wa.cand_off = d_off;
+        wa.n_cand = d_misc;
+        wa.flags = d_flags;
+        wa.counters = ctx->d_counters;
+        wa.err = ctx->d_err;
+        wa.q_cap = wq_cap;
+        wa.MA = A->M;
+        wa.MB = B->M;
+        WaveExpandKernel kx = pick_wave_expand(W);
+        WaveLeafKernel kl = pick_wave_leaf(W, exact);
+        WaveParityKernel kp = pick_wave_parity(W);
+        const int wblocks = wave_grid[0], lblocks = wave_grid[1], pblocks = wave_grid[2];
+        k_wave_init<<<wblocks, 256, 0, s>>>(wa, wqa, wctr);
+        kp<<<pblocks, 128, 0, s>>>(wa);
+        uint4 *qin = wqa, *qout = wqb;
+        unsigned int *qin_n = wctr, *qout_n = wctr + 2;
+        for (int lvl = 0; lvl < wave_levels; ++lvl) {
+          PJ_CK(cudaMemsetAsync(qout_n, 0, 4, s));
+          PJ_CK(cudaMemsetAsync(wctr + 4, 0, 4, s));
+          kx<<<wblocks, 256, 0, s>>>(wa, qin, qin_n, qout, qout_n, wlq, wctr + 4);
+          kl<<<lblocks, 256, 0, s>>>(wa, wlq, wctr + 4);
+          std::swap(qin, qout);
+          std::swap(qin_n, qout_n);
+        }
+        RefineArgs a1 = args;
+        a1.q_in = qin;
+        a1.q_in_n = qin_n;
+        a1.q_in_pos = qin_n + 1;
+        a1.q_in_cap = wq_cap;
+        a1.q_out = budget1 > 0 ? q1 : nullptr;
+        a1.q_out_n = qctr;
+        a1.budget = budget1;
+        kern_tasks<<<(int)blocks, threads, smem, s>>>(a1);
+        RefineArgs a2 = args;
+        a2.q_in = q1;
+        a2.q_in_n = qctr;
+        a2.q_in_pos = qctr + 1;
+        a2.q_out = q2;
+        a2.q_out_n = qctr + 2;
+        a2.budget = budget2;
+        kern_tasks<<<(int)blocks, threads, smem, s>>>(a2);
+        RefineArgs a3 = args;
+        a3.q_in = q2;
+        a3.q_in_n = qctr + 2;
+        a3.q_in_pos = qctr + 3;
+        a3.q_out = nullptr;
+        a3.q_out_n = nullptr;
+        a3.budget = 0;
+        kern_tasks<<<(int)blocks, threads, smem, s>>>(a3);
+        ctx->launches += 5 + 2 * wave_levels;
       } else {
         PJ_CK(cudaMemsetAsync(d_misc + 2, 0, 24, s));  // work counter, queue counters
         RefineArgs a1 = args;
@@ -1276,7 +1794,7 @@ pj_status run_join(Ctx *ctx, Dataset *A, Dataset *B, const int32_t *cand,
   char gk[256];
   snprintf(gk, sizeof(gk), "%p|%p|%p|%p|%p|%d|%d|%d|%d|%d|%lld|%d|%d", (void *)A, (void *)B,
            (void *)d_cand, (void *)d_off, (void *)d_cycles, W, key.second, (int)exact, k,
-           (int)o->launch_mode, (long long)C, (int)budget1, args.max_pop);
+           (int)o->launch_mode, (long long)C, (int)budget1, args.max_pop * 100 + wave_levels);
   bool replayed = false;
   if (graph) {
     auto it = ctx->graphs.find(gk);
@@ -1322,6 +1840,7 @@ pj_status run_join(Ctx *ctx, Dataset *A, Dataset *B, const int32_t *cand,
     // construction) and in one pass
     args.max_pop = 1;
     budget1 = 0;
+    wave_levels = 0;
     PJ_CK(cudaMemsetAsync(ctx->d_err, 0, sizeof(int) * 4, s));
     if ((st = device_part(true)) != PJ_OK) return st;
     PJ_CK(cudaEventRecord(e1, s));
@@ -1483,6 +2002,7 @@ pj_status run_join_noalloc(Ctx *ctx, Dataset *A, Dataset *B, const int32_t *d_ca
   args.q_in = nullptr;
   args.q_in_n = nullptr;
   args.q_in_pos = nullptr;
+  args.q_in_cap = 0;
   args.n_cand = d_n;
   args.flags = d_flags;
   args.work = work;

@@ -47,7 +47,8 @@ class pj_join_opts(ctypes.Structure):
                 ("warps_per_pair", ctypes.c_int32), ("leaf_mode", ctypes.c_int32),
                 ("launch_mode", ctypes.c_int32), ("use_graph", ctypes.c_int32),
                 ("out_host", ctypes.c_int32), ("keep_flags", ctypes.c_int32),
-                ("record_cycles", ctypes.c_int32), ("spill_budget", ctypes.c_int32)]
+                ("record_cycles", ctypes.c_int32), ("spill_budget", ctypes.c_int32),
+                ("wave_levels", ctypes.c_int32), ("reserved", ctypes.c_int32)]
 
 
 class pj_pairs(ctypes.Structure):
@@ -221,7 +222,8 @@ def pj_dataset_info_get(ctx, ds: int) -> dict:
 def pj_join_intersects_ex(ctx, a: int, b: int, cand=None, cand_offsets=None, self_join=False,
                           width=0, leaf_size=0, warps_per_pair=0, leaf_mode=PJ_LEAF_FILTERED,
                           launch_mode=PJ_LAUNCH_PERSISTENT, use_graph=False, out_host=True,
-                          keep_flags=False, record_cycles=False, spill_budget=0, stream=None):
+                          keep_flags=False, record_cycles=False, spill_budget=0, wave_levels=0,
+                          stream=None):
     """Run the join.  Returns the filled pj_pairs (free it with pj_free_pairs).
 
     cand / cand_offsets: None (device bounding-box filter join), numpy int32
@@ -236,7 +238,7 @@ def pj_join_intersects_ex(ctx, a: int, b: int, cand=None, cand_offsets=None, sel
         n = int(cand.shape[0])
     opts = pj_join_opts(width, leaf_size, warps_per_pair, leaf_mode, launch_mode,
                         int(use_graph), int(out_host), int(keep_flags), int(record_cycles),
-                        int(spill_budget))
+                        int(spill_budget), int(wave_levels), 0)
     res = pj_pairs()
     rc = load().pj_join_intersects_ex(ctx, a, b, _ptr(cand), _ptr(cand_offsets), n,
                                       1 if dev else 0, int(self_join), ctypes.byref(opts),

@@ -52,7 +52,7 @@ def test_tiny_spheres_all_bvh_shapes(ctx, tiny, W, L):
 
 
 @pytest.mark.parametrize("mode", ["exact", "warps2", "warps4", "per_pair", "explicit", "graph",
-                                  "spill1", "spill3", "nospill"])
+                                  "spill1", "spill3", "nospill", "nowave", "wave1", "wave9"])
 def test_tiny_spheres_modes(ctx, tiny, mode):
     for A, B, ha, hb, exp in tiny:
         kw = {}
@@ -78,6 +78,14 @@ def test_tiny_spheres_modes(ctx, tiny, mode):
             kw["spill_budget"] = 3
         elif mode == "nospill":
             kw["spill_budget"] = -1
+        elif mode == "nowave":
+            kw["wave_levels"] = -1
+        elif mode == "wave1":
+            kw["wave_levels"] = 1
+            kw["spill_budget"] = 1
+        elif mode == "wave9":
+            kw["wave_levels"] = 9
+            kw["use_graph"] = True
         got, _ = ctx.join(ha, hb, cand=cand, width=4, leaf_size=4, **kw)
         if mode == "explicit":
             got = got[np.lexsort((got[:, 1], got[:, 0]))]
@@ -121,9 +129,9 @@ def test_exhaustive_lattice(ctx):
     exp = oracle.join(A, B, cand, tier=1)
     ha, hb = _load(ctx, A, ((4, 4), (2, 1), (8, 8))), _load(ctx, B, ((4, 4), (2, 1), (8, 8)))
     for W, L in ((4, 4), (2, 1), (8, 8)):
-        for mode in (pierce.PJ_LEAF_FILTERED, pierce.PJ_LEAF_EXACT):
+        for mode, wave in ((pierce.PJ_LEAF_FILTERED, 0), (pierce.PJ_LEAF_EXACT, -1)):
             res = pierce.pj_join_intersects_ex(ctx.h, ha, hb, cand=cand, width=W, leaf_size=L,
-                                               leaf_mode=mode, out_host=True)
+                                               leaf_mode=mode, wave_levels=wave, out_host=True)
             got = pierce.pairs_to_numpy(res)
             pierce.pj_free_pairs(ctx.h, res)
             assert np.array_equal(got, cand[exp.astype(bool)]), (W, L, mode)
@@ -302,3 +310,39 @@ def test_counters_move(ctx, tiny):
     assert c["pairs_refined"] == len(oracle.mbb_candidates(A, B))
     assert c["pairs_hit"] == len(exp)
     assert c["segtri_tests"] > 0 and c["node_pairs"] > 0 and c["bytes_fetched"] > 0
+
+
+def test_parity_rays_along_every_axis(ctx):
+    """Containment is decided by a parity ray along the axis and direction
+    that leaves the target's box soonest; the result must equal the oracle's
+    +z parity for every choice.  Small tetrahedra sit inside and outside a
+    noisy sphere and a straight vertical tube, near each face of their boxes."""
+    rng = np.random.default_rng(12)
+    sphere = synth._placed_sphere(3, np.array([0.5, 0.5, 0.5]), 0.1, np.eye(3),
+                                  noise=lambda u: 0.05 * np.sin(3 * u[:, 0]))
+    z = np.linspace(0.2, 0.8, 64)
+    curve = np.stack([np.full_like(z, 0.3), np.full_like(z, 0.7), z], axis=1)
+    V, T = synth._tube(curve, 0.03, 40)
+    tube = (synth.quantize(V), T)
+    A = synth.concat([sphere, tube])
+    smalls, cand = [], []
+    for target, (v, _) in enumerate([sphere, tube]):
+        lo, hi = v.min(axis=0), v.max(axis=0)
+        for _ in range(150):
+            p = lo + rng.uniform(0.02, 0.98, size=3) * (hi - lo)
+            k = rng.integers(3)
+            p[k] = (lo[k] + rng.uniform(0.0, 0.08) * (hi[k] - lo[k])) if rng.random() < 0.5 else \
+                (hi[k] - rng.uniform(0.0, 0.08) * (hi[k] - lo[k]))
+            d = rng.integers(40, 400, size=(3, 3))
+            t = synth.tetra(p, p + [d[0, 0], 0, 0], p + [0, d[1, 1], 0], p + [0, 0, d[2, 2]])
+            smalls.append((np.rint(t[0]).astype(np.float32), t[1]))
+            cand.append((target, len(smalls) - 1))
+    B = synth.concat(smalls)
+    cand = np.array(cand, dtype=np.int32)
+    exp = oracle.join(A, B, cand, tier=2)
+    assert 30 < exp.sum() < len(cand) - 30
+    ha, hb = _load(ctx, A, ((4, 4), (8, 2))), _load(ctx, B, ((4, 4), (8, 2)))
+    for W, L in ((4, 4), (8, 2)):
+        for wave in (0, -1):
+            got, _ = ctx.join(ha, hb, cand=cand, width=W, leaf_size=L, wave_levels=wave)
+            assert np.array_equal(got, cand[exp.astype(bool)]), (W, L, wave)
