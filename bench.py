@@ -240,16 +240,15 @@ def run_ours(args, rank, world, local_rank):
     if dist:
         dist.barrier()
     torch.cuda.synchronize()
-    total_ms, refine_ms, C, K = 0.0, 0.0, 0, 0
+    total_ms, C, K = 0.0, 0, 0
     for _ in range(args.steps):
         flush.zero_()                                   # evict L2 between steps
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(stream)
-        C, K, rms = step()
+        C, K, _ = step()
         e1.record(stream)
         e1.synchronize()
         total_ms += e0.elapsed_time(e1)
-        refine_ms += rms
     torch.cuda.synchronize()
     if dist:
         dist.barrier()
@@ -259,13 +258,26 @@ def run_ours(args, rank, world, local_rank):
     value = C_all / (ms_step / 1000.0)
     segtri_s = cnt["segtri_tests"] / (total_ms / 1000.0)
     launches = cnt["kernel_launches"]
-    # dominant kernel: the refinement launch
-    refine_avg = refine_ms / args.steps
-    bytes_launch = cnt["bytes_fetched"] / args.steps
+    # phase breakdown (same join, not replayed from a graph, so CUDA events
+    # separate the phases): parity rays, breadth-first front end, warp passes
+    ctx.reset_counters()
+    ph = {"parity_ms": [], "front_ms": [], "tasks_ms": [], "refine_ms": []}
+    for _ in range(args.steps):
+        flush.zero_()
+        res = pierce.pj_join_intersects_ex(ctx.h, ha, hb, **dict(opts, use_graph=False))
+        for k in ph:
+            ph[k].append(getattr(res, k))
+        pierce.pj_free_pairs(ctx.h, res)
+    torch.cuda.synchronize()
+    pc = ctx.counters()
+    phase_ms = {k: float(np.median(v)) for k, v in ph.items()}
+    bytes_tasks = pc["bytes_tasks"] / args.steps
+    bytes_all = pc["bytes_fetched"] / args.steps
     peak, peak_kind = measured_peaks()
-    achieved = bytes_launch / (refine_avg / 1000.0) / 1e9
+    # dominant kernel: the per-warp passes (k_refine_tasks, 3 launches a step)
+    tasks_ms = max(phase_ms["tasks_ms"], 1e-6)
+    achieved = bytes_tasks / (tasks_ms / 1000.0) / 1e9
     traffic = profile_traffic(os.path.join(ROOT, "paper_2609_24513_gb300", "csrc", "pj_join.cu"))
-
     line_e2e = None
     cand_host = _candidates_host(ctx, ha, hb, C)
     if not args.no_e2e:
@@ -286,9 +298,14 @@ def run_ours(args, rank, world, local_rank):
             "gpu_launches": int(launches),
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "traffic": traffic,
-                         "kernel": "k_refine", "refine_ms": refine_avg,
+                         "kernel": "k_refine_tasks (3 launches per step)",
+                         "launch_ms": tasks_ms / 3.0, "bytes_per_launch": bytes_tasks / 3.0,
                          "peak_source": peak_kind,
-                         "bytes_per_launch": bytes_launch},
+                         "refinement_phase": {"ms": phase_ms["refine_ms"], "bytes": bytes_all,
+                                              "achieved_gbs": bytes_all / (phase_ms["refine_ms"] / 1000.0) / 1e9,
+                                              "parity_ms": phase_ms["parity_ms"],
+                                              "front_ms": phase_ms["front_ms"],
+                                              "tasks_ms": phase_ms["tasks_ms"]}},
             "e2e": line_e2e,
             "clocks": clk}
     if rank == 0 and world == 1 and not args.no_cpu_baseline:

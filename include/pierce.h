@@ -97,7 +97,7 @@ typedef struct {
                                second pass allows 8 times as many            */
   int32_t wave_levels;      /* BVH levels descended breadth-first, one thread
                                per child test, before the per-warp passes
-                               (0: 8; < 0: none)                             */
+                               (0: 12; < 0: none)                            */
   int32_t reserved;
 } pj_join_opts;
 
@@ -115,6 +115,12 @@ typedef struct {
   float mbb_ms;             /* of which: bounding-box filter join             */
   float refine_ms;          /* of which: refinement (crossing + parity)       */
   float compact_ms;         /* of which: compaction                           */
+  float parity_ms;          /* refinement phases (CUDA events; -1 when the
+                               join was replayed from a graph): parity rays, */
+  float front_ms;           /* breadth-first front end (levels and leaf
+                               pairs),                                       */
+  float tasks_ms;           /* and the per-warp passes over what was left     */
+  float reserved3;
   uint32_t *cycles;         /* device, C values (only with record_cycles):
                                clock64 cycles the refinement spent on each
                                candidate (saturated at 2^32 - 1)              */
@@ -138,7 +144,7 @@ typedef struct {
   uint64_t kernel_launches;     /* kernels launched by joins (host count)       */
   uint64_t tasks_spilled;       /* traversal tasks handed to a later pass        */
   uint64_t tasks_resumed;       /* spilled tasks taken up by a later pass        */
-  uint64_t reserved;
+  uint64_t bytes_tasks;         /* of bytes_fetched: the per-warp passes        */
 } pj_counters;
 
 /* Dataset summary. */
@@ -270,6 +276,49 @@ pj_status pj_join_intersects_noalloc(pj_ctx *ctx, pj_dataset a, pj_dataset b,
                                      const int32_t *d_cand, int64_t n_cand,
                                      uint8_t *d_flags, int32_t *d_pairs,
                                      int64_t *d_count, void *cuda_stream);
+
+/* --------------------------------------------------------------------------
+ * Autotuning (the paper has no counterpart: its parameters are fixed by
+ * OptiX; here BVH width, leaf size, warps per pair and the depth of the
+ * breadth-first front end are chosen per dataset pair by measurement)
+ * ------------------------------------------------------------------------ */
+
+/* The configurations to try: every combination of the listed values. */
+typedef struct {
+  int32_t widths[3];        /* subset of {2, 4, 8}                           */
+  int32_t n_widths;
+  int32_t leaf_sizes[4];    /* subset of {1, 2, 4, 8}                        */
+  int32_t n_leaf_sizes;
+  int32_t warps[3];         /* subset of {1, 2, 4}                           */
+  int32_t n_warps;
+  int32_t wave_levels[4];   /* values of pj_join_opts.wave_levels            */
+  int32_t n_wave_levels;
+  int32_t sample_permille;  /* calibration sample, per mille of the
+                               candidates (0: 20, i.e. 2 %; at least 1,000
+                               candidates or all of them)                   */
+  int32_t repeats;          /* timed joins per configuration (0: 3)          */
+  uint64_t seed;            /* sample seed                                   */
+} pj_tune_space;
+
+/* One measured configuration. */
+typedef struct {
+  int32_t width, leaf_size, warps_per_pair, wave_levels;
+  float ms;                 /* median device time of the join on the sample  */
+  float reserved;
+} pj_tune_entry;
+
+/* Measure every configuration of *space on a seeded sample of the
+ * candidates (cand: n_cand x 2 host array, or NULL for the bounding-box
+ * candidates) and return the fastest as *best (a complete pj_join_opts with
+ * that width, leaf size, warps per pair and front-end depth, other fields
+ * default).  table (may be NULL) receives up to table_cap entries in the
+ * order measured, *table_n (may be NULL) their count.  Builds the BVHs the
+ * space needs; the ones it built that did not win are freed again.
+ * Synchronous. */
+pj_status pj_autotune(pj_ctx *ctx, pj_dataset a, pj_dataset b,
+                      const int32_t *cand, int64_t n_cand, int32_t self_join,
+                      const pj_tune_space *space, pj_join_opts *best,
+                      pj_tune_entry *table, int32_t table_cap, int32_t *table_n);
 
 /* --------------------------------------------------------------------------
  * Counters and diagnostics

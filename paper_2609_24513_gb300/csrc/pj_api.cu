@@ -204,7 +204,7 @@ static cudaError_t dalloc(T **p, int64_t n) {
   return cudaMalloc((void **)p, sizeof(T) * (size_t)(n > 0 ? n : 1));
 }
 
-static void free_bvh(Bvh &b) {
+void free_bvh(Bvh &b) {
   cudaFree(b.d_nodes);
   cudaFree(b.d_roots);
   cudaFree(b.d_tri_order);
@@ -570,6 +570,25 @@ pj_status pj_free_pairs(pj_ctx *h, pj_pairs *res) {
   return PJ_OK;
 }
 
+pj_status pj_autotune(pj_ctx *h, pj_dataset a, pj_dataset b, const int32_t *cand,
+                      int64_t n_cand, int32_t self_join, const pj_tune_space *space,
+                      pj_join_opts *best, pj_tune_entry *table, int32_t table_cap,
+                      int32_t *table_n) {
+  Ctx *ctx = reinterpret_cast<Ctx *>(h);
+  if (!ctx || !space || !best) return PJ_ERR_INVALID_ARG;
+  std::lock_guard<std::mutex> lk(ctx->mu);
+  ctx->err.clear();
+  Dataset *A = get_ds(ctx, a), *B = get_ds(ctx, b);
+  if (!A || !B) return fail(ctx, PJ_ERR_INVALID_ARG, "unknown dataset");
+  if (self_join && a != b) return fail(ctx, PJ_ERR_INVALID_ARG, "self_join needs a == b");
+  cudaSetDevice(ctx->device);
+  int n = 0;
+  pj_status st = run_autotune(ctx, A, B, cand, cand ? n_cand : -1, self_join, space, best, table,
+                              table ? table_cap : 0, &n);
+  if (table_n) *table_n = n;
+  return st;
+}
+
 pj_status pj_get_counters(pj_ctx *h, pj_counters *out) {
   Ctx *ctx = reinterpret_cast<Ctx *>(h);
   if (!ctx || !out) return PJ_ERR_INVALID_ARG;
@@ -594,6 +613,7 @@ pj_status pj_get_counters(pj_ctx *h, pj_counters *out) {
   out->kernel_launches = ctx->launches;
   out->tasks_spilled = c[C_SPILLED];
   out->tasks_resumed = c[C_TASKS];
+  out->bytes_tasks = c[C_BYTES_TASKS];
   return PJ_OK;
 }
 

@@ -69,7 +69,7 @@ struct Dataset {
 enum {
   C_PAIRS = 0, C_NODE_PAIRS, C_BOX_TESTS, C_LEAF_PAIRS, C_SLAB_TESTS,
   C_SEGTRI, C_FALLBACK, C_PARITY_RAYS, C_PARITY_NODES, C_PARITY_TRIS,
-  C_BYTES, C_HITS, C_SPILLED, C_TASKS, C_NUM = 16
+  C_BYTES, C_HITS, C_SPILLED, C_TASKS, C_BYTES_TASKS, C_NUM = 16
 };
 
 struct Workspace {
@@ -113,6 +113,11 @@ enum { DERR_NONE = 0, DERR_STACK = 1, DERR_QUEUE = 2, DERR_OFFSET = 3 };
 
 // build.cu
 pj_status build_bvh(Ctx *ctx, Dataset *ds, int W, int L, cudaStream_t s);
+void free_bvh(Bvh &b);
+// tune.cu
+pj_status run_autotune(Ctx *ctx, Dataset *A, Dataset *B, const int32_t *cand, int64_t n_cand,
+                       int self_join, const pj_tune_space *space, pj_join_opts *best,
+                       pj_tune_entry *table, int table_cap, int *table_n);
 // join.cu
 pj_status run_join(Ctx *ctx, Dataset *A, Dataset *B, const int32_t *cand,
                    const int32_t *cand_off, int64_t n_cand, int cand_on_device,

@@ -1324,6 +1324,7 @@ __global__ void __launch_bounds__(128, 4) k_refine_tasks(RefineArgs P) {
     }
     if (lane == 0) cnt.v[C_TASKS] += 1;
   }
+  cnt.v[C_BYTES_TASKS] = cnt.v[C_BYTES];
   for (int i = 0; i < C_NUM; ++i) {
     unsigned long long v = cnt.v[i];
     for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(FULL, v, o);
@@ -1516,14 +1517,17 @@ pj_status run_join(Ctx *ctx, Dataset *A, Dataset *B, const int32_t *cand,
   if (!d_misc) return st;
   int64_t *h_misc = (int64_t *)ctx->h_pinned;
 
-  cudaEvent_t ev[4];
+  // events: 0 start, 1 candidates ready, 2 refinement done, 3 end,
+  // 4 parity done, 5 front end done (wavefront path, not in graph replays)
+  cudaEvent_t ev[6];
   for (auto &e : ev) cudaEventCreate(&e);
   struct EvGuard {
     cudaEvent_t *e;
     ~EvGuard() {
-      for (int i = 0; i < 4; ++i) cudaEventDestroy(e[i]);
+      for (int i = 0; i < 6; ++i) cudaEventDestroy(e[i]);
     }
   } eg{ev};
+  bool phases = false;
   cudaEvent_t e0 = ev[0], e1 = ev[3];
   // the legacy default stream cannot be captured into a graph: order the
   // work on the context's stream after everything already queued on it
@@ -1616,7 +1620,7 @@ pj_status run_join(Ctx *ctx, Dataset *A, Dataset *B, const int32_t *cand,
   unsigned int *qctr = reinterpret_cast<unsigned int *>(d_misc + 3);  // q1 n/pos, q2 n/pos
   // wavefront front end: breadth-first levels before the warp passes (a
   // per-thread parity stack needs the BVH depth to stay within 64 levels)
-  int wave_levels = o->wave_levels > 0 ? o->wave_levels : (o->wave_levels < 0 ? 0 : 8);
+  int wave_levels = o->wave_levels > 0 ? o->wave_levels : (o->wave_levels < 0 ? 0 : 12);
   if (std::max(bA.max_depth, bB.max_depth) > 64) wave_levels = 0;
   const unsigned int wq_cap = 1u << 23;
   uint4 *wqa = nullptr, *wqb = nullptr, *wlq = nullptr;
@@ -1717,6 +1721,7 @@ pj_status run_join(Ctx *ctx, Dataset *A, Dataset *B, const int32_t *cand,
         const int wblocks = wave_grid[0], lblocks = wave_grid[1], pblocks = wave_grid[2];
         k_wave_init<<<wblocks, 256, 0, s>>>(wa, wqa, wctr);
         kp<<<pblocks, 128, 0, s>>>(wa);
+        if (timed) PJ_CK(cudaEventRecord(ev[4], s));
         uint4 *qin = wqa, *qout = wqb;
         unsigned int *qin_n = wctr, *qout_n = wctr + 2;
         for (int lvl = 0; lvl < wave_levels; ++lvl) {
@@ -1726,6 +1731,10 @@ pj_status run_join(Ctx *ctx, Dataset *A, Dataset *B, const int32_t *cand,
           kl<<<lblocks, 256, 0, s>>>(wa, wlq, wctr + 4);
           std::swap(qin, qout);
           std::swap(qin_n, qout_n);
+        }
+        if (timed) {
+          PJ_CK(cudaEventRecord(ev[5], s));
+          phases = true;
         }
         RefineArgs a1 = args;
         a1.q_in = qin;
@@ -1854,6 +1863,7 @@ pj_status run_join(Ctx *ctx, Dataset *A, Dataset *B, const int32_t *cand,
   float ms = 0.f;
   cudaEventElapsedTime(&ms, e0, e1);
   cudaEventElapsedTime(&out->mbb_ms, ev[0], ev[1]);
+  out->parity_ms = out->front_ms = out->tasks_ms = -1.f;
   if (replayed) {
     // one graph launch: refinement and compaction are not separated
     cudaEventElapsedTime(&out->refine_ms, ev[1], ev[3]);
@@ -1861,6 +1871,11 @@ pj_status run_join(Ctx *ctx, Dataset *A, Dataset *B, const int32_t *cand,
   } else {
     cudaEventElapsedTime(&out->refine_ms, ev[1], ev[2]);
     cudaEventElapsedTime(&out->compact_ms, ev[2], ev[3]);
+    if (phases) {
+      cudaEventElapsedTime(&out->parity_ms, ev[1], ev[4]);
+      cudaEventElapsedTime(&out->front_ms, ev[4], ev[5]);
+      cudaEventElapsedTime(&out->tasks_ms, ev[5], ev[2]);
+    }
   }
 
   out->count = K;

@@ -57,6 +57,8 @@ class pj_pairs(ctypes.Structure):
                 ("n_candidates", ctypes.c_int64), ("flags", ctypes.c_void_p),
                 ("device_ms", ctypes.c_float), ("mbb_ms", ctypes.c_float),
                 ("refine_ms", ctypes.c_float), ("compact_ms", ctypes.c_float),
+                ("parity_ms", ctypes.c_float), ("front_ms", ctypes.c_float),
+                ("tasks_ms", ctypes.c_float), ("reserved3", ctypes.c_float),
                 ("cycles", ctypes.c_void_p), ("impl", ctypes.c_void_p)]
 
 
@@ -65,7 +67,7 @@ class pj_counters(ctypes.Structure):
         "pairs_refined", "node_pairs", "box_tests", "leaf_pairs", "edge_slab_tests",
         "segtri_tests", "exact_fallbacks", "parity_rays", "parity_nodes",
         "parity_tri_tests", "bytes_fetched", "pairs_hit", "kernel_launches",
-        "tasks_spilled", "tasks_resumed")] + [("reserved", ctypes.c_uint64)]
+        "tasks_spilled", "tasks_resumed", "bytes_tasks")]
 
 
 class pj_dataset_info(ctypes.Structure):
@@ -74,6 +76,21 @@ class pj_dataset_info(ctypes.Structure):
                 ("bvh_nodes", ctypes.c_int64), ("bvh_width", ctypes.c_int32),
                 ("bvh_leaf_size", ctypes.c_int32), ("bvh_max_depth", ctypes.c_int32),
                 ("reserved", ctypes.c_int32), ("device_bytes", ctypes.c_int64)]
+
+
+class pj_tune_space(ctypes.Structure):
+    _fields_ = [("widths", ctypes.c_int32 * 3), ("n_widths", ctypes.c_int32),
+                ("leaf_sizes", ctypes.c_int32 * 4), ("n_leaf_sizes", ctypes.c_int32),
+                ("warps", ctypes.c_int32 * 3), ("n_warps", ctypes.c_int32),
+                ("wave_levels", ctypes.c_int32 * 4), ("n_wave_levels", ctypes.c_int32),
+                ("sample_permille", ctypes.c_int32), ("repeats", ctypes.c_int32),
+                ("seed", ctypes.c_uint64)]
+
+
+class pj_tune_entry(ctypes.Structure):
+    _fields_ = [("width", ctypes.c_int32), ("leaf_size", ctypes.c_int32),
+                ("warps_per_pair", ctypes.c_int32), ("wave_levels", ctypes.c_int32),
+                ("ms", ctypes.c_float), ("reserved", ctypes.c_float)]
 
 
 _vp = ctypes.c_void_p
@@ -97,6 +114,9 @@ SIGNATURES = {
                                      ctypes.POINTER(pj_pairs)]),
     "pj_free_pairs": (_i32, [_vp, ctypes.POINTER(pj_pairs)]),
     "pj_join_intersects_noalloc": (_i32, [_vp, _i32, _i32, _vp, _i64, _vp, _vp, _vp, _vp]),
+    "pj_autotune": (_i32, [_vp, _i32, _i32, _vp, _i64, _i32, ctypes.POINTER(pj_tune_space),
+                           ctypes.POINTER(pj_join_opts), ctypes.POINTER(pj_tune_entry), _i32,
+                           ctypes.POINTER(_i32)]),
     "pj_get_counters": (_i32, [_vp, ctypes.POINTER(pj_counters)]),
     "pj_reset_counters": (_i32, [_vp]),
     "pj_segtri_batch": (_i32, [_vp, _vp, _vp, _i64, _i32, _vp, ctypes.POINTER(_i64), _vp]),
@@ -273,6 +293,36 @@ def pj_join_intersects_noalloc(ctx, a: int, b: int, d_cand, d_flags, d_pairs, d_
 
 def pj_free_pairs(ctx, res: pj_pairs):
     _check(ctx, load().pj_free_pairs(ctx, ctypes.byref(res)))
+
+
+def pj_autotune(ctx, a: int, b: int, cand=None, self_join=False, widths=(2, 4, 8),
+                leaf_sizes=(1, 2, 4, 8), warps=(1, 2, 4), wave_levels=(0,), sample_permille=0,
+                repeats=0, seed=0):
+    """Measure every configuration of the space on a calibration sample.
+    Returns (best pj_join_opts as a dict, table of measured entries)."""
+    sp = pj_tune_space()
+    for name, vals, cap in (("widths", widths, 3), ("leaf_sizes", leaf_sizes, 4),
+                            ("warps", warps, 3), ("wave_levels", wave_levels, 4)):
+        vals = list(vals)[:cap]
+        arr = getattr(sp, name)
+        for k, v in enumerate(vals):
+            arr[k] = int(v)
+        setattr(sp, "n_" + name, len(vals))
+    sp.sample_permille, sp.repeats, sp.seed = int(sample_permille), int(repeats), int(seed)
+    n = 0
+    if cand is not None:
+        cand = np.ascontiguousarray(cand, dtype=np.int32).reshape(-1, 2)
+        n = cand.shape[0]
+    best = pj_join_opts()
+    cap = 3 * 4 * 3 * 4
+    table = (pj_tune_entry * cap)()
+    tn = _i32()
+    _check(ctx, load().pj_autotune(ctx, a, b, _ptr(cand), n, int(self_join), ctypes.byref(sp),
+                                   ctypes.byref(best), table, cap, ctypes.byref(tn)))
+    best_d = {f: getattr(best, f) for f, _ in pj_join_opts._fields_ if f != "reserved"}
+    rows = [{f: getattr(table[k], f) for f, _ in pj_tune_entry._fields_ if f != "reserved"}
+            for k in range(tn.value)]
+    return best_d, rows
 
 
 def pj_get_counters(ctx) -> dict:

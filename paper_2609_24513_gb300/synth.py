@@ -415,3 +415,232 @@ def sample_indices(seed: int, n: int, k: int) -> np.ndarray:
     rng = np.random.default_rng(seed)
     k = min(k, n)
     return np.sort(rng.choice(n, size=k, replace=False)) if k else np.zeros(0, np.int64)
+
+
+# ---------------------------------------------------------------------------
+# Batching workload: many candidate pairs of very uneven size, built from a
+# pool of template meshes placed by per-pair integer translations
+# ---------------------------------------------------------------------------
+
+def latlong_sphere(faces: int, radius: float, centre, rng, noise_amp: float = 0.05):
+    """Closed latitude/longitude sphere with about `faces` triangles
+    (F = 2 s (r - 1) for s segments and r rings), smooth radial noise."""
+    s = max(3, int(round(math.sqrt(faces / 2.0))))
+    r = max(2, int(round(faces / (2.0 * s))) + 1)
+    lat = np.linspace(0, np.pi, r + 1)[1:-1]            # r - 1 interior rings
+    lon = np.linspace(0, 2 * np.pi, s, endpoint=False)
+    ring = np.stack([np.sin(lat)[:, None] * np.cos(lon)[None, :],
+                     np.sin(lat)[:, None] * np.sin(lon)[None, :],
+                     np.cos(lat)[:, None] * np.ones_like(lon)[None, :]], axis=-1).reshape(-1, 3)
+    U = np.concatenate([[[0, 0, 1.0]], ring, [[0, 0, -1.0]]])
+    field = _smooth_field(rng)
+    X = U * (1.0 + noise_amp * field(U))[:, None] * radius + np.asarray(centre)
+    N, S = 0, len(U) - 1
+    idx = lambda i, j: 1 + i * s + (j % s)               # ring i, segment j
+    faces_l = []
+    for j in range(s):
+        faces_l.append((N, idx(0, j), idx(0, j + 1)))
+    for i in range(r - 2):
+        for j in range(s):
+            faces_l.append((idx(i, j), idx(i + 1, j), idx(i + 1, j + 1)))
+            faces_l.append((idx(i, j), idx(i + 1, j + 1), idx(i, j + 1)))
+    for j in range(s):
+        faces_l.append((S, idx(r - 2, j + 1), idx(r - 2, j)))
+    F = np.array(faces_l, dtype=np.int32)
+    a, b, c = X[F[:, 0]], X[F[:, 1]], X[F[:, 2]]
+    if np.einsum("ij,ij->i", a - centre, np.cross(b - a, c - a)).sum() < 0:
+        F = F[:, [0, 2, 1]]
+    return quantize(X), F
+
+
+def _short_tube(rng, faces: int, centre, radius: float, length: float):
+    rings = max(2, int(round(faces / 32.0)))
+    d = rng.normal(size=3)
+    d /= np.linalg.norm(d)
+    e = np.cross(d, rng.normal(size=3))
+    e /= np.linalg.norm(e)
+    t = np.linspace(-0.5, 0.5, 5)[:, None]
+    ctrl = np.asarray(centre) + t * d * length + (t ** 2 - 0.1) * e * length * 0.3
+    curve = _bspline(ctrl, 1024)
+    V, T = _tube(curve, radius, rings)
+    return quantize(V), T
+
+
+def batching(seed: int, n_pairs: int = 100000, n_templates: int = 2000,
+             f_range=(200, 50000), classes=(0.30, 0.10, 0.60)):
+    """(A templates, B templates, candidates n x 2, offsets n x 3, intended
+    class per pair: 0 crossing, 1 containment, 2 disjoint with overlapping
+    boxes).  Face counts are log-uniform in f_range; half the templates are
+    noisy spheres and half short swept tubes (spheres below 1,000 faces).
+    Every template sits at the box centre; pair k tests A_i against B_j
+    translated by offsets[k]."""
+    rng = np.random.default_rng(seed)
+    centre = np.full(3, 0.5)
+
+    def pool(n):
+        meshes, radius, kind = [], [], []
+        for _ in range(n):
+            F = math.exp(rng.uniform(math.log(f_range[0]), math.log(f_range[1])))
+            if F < 1000 or rng.random() < 0.5:
+                rr = rng.uniform(0.01, 0.04)
+                meshes.append(latlong_sphere(int(F), rr, centre, rng))
+                kind.append(0)
+            else:
+                rr = rng.uniform(0.003, 0.008)
+                meshes.append(_short_tube(rng, int(F), centre, rr, rng.uniform(0.04, 0.1)))
+                kind.append(1)
+            v = meshes[-1][0].astype(np.float64)
+            radius.append(np.linalg.norm(v - v.mean(axis=0), axis=1).max())
+        return meshes, np.array(radius), np.array(kind)
+
+    ma, ra, ka = pool(n_templates)
+    mb, rb, kb = pool(n_templates)
+    A = concat(ma, dict(kind="batching_templates", seed=seed))
+    B = concat(mb, dict(kind="batching_templates", seed=seed + 1))
+    lo_a = np.stack([v.min(axis=0) for v, _ in ma]).astype(np.int64)
+    hi_a = np.stack([v.max(axis=0) for v, _ in ma]).astype(np.int64)
+    lo_b = np.stack([v.min(axis=0) for v, _ in mb]).astype(np.int64)
+    hi_b = np.stack([v.max(axis=0) for v, _ in mb]).astype(np.int64)
+    ca, cb = (lo_a + hi_a) / 2.0, (lo_b + hi_b) / 2.0
+    spheres_a = np.nonzero(ka == 0)[0]
+    cls = rng.choice(3, size=n_pairs, p=np.asarray(classes) / np.sum(classes))
+    cand = np.zeros((n_pairs, 2), dtype=np.int32)
+    off = np.zeros((n_pairs, 3), dtype=np.int64)
+    small_b = np.argsort(rb)
+    for k in range(n_pairs):
+        if cls[k] == 1:
+            i = int(rng.choice(spheres_a))
+            # a B template well inside A's inscribed ball
+            fit = small_b[: max(1, np.searchsorted(rb[small_b], 0.35 * ra[i]))]
+            j = int(rng.choice(fit))
+            u = rng.normal(size=3)
+            d = u / np.linalg.norm(u) * rng.uniform(0, 0.15) * ra[i]
+        else:
+            i, j = int(rng.integers(n_templates)), int(rng.integers(n_templates))
+            if cls[k] == 0:
+                u = rng.normal(size=3)
+                d = u / np.linalg.norm(u) * ra[i] * rng.uniform(0.85, 1.05)
+            else:
+                h = (hi_a[i] - lo_a[i] + hi_b[j] - lo_b[j]) / 2.0
+                d = rng.choice([-1.0, 1.0], size=3) * h * rng.uniform(0.8, 0.95, size=3)
+        o = np.rint(ca[i] + d - cb[j]).astype(np.int64)
+        o = np.clip(o, -lo_b[j], QMAX - hi_b[j])
+        cand[k] = (i, j)
+        off[k] = o
+    return A, B, cand, off.astype(np.int32), cls.astype(np.int8)
+
+
+# ---------------------------------------------------------------------------
+# Urban precision stress: extruded star-shaped buildings with pitched roofs
+# on a jittered grid, some sharing walls exactly, plus boxes and cylinders
+# ---------------------------------------------------------------------------
+
+def building(footprint: np.ndarray, z0: int, height: int, roof: int, bands: int):
+    """Closed prism over a star-shaped integer footprint (n x 2, counter-
+    clockwise around its first point's kernel centre), walls split into
+    `bands` rows, pitched roof to an apex over the footprint centre.
+    F = 2 n (bands + 1)."""
+    n = len(footprint)
+    cx, cy = np.rint(footprint.mean(axis=0))
+    levels = np.rint(np.linspace(z0, z0 + height, bands + 1)).astype(np.int64)
+    rings = [np.column_stack([footprint, np.full(n, z)]) for z in levels]
+    V = np.concatenate([[[cx, cy, z0]]] + rings + [[[cx, cy, z0 + height + roof]]]).astype(np.float64)
+    bot, apex = 0, len(V) - 1
+    vid = lambda lv, k: 1 + lv * n + (k % n)
+    F = []
+    for k in range(n):
+        F.append((bot, vid(0, k + 1), vid(0, k)))
+    for lv in range(bands):
+        for k in range(n):
+            F.append((vid(lv, k), vid(lv, k + 1), vid(lv + 1, k + 1)))
+            F.append((vid(lv, k), vid(lv + 1, k + 1), vid(lv + 1, k)))
+    for k in range(n):
+        F.append((apex, vid(bands, k), vid(bands, k + 1)))
+    return V.astype(np.float32), np.array(F, dtype=np.int32)
+
+
+def _star(rng, n, R):
+    th = np.sort(2 * np.pi * (np.arange(n) + rng.uniform(-0.3, 0.3, size=n)) / n)
+    rr = R * rng.uniform(0.6, 1.0, size=n)
+    return np.stack([rr * np.cos(th), rr * np.sin(th)], axis=1)
+
+
+def _rect(w, h, per_side):
+    """Rectangle boundary, counter-clockwise, per_side points on each side."""
+    t = np.arange(per_side) / per_side
+    pts = [np.stack([-w / 2 + w * t, np.full(per_side, -h / 2)], 1),
+           np.stack([np.full(per_side, w / 2), -h / 2 + h * t], 1),
+           np.stack([w / 2 - w * t, np.full(per_side, h / 2)], 1),
+           np.stack([np.full(per_side, -w / 2), h / 2 - h * t], 1)]
+    return np.concatenate(pts)
+
+
+def cylinder(centre, radius: float, height: float, sides: int, z_axis=True):
+    """Capped cylinder (4 * sides triangles) around a vertical axis."""
+    th = 2 * np.pi * np.arange(sides) / sides
+    ring = np.stack([radius * np.cos(th), radius * np.sin(th)], 1)
+    cx, cy, cz = centre
+    V = np.concatenate([[[cx, cy, cz]],
+                        np.column_stack([ring + [cx, cy], np.full(sides, cz)]),
+                        np.column_stack([ring + [cx, cy], np.full(sides, cz + height)]),
+                        [[cx, cy, cz + height]]])
+    F = []
+    for k in range(sides):
+        a, b = 1 + k, 1 + (k + 1) % sides
+        F += [(0, b, a), (a, b, b + sides), (a, b + sides, a + sides),
+              (len(V) - 1, a + sides, b + sides)]
+    return np.rint(V).astype(np.float32), np.array(F, dtype=np.int32)
+
+
+def urban(seed: int, n_buildings: int = 50000, n_parts: int = 5000,
+          f_range=(100, 2000), degenerate_frac: float = 0.05):
+    """One dataset for a self join: buildings (F log-uniform in f_range, 6-64
+    footprint sides) on a jittered grid; a `degenerate_frac` share of them
+    come as exactly adjacent rectangular pairs sharing a wall plane, an edge
+    or a corner; plus boxes and cylinders placed among them."""
+    rng = np.random.default_rng(seed)
+    side = int(math.ceil(math.sqrt(n_buildings)))
+    cell = QMAX / (side + 6.0)          # a 3-cell margin keeps every mesh on the grid
+    meshes, tags = [], []
+    k = 0
+    while k < n_buildings:
+        gx, gy = k % side, k // side
+        base = np.array([(gx + 3.5) * cell, (gy + 3.5) * cell])
+        F = math.exp(rng.uniform(math.log(f_range[0]), math.log(f_range[1])))
+        z0 = int(rng.integers(1000, 3000))
+        height = int(rng.integers(int(0.5 * cell), int(3 * cell)))
+        if rng.random() < degenerate_frac and k + 1 < n_buildings:
+            # two rectangular buildings touching exactly
+            w, h = int(0.45 * cell), int(0.35 * cell)
+            per = max(2, int(F / 16))
+            bands = max(1, int(F / (2 * 4 * per)) - 1)
+            fp = np.rint(_rect(w, h, per) + base).astype(np.int64)
+            meshes.append(building(fp.astype(np.float64), z0, height, int(0.3 * h), bands))
+            mode = rng.integers(3)
+            shift = {0: (w, 0), 1: (w, h), 2: (w, int(h / 2))}[int(mode)]
+            fp2 = fp + np.array(shift)
+            meshes.append(building(fp2.astype(np.float64), z0 if mode != 1 else z0 + height // 3,
+                                   height, int(0.3 * h), bands))
+            tags += ["shared_wall", "shared_wall"] if mode != 1 else ["shared_edge", "shared_edge"]
+            k += 2
+            continue
+        n = int(rng.integers(6, max(7, min(64, int(F / 4)) + 1)))
+        bands = max(1, int(round(F / (2 * n))) - 1)
+        R = cell * rng.uniform(0.35, 0.7)
+        fp = np.rint(_star(rng, n, R) + base + rng.uniform(-0.2, 0.2, size=2) * cell)
+        meshes.append(building(fp, z0, height, int(rng.uniform(0.2, 0.5) * R), bands))
+        tags.append("building")
+        k += 1
+    for _ in range(n_parts):
+        c = np.array([rng.uniform(3 * cell, QMAX - 3 * cell), rng.uniform(3 * cell, QMAX - 3 * cell),
+                      rng.uniform(800, 3000)])
+        if rng.random() < 0.5:
+            h = rng.uniform(0.3, 1.5, size=3) * cell
+            meshes.append(box(np.rint(c), np.rint(c + h)))
+            tags.append("box")
+        else:
+            meshes.append(cylinder(c, rng.uniform(0.1, 0.5) * cell, rng.uniform(0.5, 2) * cell,
+                                   int(rng.integers(8, 33))))
+            tags.append("cylinder")
+    meshes = [(np.asarray(v, np.float32), t) for v, t in meshes]
+    return concat(meshes, dict(kind="urban", seed=seed, tags=tags))

@@ -346,3 +346,23 @@ def test_parity_rays_along_every_axis(ctx):
         for wave in (0, -1):
             got, _ = ctx.join(ha, hb, cand=cand, width=W, leaf_size=L, wave_levels=wave)
             assert np.array_equal(got, cand[exp.astype(bool)]), (W, L, wave)
+
+
+def test_autotune_picks_a_measured_configuration(ctx):
+    A, B = synth.tiny_spheres(1003)
+    exp = oracle.join_all(A, B, tier=2)
+    ha, hb = ctx.load(A), ctx.load(B)
+    best, table = pierce.pj_autotune(ctx.h, ha, hb, widths=(2, 4), leaf_sizes=(2, 4),
+                                     warps=(1, 2), wave_levels=(0, -1), repeats=2, seed=3)
+    assert len(table) == 2 * 2 * 2 * 2
+    fastest = min(table, key=lambda r: r["ms"])
+    assert (best["width"], best["leaf_size"], best["warps_per_pair"], best["wave_levels"]) == \
+        (fastest["width"], fastest["leaf_size"], fastest["warps_per_pair"], fastest["wave_levels"])
+    # only the winning BVH shape is kept, and it is the dataset default now
+    info = pierce.pj_dataset_info_get(ctx.h, ha)
+    assert (info["bvh_width"], info["bvh_leaf_size"]) == (best["width"], best["leaf_size"])
+    got, _ = ctx.join(ha, hb, **{k: best[k] for k in ("width", "leaf_size", "warps_per_pair",
+                                                      "wave_levels")})
+    assert np.array_equal(got, exp)
+    with pytest.raises(pierce.PierceError):
+        pierce.pj_autotune(ctx.h, ha, hb, widths=(3,))

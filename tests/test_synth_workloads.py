@@ -1,0 +1,51 @@
+"""Generators of the batching and urban workloads: closed meshes, the face
+counts and shapes they promise, and (with the oracle) the intended mix of
+pair classes."""
+import collections
+
+import numpy as np
+
+import oracle
+from paper_2609_24513_gb300 import synth
+
+
+def test_latlong_sphere_counts_and_closure():
+    rng = np.random.default_rng(0)
+    for F in (200, 1000, 5000):
+        v, t = synth.latlong_sphere(F, 0.02, np.full(3, 0.5), rng)
+        ds = synth.concat([(v, t)])
+        assert oracle.is_closed_manifold(ds, 0)
+        assert 0.7 * F < len(t) < 1.3 * F
+
+
+def test_batching_workload():
+    A, B, cand, off, cls = synth.batching(3001, n_pairs=300, n_templates=60)
+    for ds in (A, B):
+        f = np.diff(ds.toff)
+        assert f.min() >= 150 and f.max() <= 60000
+        assert all(oracle.is_closed_manifold(ds, k) for k in range(ds.nmesh))
+    # translated meshes stay on the grid
+    for (i, j), o in zip(cand, off):
+        v, _ = B.mesh(int(j))
+        assert np.all(v.min(axis=0) + o >= 0) and np.all(v.max(axis=0) + o <= synth.QMAX)
+    flags = oracle.join(A, B, cand, tier=2, offsets=off)
+    assert flags[cls == 1].all()                 # containment pairs intersect
+    assert flags[cls == 2].mean() < 0.05          # box-corner placements rarely touch
+    assert 0.5 < flags[cls == 0].mean() <= 1.0    # most crossing placements cross
+    assert 0.2 < flags.mean() < 0.5
+
+
+def test_urban_workload():
+    U = synth.urban(5001, n_buildings=400, n_parts=40)
+    assert all(oracle.is_closed_manifold(U, k) for k in range(U.nmesh))
+    tags = collections.Counter(U.meta["tags"])
+    assert tags["building"] > 300 and tags["box"] + tags["cylinder"] == 40
+    assert tags["shared_wall"] + tags["shared_edge"] > 0
+    cand = oracle.mbb_candidates(U, U, self_join=True)
+    flags = oracle.join(U, U, cand, tier=2)
+    t = U.meta["tags"]
+    # buildings sharing a wall plane or an edge touch but never intersect
+    for (i, j), f in zip(cand, flags):
+        if t[i] == t[j] and t[i] in ("shared_wall", "shared_edge") and abs(int(i) - int(j)) == 1:
+            assert not f
+    assert 0 < flags.sum() < len(cand)
