@@ -121,49 +121,88 @@ __device__ __forceinline__ int sgn64(long long v) { return (v > 0) - (v < 0); }
 // Strict crossing from the exact signs.  With A = a - p, B = b - p,
 // C = c - p, d = q - p:  orient(p,q,a,b) = d.(A x B), orient(p,q,b,c) =
 // d.(B x C), orient(p,q,c,a) = d.(C x A), orient(a,b,c,p) = -A.(B x C) and
-// orient(a,b,c,q) = orient(a,b,c,p) + the three former.
-__device__ __forceinline__ bool segtri_exact(F3 pf, F3 qf, F3 af, F3 bf,
-                                             F3 cf) {
+// orient(a,b,c,q) = -(a - q).((b - q) x (c - q)).  The segment crosses iff
+// the last two have opposite nonzero signs and the first three one nonzero
+// sign.
+// Exact strict test with early exits: the plane side of p and q first (two
+// orientations), the three edge orientations only if the plane separates
+// them.
+__device__ __forceinline__ bool segtri_exact_staged(F3 pf, F3 qf, F3 af, F3 bf, F3 cf) {
   I3 p = toi(pf), q = toi(qf);
   I3 A = isub(toi(af), p), B = isub(toi(bf), p), C = isub(toi(cf), p);
-  I3 d = isub(q, p);
   L3 bc = cross64(B, C);
-  long long u = dot64(d, cross64(A, B));
-  long long v = dot64(d, bc);
-  long long w = dot64(d, cross64(C, A));
-  long long sp = -dot64(A, bc);
-  long long sq = sp + u + v + w;
-  int su = sgn64(u);
-  if (su == 0 || sgn64(v) != su || sgn64(w) != su) return false;
-  int a1 = sgn64(sp), a2 = sgn64(sq);
-  return a1 != 0 && a2 != 0 && a1 != a2;
+  const int a1 = -sgn64(dot64(A, bc));
+  I3 Aq = isub(toi(af), q), Bq = isub(toi(bf), q), Cq = isub(toi(cf), q);
+  const int a2 = -sgn64(dot64(Aq, cross64(Bq, Cq)));
+  if (a1 == 0 || a2 == 0 || a1 == a2) return false;
+  I3 d = isub(q, p);
+  const int su = sgn64(dot64(d, cross64(A, B)));
+  if (su == 0) return false;
+  if (sgn64(dot64(d, bc)) != su) return false;
+  return sgn64(dot64(d, cross64(C, A))) == su;
 }
 
-// Filtered strict test: returns 1 (cross), 0 (no cross) or -1 (undecided by
-// the filter; call segtri_exact).
-__device__ __forceinline__ int segtri_filter(F3 p, F3 q, F3 a, F3 b, F3 c) {
-  F3 d = sub(q, p);
-  F3 A = sub(a, p), B = sub(b, p), C = sub(c, p);
-  // side of p and q w.r.t. the triangle's plane
-  CrossP bc = cross_p(B, C);
-  float dA, eA;
-  dot_p(A, bc, dA, eA);  // -orient(a,b,c,p)
-  F3 Aq = sub(a, q), Bq = sub(b, q), Cq = sub(c, q);
-  CrossP bcq = cross_p(Bq, Cq);
-  float dQ, eQ;
-  dot_p(Aq, bcq, dQ, eQ);  // -orient(a,b,c,q)
-  int sp = -cert(dA, eA), sq = -cert(dQ, eQ);
-  if (sp != 0 && sp == sq) return 0;  // both endpoints strictly on one side
-  CrossP ab = cross_p(A, B), ca = cross_p(C, A);
-  float u, eu, v, ev, w, ew;
-  dot_p(d, ab, u, eu);
-  dot_p(d, bc, v, ev);
-  dot_p(d, ca, w, ew);
-  int su = cert(u, eu), sv = cert(v, ev), sw = cert(w, ew);
-  // two certified, opposite signs among u, v, w: the line misses
-  if ((su > 0 || sv > 0 || sw > 0) && (su < 0 || sv < 0 || sw < 0)) return 0;
-  if (sp == 0 || sq == 0 || su == 0 || sv == 0 || sw == 0) return -1;
-  return sp != sq ? 1 : 0;  // su == sv == sw here
+// Strict test deciding each of the five signs by the FP32 filter and only
+// the uncertain ones in int64, stopping at the first sign that settles the
+// answer.  *exact is set when any sign needed int64.
+__device__ __forceinline__ bool segtri_filtered(F3 p, F3 q, F3 a, F3 b, F3 c, bool *exact) {
+  const F3 A = sub(a, p), B = sub(b, p), C = sub(c, p);
+  const CrossP bc = cross_p(B, C);
+  float dv, ev;
+  dot_p(A, bc, dv, ev);
+  int sp = -cert(dv, ev);
+  if (sp == 0) {
+    *exact = true;
+    const I3 pi = toi(p);
+    sp = -sgn64(dot64(isub(toi(a), pi), cross64(isub(toi(b), pi), isub(toi(c), pi))));
+    if (sp == 0) return false;
+  }
+  const F3 Aq = sub(a, q), Bq = sub(b, q), Cq = sub(c, q);
+  const CrossP bcq = cross_p(Bq, Cq);
+  dot_p(Aq, bcq, dv, ev);
+  int sq = -cert(dv, ev);
+  if (sq == 0) {
+    *exact = true;
+    const I3 qi = toi(q);
+    sq = -sgn64(dot64(isub(toi(a), qi), cross64(isub(toi(b), qi), isub(toi(c), qi))));
+  }
+  if (sq == 0 || sq == sp) return false;
+  const F3 d = sub(q, p);
+  // u = d.(A x B), v = d.(B x C), w = d.(C x A): one sign, none zero
+  int su;
+  {
+    const CrossP ab = cross_p(A, B);
+    dot_p(d, ab, dv, ev);
+    su = cert(dv, ev);
+    if (su == 0) {
+      *exact = true;
+      const I3 pi = toi(p);
+      su = sgn64(dot64(isub(toi(q), pi), cross64(isub(toi(a), pi), isub(toi(b), pi))));
+      if (su == 0) return false;
+    }
+  }
+  {
+    dot_p(d, bc, dv, ev);
+    int sv = cert(dv, ev);
+    if (sv == -su) return false;
+    if (sv == 0) {
+      *exact = true;
+      const I3 pi = toi(p);
+      sv = sgn64(dot64(isub(toi(q), pi), cross64(isub(toi(b), pi), isub(toi(c), pi))));
+      if (sv != su) return false;
+    }
+  }
+  {
+    const CrossP ca = cross_p(C, A);
+    dot_p(d, ca, dv, ev);
+    int sw = cert(dv, ev);
+    if (sw == 0) {
+      *exact = true;
+      const I3 pi = toi(p);
+      sw = sgn64(dot64(isub(toi(q), pi), cross64(isub(toi(c), pi), isub(toi(a), pi))));
+    }
+    return sw == su;
+  }
 }
 
 // ---------------------------------------------------------------------------

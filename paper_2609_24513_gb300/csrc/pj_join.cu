@@ -465,15 +465,11 @@ __device__ bool leaf_units(const Side &A, const Side &B, int64_t tA, int64_t tB,
           cnt.v[C_SEGTRI] += 1;
           bool r;
           if (EXACT) {
-            r = segtri_exact(p, qv, a, b, c);
+            r = segtri_exact_staged(p, qv, a, b, c);
           } else {
-            int f = segtri_filter(p, qv, a, b, c);
-            if (f < 0) {
-              cnt.v[C_FALLBACK] += 1;
-              r = segtri_exact(p, qv, a, b, c);
-            } else {
-              r = f == 1;
-            }
+            bool ex = false;
+            r = segtri_filtered(p, qv, a, b, c, &ex);
+            cnt.v[C_FALLBACK] += ex ? 1 : 0;
           }
           if (r) {
             hit = true;
@@ -1155,15 +1151,11 @@ __global__ void __launch_bounds__(256) k_wave_leaf(WaveArgs P, const uint4 *lq, 
         c_st += 1;
         bool r;
         if (EXACT) {
-          r = segtri_exact(p, qv, a, b, c);
+          r = segtri_exact_staged(p, qv, a, b, c);
         } else {
-          const int f = segtri_filter(p, qv, a, b, c);
-          if (f < 0) {
-            c_fb += 1;
-            r = segtri_exact(p, qv, a, b, c);
-          } else {
-            r = f == 1;
-          }
+          bool ex = false;
+          r = segtri_filtered(p, qv, a, b, c, &ex);
+          c_fb += ex ? 1 : 0;
         }
         if (r) {
           hit = true;
@@ -1404,15 +1396,11 @@ __global__ void k_segtri_batch(const float *pq, const float *abc, int64_t n, int
     F3 a = ld3(abc + 9 * i), b = ld3(abc + 9 * i + 3), c = ld3(abc + 9 * i + 6);
     bool r;
     if (mode == PJ_LEAF_EXACT) {
-      r = segtri_exact(p, q, a, b, c);
+      r = segtri_exact_staged(p, q, a, b, c);
     } else {
-      int f = segtri_filter(p, q, a, b, c);
-      if (f < 0) {
-        ++fb;
-        r = segtri_exact(p, q, a, b, c);
-      } else {
-        r = f == 1;
-      }
+      bool ex = false;
+      r = segtri_filtered(p, q, a, b, c, &ex);
+      fb += ex ? 1 : 0;
     }
     res[i] = r ? 1 : 0;
   }
