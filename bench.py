@@ -485,6 +485,113 @@ def run_urban(args):
     print(json.dumps(line), flush=True)
 
 
+def _serve_stream(ctx, pierce, ha, hb, lo, hi, arrivals):
+    """Submit query k at arrivals[k] seconds (a submitting thread) while this
+    thread collects; returns (answers, stats, makespan seconds)."""
+    n = len(lo)
+    tickets = [None] * n
+    ready = [threading.Event() for _ in range(n)]
+    err = []
+
+    def submitter():
+        try:
+            t0 = time.perf_counter()
+            for k in range(n):
+                d = arrivals[k] - (time.perf_counter() - t0)
+                if d > 0:
+                    time.sleep(d)
+                tickets[k] = ctx.submit(ha, hb, lo[k], hi[k])
+                ready[k].set()
+        except Exception as e:  # reported by the collector
+            err.append(e)
+            for r in ready:
+                r.set()
+
+    th = threading.Thread(target=submitter)
+    t_start = time.perf_counter()
+    th.start()
+    answers, stats = [None] * n, [None] * n
+    for k in range(n):
+        ready[k].wait()
+        if err:
+            break
+        answers[k], stats[k] = ctx.poll(tickets[k], wait=True)
+    th.join()
+    if err:
+        raise err[0]
+    return answers, stats, time.perf_counter() - t_start
+
+
+def _latency_summary(stats, makespan):
+    lat = np.array([(s["t_done"] - s["t_submit"]) * 1000.0 for s in stats])
+    qwait = np.array([(s["t_admit"] - s["t_submit"]) * 1000.0 for s in stats])
+    pairs = sum(int(s["n_pairs"]) for s in stats)
+    cands = sum(int(s["n_candidates"]) for s in stats)
+    return {"queries": len(stats), "p50_ms": float(np.percentile(lat, 50)),
+            "p99_ms": float(np.percentile(lat, 99)), "mean_ms": float(lat.mean()),
+            "p50_admit_wait_ms": float(np.percentile(qwait, 50)),
+            "pairs_per_s": pairs / makespan, "candidates_per_s": cands / makespan,
+            "queries_per_s": len(stats) / makespan, "makespan_s": makespan,
+            "mean_batch_queries": float(np.mean([s["batch_queries"] for s in stats]))}
+
+
+def run_serving(args):
+    """Serving: the pathology datasets resident with their BVHs; Poisson
+    streams of cube-window join queries (window volume log-uniform in
+    [1e-3, 1] of the cube, i.e. about 10 to 10,000 nuclei per query) at
+    several rates, admitted under a 40 GiB device budget and batched
+    continuously on 4 streams; p50/p99 latency (submit to results on the
+    host) and pairs/s per rate, against the same queries served one at a
+    time, whose answers must be identical."""
+    from paper_2609_24513_gb300 import pierce, synth
+    A, B = make_workload(args.seed, args.nuclei, args.vessels)
+    ctx = pierce.Context(0, serve_streams=4, budget_bytes=40 << 30)
+    ha, hb = ctx.load(A), ctx.load(B)
+    ctx.build(ha, args.width, args.leaf)
+    ctx.build(hb, args.width, args.leaf)
+    rates = [float(r) for r in args.rates.split(",")]
+    n_alone = args.alone_queries
+    counts = [int(min(args.max_queries, max(100, r * args.seconds_per_rate))) for r in rates]
+    # one window list; every run takes a prefix of it
+    lo, hi = synth.serving_windows(args.seed + 77, max(counts + [n_alone, 64]))
+    # warm-up: every serving stream grows its scratch
+    for _ in range(args.warmup):
+        _serve_stream(ctx, pierce, ha, hb, lo[:64], hi[:64], np.zeros(64))
+    # one query at a time: submit, wait for it, then the next
+    alone_ans, alone_st = [], []
+    t0 = time.perf_counter()
+    for k in range(n_alone):
+        a, st = ctx.poll(ctx.submit(ha, hb, lo[k], hi[k]), wait=True)
+        alone_ans.append(a)
+        alone_st.append(st)
+    alone = _latency_summary(alone_st, time.perf_counter() - t0)
+    clocks = ClockSampler(0)
+    clocks.start()
+    per_rate = {}
+    identical = True
+    for i, rate in enumerate(rates):
+        n = counts[i]
+        arr = synth.poisson_arrivals(args.seed + 100 + i, rate, n)
+        ans, st, span = _serve_stream(ctx, pierce, ha, hb, lo[:n], hi[:n], arr)
+        for k in range(min(n, n_alone)):   # same windows as the alone run
+            identical &= bool(np.array_equal(ans[k], alone_ans[k]))
+        per_rate[str(int(rate))] = _latency_summary(st, span)
+    clk = clocks.stop()
+    ctx.close()
+    top = per_rate[str(int(rates[-1]))]
+    line = {"metric": METRIC, "value": top["pairs_per_s"], "unit": "intersecting pairs/s",
+            "n_gpus": 1, "steps": len(rates), "warmup": args.warmup,
+            "ms_per_step": None, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32+int64", "data": "synthetic",
+            "config": {"workload": "serving: " + WORKLOAD + "; Poisson streams of cube-window "
+                                   "join queries, window volume log-uniform in [1e-3, 1] of "
+                                   "the cube, 40 GiB admission budget, 4 serving streams",
+                       "rates_qps": rates, "alone_queries": n_alone},
+            "alone": alone, "per_rate": per_rate, "answers_identical_to_alone": identical,
+            "clocks": clk}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -502,7 +609,12 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--nuclei", type=int, default=10000)
     ap.add_argument("--vessels", type=int, default=500)
-    ap.add_argument("--workload", default="pathology", choices=["pathology", "batching", "urban"])
+    ap.add_argument("--workload", default="pathology",
+                    choices=["pathology", "batching", "urban", "serving"])
+    ap.add_argument("--rates", default="50,100,200,500,1000,2000")
+    ap.add_argument("--seconds-per-rate", type=float, default=2.0)
+    ap.add_argument("--max-queries", type=int, default=4000)
+    ap.add_argument("--alone-queries", type=int, default=400)
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -514,6 +626,8 @@ def main():
         run_batching(args)
     elif args.workload == "urban":
         run_urban(args)
+    elif args.workload == "serving":
+        run_serving(args)
     else:
         run_ours(args, rank, world, local_rank)
 

@@ -107,7 +107,8 @@ typedef struct {
   int32_t *pairs;           /* K x 2 (idA, idB), in candidate order: sorted
                                and unique when the candidates are            */
   int32_t on_device;        /* 1 if pairs is a device pointer                 */
-  int32_t reserved;
+  int32_t pairs_malloc;     /* 1 if pairs is plain malloc'd host memory
+                               (results of pj_poll); 0 otherwise             */
   int64_t n_candidates;     /* C: candidates refined                          */
   uint8_t *flags;           /* device, C bytes (only with keep_flags)         */
   float device_ms;          /* device time of the join, candidates to
@@ -319,6 +320,67 @@ pj_status pj_autotune(pj_ctx *ctx, pj_dataset a, pj_dataset b,
                       const int32_t *cand, int64_t n_cand, int32_t self_join,
                       const pj_tune_space *space, pj_join_opts *best,
                       pj_tune_entry *table, int32_t table_cap, int32_t *table_n);
+
+/* --------------------------------------------------------------------------
+ * Serving (the paper has no counterpart: it runs one join at a time, Sec. 4;
+ * this is the request loop around the same refinement)
+ *
+ * A query asks for the intersecting pairs among the meshes of datasets a and
+ * b whose closed bounding boxes meet a closed window box.  pj_submit queues
+ * it and returns at once; pj_poll collects the answer.  Queued queries are
+ * admitted oldest first while the device bytes of the admitted ones stay
+ * within pj_config.budget_bytes (0: 40 GiB), and a free serving stream
+ * (pj_config.serve_streams, 0: 4) takes every admissible queued query on the
+ * same datasets as one batch: the bounding-box filter over the queries'
+ * selections, one refinement of all their candidates, and a per-query split
+ * of the result.  Batches on different streams run concurrently.  A query's
+ * answer does not depend on what it was batched with.
+ *
+ * Both datasets need a BVH of the same shape (their last pj_build_bvh).  The
+ * first pj_submit on a context starts the serving threads and gives each its
+ * own stream and scratch (about 0.7 GB of device memory per stream, outside
+ * the budget).  pj_free_dataset answers PJ_ERR_BUSY while queries on the
+ * dataset have not been polled; pj_build_bvh and pj_autotune wait for the
+ * running batches.
+ * ------------------------------------------------------------------------ */
+
+typedef int64_t pj_ticket;
+
+typedef struct {
+  pj_dataset a, b;
+  int32_t self_join;        /* 1: a == b and only pairs idA < idB             */
+  int32_t window_lo[3];     /* closed window box, grid units                  */
+  int32_t window_hi[3];
+  int32_t reserved;
+} pj_query;
+
+/* Timings of one query (seconds on the host's steady clock) and its sizes. */
+typedef struct {
+  double t_submit;          /* pj_submit returned the ticket                  */
+  double t_admit;           /* taken into a batch                             */
+  double t_launch;          /* the batch's refinement was enqueued            */
+  double t_done;            /* the batch's results were on the host           */
+  int64_t n_a, n_b;         /* meshes selected by the window on each side     */
+  int64_t n_candidates;     /* pairs whose boxes meet                         */
+  int64_t n_pairs;          /* intersecting pairs                             */
+  int64_t device_bytes;     /* bytes admitted against the budget              */
+  int32_t batch_id;         /* batch the query ran in                         */
+  int32_t batch_queries;    /* queries in that batch                          */
+} pj_query_stats;
+
+/* Queue a query.  *out receives its ticket.  A query that needs more device
+ * bytes than the whole budget is refused with PJ_ERR_BUSY.  May be called
+ * from any thread. */
+pj_status pj_submit(pj_ctx *ctx, const pj_query *q, pj_ticket *out);
+
+/* Collect a query.  wait = 0: returns PJ_PENDING while it is not done;
+ * wait = 1: blocks until it is done, at most pj_config.wait_limit_us (0:
+ * 10 s; then PJ_ERR_TIMEOUT and the ticket stays valid).  When done, *out
+ * receives the pairs (host memory, sorted by (idA, idB); free with
+ * pj_free_pairs), stats (may be NULL) the timings, and the ticket is
+ * released.  May be called from any thread. */
+pj_status pj_poll(pj_ctx *ctx, pj_ticket ticket, int32_t wait, pj_pairs *out,
+                  pj_query_stats *stats);
 
 /* --------------------------------------------------------------------------
  * Counters and diagnostics

@@ -17,21 +17,51 @@
 
 namespace pj {
 
+thread_local Exec *t_exec = nullptr;
+
+// a serving thread keeps its own message; API calls set the context's
 pj_status fail(Ctx *c, pj_status code, const std::string &msg) {
-  if (c) c->err = msg;
+  if (t_exec) {
+    t_exec->err = msg;
+  } else if (c) {
+    std::lock_guard<std::mutex> lk(c->err_mu);
+    c->err = msg;
+  }
   return code;
+}
+
+void clear_err(Ctx *c) {
+  std::lock_guard<std::mutex> lk(c->err_mu);
+  c->err.clear();
 }
 
 pj_status cuda_fail(Ctx *c, cudaError_t e, const char *what) {
   std::string m = std::string("CUDA error ") + cudaGetErrorName(e) + " (" +
                   cudaGetErrorString(e) + ") in " + what;
-  if (c) c->err = m;
-  return e == cudaErrorMemoryAllocation ? PJ_ERR_NO_MEMORY : PJ_ERR_CUDA;
+  return fail(c, e == cudaErrorMemoryAllocation ? PJ_ERR_NO_MEMORY : PJ_ERR_CUDA, m);
+}
+
+pj_status exec_init(Ctx *ctx, Exec *e) {
+  cudaError_t r = cudaMalloc(&e->d_err, sizeof(int) * 4);
+  if (r == cudaSuccess) r = cudaMemset(e->d_err, 0, sizeof(int) * 4);
+  if (r == cudaSuccess) r = cudaMallocHost(&e->h_pinned, 4096);
+  if (r != cudaSuccess) return cuda_fail(ctx, r, "exec_init");
+  return PJ_OK;
+}
+
+void exec_free(Exec *e) {
+  for (auto &kv : e->ws) cudaFree(kv.second.ptr);
+  e->ws.clear();
+  cudaFree(e->d_err);
+  cudaFreeHost(e->h_pinned);
+  e->d_err = nullptr;
+  e->h_pinned = nullptr;
 }
 
 void *ws_get(Ctx *ctx, const char *name, size_t bytes, pj_status *st) {
   *st = PJ_OK;
-  Workspace &w = ctx->ws[name];
+  Exec *ex = cur_exec(ctx);
+  Workspace &w = ex->ws[name];
   if (bytes == 0) bytes = 16;
   if (w.cap >= bytes) return w.ptr;
   if (w.ptr) cudaFree(w.ptr);
@@ -46,9 +76,12 @@ void *ws_get(Ctx *ctx, const char *name, size_t bytes, pj_status *st) {
     return nullptr;
   }
   w.cap = want;
-  // workspaces back captured graphs: a new address invalidates them
-  for (auto &g : ctx->graphs) cudaGraphExecDestroy(g.second);
-  ctx->graphs.clear();
+  // workspaces back captured graphs: a new address invalidates them (only
+  // the context's own scratch is ever captured)
+  if (ex == &ctx->main) {
+    for (auto &g : ctx->graphs) cudaGraphExecDestroy(g.second);
+    ctx->graphs.clear();
+  }
   return w.ptr;
 }
 
@@ -368,6 +401,9 @@ static pj_status load_impl(Ctx *ctx, const float *xyz, int64_t V,
     return fail(ctx, PJ_ERR_NOT_MANIFOLD, buf);
   }
   d->E = (int64_t)hf[3];
+  d->h_aabb.resize(6 * (size_t)M);
+  if (M > 0)
+    PJ_CK(cudaMemcpy(d->h_aabb.data(), d->d_aabb, sizeof(float) * 6 * M, cudaMemcpyDeviceToHost));
   return PJ_OK;
 }
 
@@ -392,11 +428,9 @@ pj_status pj_create(const pj_config *cfg, pj_ctx **out) {
   if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&ctx->stream, cudaStreamNonBlocking);
   if (e == cudaSuccess) e = cudaMalloc(&ctx->d_counters, sizeof(unsigned long long) * C_NUM);
   if (e == cudaSuccess) e = cudaMemset(ctx->d_counters, 0, sizeof(unsigned long long) * C_NUM);
-  if (e == cudaSuccess) e = cudaMalloc(&ctx->d_err, sizeof(int) * 4);
-  if (e == cudaSuccess) e = cudaMemset(ctx->d_err, 0, sizeof(int) * 4);
-  if (e == cudaSuccess) e = cudaMallocHost(&ctx->h_pinned, 4096);
-  if (e != cudaSuccess) {
+  if (e != cudaSuccess || exec_init(ctx, &ctx->main) != PJ_OK) {
     cudaGetLastError();
+    exec_free(&ctx->main);
     delete ctx;
     return e == cudaErrorMemoryAllocation ? PJ_ERR_NO_MEMORY : PJ_ERR_CUDA;
   }
@@ -408,13 +442,12 @@ pj_status pj_destroy(pj_ctx *h) {
   Ctx *ctx = reinterpret_cast<Ctx *>(h);
   if (!ctx) return PJ_ERR_INVALID_ARG;
   cudaSetDevice(ctx->device);
+  serve_stop(ctx);
   cudaStreamSynchronize(ctx->stream);
   for (auto &kv : ctx->datasets) free_dataset(kv.second.get());
-  for (auto &kv : ctx->ws) cudaFree(kv.second.ptr);
   for (auto &g : ctx->graphs) cudaGraphExecDestroy(g.second);
+  exec_free(&ctx->main);
   cudaFree(ctx->d_counters);
-  cudaFree(ctx->d_err);
-  cudaFreeHost(ctx->h_pinned);
   cudaStreamDestroy(ctx->stream);
   delete ctx;
   return PJ_OK;
@@ -433,7 +466,7 @@ pj_status pj_load_meshes(pj_ctx *h, const float *xyz, int64_t n_verts,
   Ctx *ctx = reinterpret_cast<Ctx *>(h);
   if (!ctx || !out) return PJ_ERR_INVALID_ARG;
   std::lock_guard<std::mutex> lk(ctx->mu);
-  ctx->err.clear();
+  clear_err(ctx);
   if (n_verts < 0 || n_tris < 0) return fail(ctx, PJ_ERR_INVALID_ARG, "negative size");
   cudaSetDevice(ctx->device);
   std::unique_ptr<Dataset> d(new Dataset());
@@ -444,6 +477,7 @@ pj_status pj_load_meshes(pj_ctx *h, const float *xyz, int64_t n_verts,
     free_dataset(d.get());
     return st;
   }
+  std::unique_lock<std::shared_mutex> wl(ctx->ds_rw);
   int id = ctx->next_ds++;
   ctx->datasets[id] = std::move(d);
   *out = id;
@@ -459,8 +493,11 @@ pj_status pj_free_dataset(pj_ctx *h, pj_dataset id) {
   Ctx *ctx = reinterpret_cast<Ctx *>(h);
   if (!ctx) return PJ_ERR_INVALID_ARG;
   std::lock_guard<std::mutex> lk(ctx->mu);
+  std::unique_lock<std::shared_mutex> wl(ctx->ds_rw);
   Dataset *d = get_ds(ctx, id);
   if (!d) return fail(ctx, PJ_ERR_INVALID_ARG, "unknown dataset");
+  if (serve_uses(ctx, d))
+    return fail(ctx, PJ_ERR_BUSY, "serving queries on this dataset have not been polled yet");
   cudaSetDevice(ctx->device);
   cudaStreamSynchronize(ctx->stream);
   free_dataset(d);
@@ -474,7 +511,8 @@ pj_status pj_build_bvh(pj_ctx *h, pj_dataset id, const pj_bvh_params *p) {
   Ctx *ctx = reinterpret_cast<Ctx *>(h);
   if (!ctx) return PJ_ERR_INVALID_ARG;
   std::lock_guard<std::mutex> lk(ctx->mu);
-  ctx->err.clear();
+  std::unique_lock<std::shared_mutex> wl(ctx->ds_rw);
+  clear_err(ctx);
   Dataset *d = get_ds(ctx, id);
   if (!d) return fail(ctx, PJ_ERR_INVALID_ARG, "unknown dataset");
   int W = p && p->width ? p->width : 4, L = p && p->leaf_size ? p->leaf_size : 4;
@@ -528,7 +566,7 @@ pj_status pj_join_intersects_ex(pj_ctx *h, pj_dataset a, pj_dataset b,
   Ctx *ctx = reinterpret_cast<Ctx *>(h);
   if (!ctx || !out) return PJ_ERR_INVALID_ARG;
   std::lock_guard<std::mutex> lk(ctx->mu);
-  ctx->err.clear();
+  clear_err(ctx);
   memset(out, 0, sizeof(*out));
   Dataset *A = get_ds(ctx, a), *B = get_ds(ctx, b);
   if (!A || !B) return fail(ctx, PJ_ERR_INVALID_ARG, "unknown dataset");
@@ -548,12 +586,29 @@ pj_status pj_join_intersects_noalloc(pj_ctx *h, pj_dataset a, pj_dataset b,
   Ctx *ctx = reinterpret_cast<Ctx *>(h);
   if (!ctx) return PJ_ERR_INVALID_ARG;
   std::lock_guard<std::mutex> lk(ctx->mu);
-  ctx->err.clear();
+  clear_err(ctx);
   Dataset *A = get_ds(ctx, a), *B = get_ds(ctx, b);
   if (!A || !B) return fail(ctx, PJ_ERR_INVALID_ARG, "unknown dataset");
   cudaSetDevice(ctx->device);
   return run_join_noalloc(ctx, A, B, d_cand, n_cand, d_flags, d_pairs, d_count,
                           stream ? (cudaStream_t)stream : ctx->stream);
+}
+
+pj_status pj_submit(pj_ctx *h, const pj_query *q, pj_ticket *out) {
+  Ctx *ctx = reinterpret_cast<Ctx *>(h);
+  if (!ctx || !q || !out) return PJ_ERR_INVALID_ARG;
+  *out = 0;
+  std::shared_lock<std::shared_mutex> rl(ctx->ds_rw);
+  auto ia = ctx->datasets.find(q->a), ib = ctx->datasets.find(q->b);
+  if (ia == ctx->datasets.end() || ib == ctx->datasets.end()) return PJ_ERR_INVALID_ARG;
+  if (q->self_join && q->a != q->b) return PJ_ERR_INVALID_ARG;
+  return serve_submit(ctx, ia->second.get(), ib->second.get(), q, out);
+}
+
+pj_status pj_poll(pj_ctx *h, pj_ticket t, int32_t wait, pj_pairs *out, pj_query_stats *stats) {
+  Ctx *ctx = reinterpret_cast<Ctx *>(h);
+  if (!ctx || !out) return PJ_ERR_INVALID_ARG;
+  return serve_poll(ctx, t, wait, out, stats);
 }
 
 pj_status pj_free_pairs(pj_ctx *h, pj_pairs *res) {
@@ -562,7 +617,9 @@ pj_status pj_free_pairs(pj_ctx *h, pj_pairs *res) {
   std::lock_guard<std::mutex> lk(ctx->mu);
   cudaSetDevice(ctx->device);
   if (res->pairs) {
-    if (res->on_device) cudaFree(res->pairs); else cudaFreeHost(res->pairs);
+    if (res->on_device) cudaFree(res->pairs);
+    else if (res->pairs_malloc) free(res->pairs);
+    else cudaFreeHost(res->pairs);
   }
   if (res->flags) cudaFree(res->flags);
   if (res->cycles) cudaFree(res->cycles);
@@ -577,7 +634,8 @@ pj_status pj_autotune(pj_ctx *h, pj_dataset a, pj_dataset b, const int32_t *cand
   Ctx *ctx = reinterpret_cast<Ctx *>(h);
   if (!ctx || !space || !best) return PJ_ERR_INVALID_ARG;
   std::lock_guard<std::mutex> lk(ctx->mu);
-  ctx->err.clear();
+  std::unique_lock<std::shared_mutex> wl(ctx->ds_rw);
+  clear_err(ctx);
   Dataset *A = get_ds(ctx, a), *B = get_ds(ctx, b);
   if (!A || !B) return fail(ctx, PJ_ERR_INVALID_ARG, "unknown dataset");
   if (self_join && a != b) return fail(ctx, PJ_ERR_INVALID_ARG, "self_join needs a == b");
@@ -610,7 +668,7 @@ pj_status pj_get_counters(pj_ctx *h, pj_counters *out) {
   out->parity_tri_tests = c[C_PARITY_TRIS];
   out->bytes_fetched = c[C_BYTES];
   out->pairs_hit = c[C_HITS];
-  out->kernel_launches = ctx->launches;
+  out->kernel_launches = ctx->launches.load();
   out->tasks_spilled = c[C_SPILLED];
   out->tasks_resumed = c[C_TASKS];
   out->bytes_tasks = c[C_BYTES_TASKS];
@@ -633,7 +691,7 @@ pj_status pj_segtri_batch(pj_ctx *h, const float *pq, const float *abc, int64_t 
   if (!ctx || n < 0 || (n > 0 && (!pq || !abc || !res))) return PJ_ERR_INVALID_ARG;
   if (mode != PJ_LEAF_FILTERED && mode != PJ_LEAF_EXACT) return PJ_ERR_INVALID_ARG;
   std::lock_guard<std::mutex> lk(ctx->mu);
-  ctx->err.clear();
+  clear_err(ctx);
   cudaSetDevice(ctx->device);
   return run_segtri_batch(ctx, pq, abc, n, mode, res, n_fallback,
                           stream ? (cudaStream_t)stream : ctx->stream);

@@ -3,9 +3,11 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <atomic>
 #include <map>
 #include <memory>
 #include <mutex>
+#include <shared_mutex>
 #include <string>
 #include <utility>
 #include <vector>
@@ -58,6 +60,7 @@ struct Dataset {
   int64_t *d_toff = nullptr;    // M + 1
   std::vector<int64_t> h_voff, h_toff;
   float *d_aabb = nullptr;      // M * 6
+  std::vector<float> h_aabb;    // M * 6, host copy (serving window selection)
   int32_t *d_lexorder = nullptr;  // V: global vertex ids, per mesh in (x,y,z) order
   uint8_t *d_emask = nullptr;   // F: owned-edge bits
   std::map<std::pair<int, int>, Bvh> bvhs;
@@ -77,29 +80,56 @@ struct Workspace {
   size_t cap = 0;
 };
 
+// Scratch of one join in flight: workspaces (grown on demand), the device
+// error words and a small pinned host buffer.  The context owns one for its
+// API calls; each serving stream has its own.
+struct Exec {
+  std::map<std::string, Workspace> ws;
+  int *d_err = nullptr;      // 4 device error words
+  void *h_pinned = nullptr;  // 4 KiB pinned host scratch
+  std::string err;           // last failure message of a serving thread
+  bool borrow_out = false;   // join results stay in the workspaces (serving)
+};
+
+struct Serve;  // serving state (pj_serve.cu)
+
 struct Ctx {
   int device = 0;
   int num_sms = 0;
   cudaStream_t stream = nullptr;
   std::mutex mu;
+  std::mutex err_mu;  // guards err (pj_submit / pj_poll fail outside `mu`)
   std::string err;
   std::map<int, std::unique_ptr<Dataset>> datasets;
   int next_ds = 1;
   unsigned long long *d_counters = nullptr;  // C_NUM
-  int *d_err = nullptr;                      // device error word
-  // query workspaces (grown on demand)
-  std::map<std::string, Workspace> ws;
-  void *h_pinned = nullptr;                  // small pinned scratch (counts)
+  Exec main;                                 // scratch of the API calls
   pj_config cfg{};
   // captured graphs keyed by a shape string, with their kernel counts
   std::map<std::string, cudaGraphExec_t> graphs;
   std::map<std::string, unsigned long long> graph_kernels;
-  unsigned long long launches = 0;           // kernels launched by joins
+  std::atomic<unsigned long long> launches{0};  // kernels launched by joins
+  // datasets and their BVHs: serving threads read them under a shared lock,
+  // API calls that add or remove one take it exclusively (after `mu`)
+  std::shared_mutex ds_rw;
+  Serve *serve = nullptr;
 };
+
+// The scratch the calling thread works with: a serving thread's own, else
+// the context's.
+extern thread_local Exec *t_exec;
+inline Exec *cur_exec(Ctx *c) { return t_exec ? t_exec : &c->main; }
+pj_status exec_init(Ctx *ctx, Exec *e);
+void exec_free(Exec *e);
+void serve_stop(Ctx *ctx);
+pj_status serve_submit(Ctx *ctx, Dataset *A, Dataset *B, const pj_query *q, pj_ticket *out);
+pj_status serve_poll(Ctx *ctx, pj_ticket t, int wait, pj_pairs *out, pj_query_stats *stats);
+bool serve_uses(Ctx *ctx, const Dataset *d);  // pending or running queries on d
 
 // set ctx->err and return code
 pj_status fail(Ctx *c, pj_status code, const std::string &msg);
 pj_status cuda_fail(Ctx *c, cudaError_t e, const char *what);
+void clear_err(Ctx *c);
 void *ws_get(Ctx *c, const char *name, size_t bytes, pj_status *st);
 
 #define PJ_CK(call)                                   \

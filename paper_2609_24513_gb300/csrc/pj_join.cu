@@ -1503,7 +1503,8 @@ pj_status run_join(Ctx *ctx, Dataset *A, Dataset *B, const int32_t *cand,
   // [0] n_cand, [1] K, [2] work counter, [3..4] spill queue counters, [5..7] wave counters
   int64_t *d_misc = (int64_t *)ws_get(ctx, "misc", 64, &st);
   if (!d_misc) return st;
-  int64_t *h_misc = (int64_t *)ctx->h_pinned;
+  int64_t *h_misc = (int64_t *)cur_exec(ctx)->h_pinned;
+  int *d_err = cur_exec(ctx)->d_err;
 
   // events: 0 start, 1 candidates ready, 2 refinement done, 3 end,
   // 4 parity done, 5 front end done (wavefront path, not in graph replays)
@@ -1524,7 +1525,7 @@ pj_status run_join(Ctx *ctx, Dataset *A, Dataset *B, const int32_t *cand,
     PJ_CK(cudaStreamWaitEvent(ctx->stream, ev[0], 0));
     s = ctx->stream;
   }
-  PJ_CK(cudaMemsetAsync(ctx->d_err, 0, sizeof(int) * 4, s));
+  PJ_CK(cudaMemsetAsync(d_err, 0, sizeof(int) * 4, s));
   PJ_CK(cudaEventRecord(e0, s));
 
   // 1. candidates
@@ -1572,7 +1573,7 @@ pj_status run_join(Ctx *ctx, Dataset *A, Dataset *B, const int32_t *cand,
     PJ_CK(cudaMemcpyAsync(d_misc, h_misc, 8, cudaMemcpyHostToDevice, s));
     if (C > 0)
       k_check_cand<<<std::min(blocks_for(C, 256), ctx->num_sms * 8), 256, 0, s>>>(
-          d_cand, d_off, C, A->M, B->M, B->d_aabb, ctx->d_err);
+          d_cand, d_off, C, A->M, B->M, B->d_aabb, d_err);
     if (C > 0) ++ctx->launches;
   }
   uint8_t *d_flags = (uint8_t *)ws_get(ctx, "flags", (size_t)std::max<int64_t>(C, 1), &st);
@@ -1644,7 +1645,7 @@ pj_status run_join(Ctx *ctx, Dataset *A, Dataset *B, const int32_t *cand,
   args.flags = d_flags;
   args.work = (unsigned long long *)(d_misc + 2);
   args.counters = ctx->d_counters;
-  args.err = ctx->d_err;
+  args.err = d_err;
   args.stack_cap = stack_cap;
   args.max_pop = 32;
   args.warps_per_pair = k;
@@ -1699,7 +1700,7 @@ pj_status run_join(Ctx *ctx, Dataset *A, Dataset *B, const int32_t *cand,
         wa.n_cand = d_misc;
         wa.flags = d_flags;
         wa.counters = ctx->d_counters;
-        wa.err = ctx->d_err;
+        wa.err = d_err;
         wa.q_cap = wq_cap;
         wa.MA = A->M;
         wa.MB = B->M;
@@ -1827,7 +1828,7 @@ pj_status run_join(Ctx *ctx, Dataset *A, Dataset *B, const int32_t *cand,
   PJ_CK(cudaEventRecord(e1, s));
   PJ_CK(cudaMemcpyAsync(h_misc + 1, d_misc + 1, 8, cudaMemcpyDeviceToHost, s));
   int herr[4];
-  PJ_CK(cudaMemcpyAsync(herr, ctx->d_err, sizeof(herr), cudaMemcpyDeviceToHost, s));
+  PJ_CK(cudaMemcpyAsync(herr, d_err, sizeof(herr), cudaMemcpyDeviceToHost, s));
   PJ_CK(cudaStreamSynchronize(s));
   if (herr[1]) return fail(ctx, PJ_ERR_INVALID_ARG, "a candidate mesh id is out of range");
   if (herr[2]) return fail(ctx, PJ_ERR_INVALID_ARG, "a translated candidate mesh leaves the 2^18 grid");
@@ -1838,11 +1839,11 @@ pj_status run_join(Ctx *ctx, Dataset *A, Dataset *B, const int32_t *cand,
     args.max_pop = 1;
     budget1 = 0;
     wave_levels = 0;
-    PJ_CK(cudaMemsetAsync(ctx->d_err, 0, sizeof(int) * 4, s));
+    PJ_CK(cudaMemsetAsync(d_err, 0, sizeof(int) * 4, s));
     if ((st = device_part(true)) != PJ_OK) return st;
     PJ_CK(cudaEventRecord(e1, s));
     PJ_CK(cudaMemcpyAsync(h_misc + 1, d_misc + 1, 8, cudaMemcpyDeviceToHost, s));
-    PJ_CK(cudaMemcpyAsync(herr, ctx->d_err, sizeof(herr), cudaMemcpyDeviceToHost, s));
+    PJ_CK(cudaMemcpyAsync(herr, d_err, sizeof(herr), cudaMemcpyDeviceToHost, s));
     PJ_CK(cudaStreamSynchronize(s));
     replayed = false;
   }
@@ -1869,6 +1870,14 @@ pj_status run_join(Ctx *ctx, Dataset *A, Dataset *B, const int32_t *cand,
   out->count = K;
   out->n_candidates = C;
   out->device_ms = ms;
+  if (cur_exec(ctx)->borrow_out) {
+    // serving: the caller reads the result from this slot's workspaces
+    // before its next join (the stream is synchronised above)
+    out->pairs = d_pairs;
+    out->flags = d_flags;
+    out->on_device = 1;
+    return PJ_OK;
+  }
   size_t bytes = sizeof(int32_t) * 2 * (size_t)std::max<int64_t>(K, 1);
   if (o->out_host) {
     PJ_CK(cudaMallocHost((void **)&out->pairs, bytes));

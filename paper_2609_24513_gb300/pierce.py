@@ -53,7 +53,7 @@ class pj_join_opts(ctypes.Structure):
 
 class pj_pairs(ctypes.Structure):
     _fields_ = [("count", ctypes.c_int64), ("pairs", ctypes.POINTER(ctypes.c_int32)),
-                ("on_device", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("on_device", ctypes.c_int32), ("pairs_malloc", ctypes.c_int32),
                 ("n_candidates", ctypes.c_int64), ("flags", ctypes.c_void_p),
                 ("device_ms", ctypes.c_float), ("mbb_ms", ctypes.c_float),
                 ("refine_ms", ctypes.c_float), ("compact_ms", ctypes.c_float),
@@ -93,6 +93,21 @@ class pj_tune_entry(ctypes.Structure):
                 ("ms", ctypes.c_float), ("reserved", ctypes.c_float)]
 
 
+class pj_query(ctypes.Structure):
+    _fields_ = [("a", ctypes.c_int32), ("b", ctypes.c_int32), ("self_join", ctypes.c_int32),
+                ("window_lo", ctypes.c_int32 * 3), ("window_hi", ctypes.c_int32 * 3),
+                ("reserved", ctypes.c_int32)]
+
+
+class pj_query_stats(ctypes.Structure):
+    _fields_ = [("t_submit", ctypes.c_double), ("t_admit", ctypes.c_double),
+                ("t_launch", ctypes.c_double), ("t_done", ctypes.c_double),
+                ("n_a", ctypes.c_int64), ("n_b", ctypes.c_int64),
+                ("n_candidates", ctypes.c_int64), ("n_pairs", ctypes.c_int64),
+                ("device_bytes", ctypes.c_int64), ("batch_id", ctypes.c_int32),
+                ("batch_queries", ctypes.c_int32)]
+
+
 _vp = ctypes.c_void_p
 _i64 = ctypes.c_int64
 _i32 = ctypes.c_int32
@@ -117,6 +132,9 @@ SIGNATURES = {
     "pj_autotune": (_i32, [_vp, _i32, _i32, _vp, _i64, _i32, ctypes.POINTER(pj_tune_space),
                            ctypes.POINTER(pj_join_opts), ctypes.POINTER(pj_tune_entry), _i32,
                            ctypes.POINTER(_i32)]),
+    "pj_submit": (_i32, [_vp, ctypes.POINTER(pj_query), ctypes.POINTER(_i64)]),
+    "pj_poll": (_i32, [_vp, _i64, _i32, ctypes.POINTER(pj_pairs),
+                       ctypes.POINTER(pj_query_stats)]),
     "pj_get_counters": (_i32, [_vp, ctypes.POINTER(pj_counters)]),
     "pj_reset_counters": (_i32, [_vp]),
     "pj_segtri_batch": (_i32, [_vp, _vp, _vp, _i64, _i32, _vp, ctypes.POINTER(_i64), _vp]),
@@ -325,6 +343,31 @@ def pj_autotune(ctx, a: int, b: int, cand=None, self_join=False, widths=(2, 4, 8
     return best_d, rows
 
 
+def pj_submit(ctx, a: int, b: int, window_lo, window_hi, self_join=False) -> int:
+    """Queue a window join query; returns its ticket."""
+    q = pj_query(a, b, int(self_join), (ctypes.c_int32 * 3)(*[int(v) for v in window_lo]),
+                 (ctypes.c_int32 * 3)(*[int(v) for v in window_hi]), 0)
+    t = _i64()
+    _check(ctx, load().pj_submit(ctx, ctypes.byref(q), ctypes.byref(t)))
+    return t.value
+
+
+def pj_poll(ctx, ticket: int, wait=True):
+    """None while the query is pending (wait=False); else (pairs K x 2 numpy,
+    stats dict)."""
+    res = pj_pairs()
+    st = pj_query_stats()
+    rc = load().pj_poll(ctx, int(ticket), int(bool(wait)), ctypes.byref(res), ctypes.byref(st))
+    if rc == PJ_PENDING:
+        return None
+    _check(ctx, rc)
+    try:
+        pairs = pairs_to_numpy(res)
+    finally:
+        pj_free_pairs(ctx, res)
+    return pairs, {f: getattr(st, f) for f, _ in pj_query_stats._fields_}
+
+
 def pj_get_counters(ctx) -> dict:
     c = pj_counters()
     _check(ctx, load().pj_get_counters(ctx, ctypes.byref(c)))
@@ -439,6 +482,12 @@ class Context:
         finally:
             pj_free_pairs(self.h, res)
         return pairs, info
+
+    def submit(self, a: int, b: int, window_lo, window_hi, self_join=False) -> int:
+        return pj_submit(self.h, a, b, window_lo, window_hi, self_join)
+
+    def poll(self, ticket: int, wait=True):
+        return pj_poll(self.h, ticket, wait)
 
     def counters(self) -> dict:
         return pj_get_counters(self.h)

@@ -417,6 +417,48 @@ def sample_indices(seed: int, n: int, k: int) -> np.ndarray:
     return np.sort(rng.choice(n, size=k, replace=False)) if k else np.zeros(0, np.int64)
 
 
+def mesh_boxes(ds: MeshSet) -> np.ndarray:
+    """M x 6 float32 (lo x, y, z, hi x, y, z) of each mesh's vertices."""
+    out = np.zeros((ds.nmesh, 6), dtype=np.float32)
+    for k in range(ds.nmesh):
+        v = ds.xyz[ds.voff[k]:ds.voff[k + 1]]
+        out[k, :3], out[k, 3:] = v.min(0), v.max(0)
+    return out
+
+
+def windows(seed: int, n: int, half_range=(1 << 10, 1 << 16)):
+    """n query windows on the grid: centres uniform, half-sizes log-uniform in
+    half_range (grid units), clipped to the grid.  Returns (lo, hi), n x 3
+    int32 each."""
+    rng = np.random.default_rng(seed)
+    c = rng.integers(0, GRID, size=(n, 3))
+    h = np.exp(rng.uniform(np.log(half_range[0]), np.log(half_range[1]), size=(n, 3)))
+    lo = np.clip(c - h, 0, QMAX).astype(np.int32)
+    hi = np.clip(c + h, 0, QMAX).astype(np.int32)
+    return lo, hi
+
+
+def serving_windows(seed: int, n: int, frac_range=(1e-3, 1.0)):
+    """n cube windows whose volume, as a fraction of the grid cube, is
+    log-uniform in frac_range, placed uniformly inside the grid.  Over a
+    dataset spread through the cube, a window selects about that fraction
+    of its meshes (10 to 10,000 of 10,000 nuclei for the default range).
+    Returns (lo, hi), n x 3 int32 each."""
+    rng = np.random.default_rng(seed)
+    f = np.exp(rng.uniform(np.log(frac_range[0]), np.log(frac_range[1]), size=n))
+    side = np.minimum(np.cbrt(f) * QMAX, QMAX)
+    lo = rng.uniform(0, 1, size=(n, 3)) * (QMAX - side)[:, None]
+    lo = np.floor(lo).astype(np.int64)
+    hi = np.minimum(lo + np.ceil(side)[:, None].astype(np.int64), QMAX)
+    return lo.astype(np.int32), hi.astype(np.int32)
+
+
+def poisson_arrivals(seed: int, rate: float, n: int) -> np.ndarray:
+    """n arrival times (seconds from 0) of a Poisson stream of the given rate."""
+    rng = np.random.default_rng(seed)
+    return np.cumsum(rng.exponential(1.0 / rate, size=n))
+
+
 # ---------------------------------------------------------------------------
 # Batching workload: many candidate pairs of very uneven size, built from a
 # pool of template meshes placed by per-pair integer translations

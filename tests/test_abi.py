@@ -44,6 +44,41 @@ def test_struct_sizes_match_header_layout():
     assert ctypes.sizeof(pierce.pj_join_opts) == 48
     assert ctypes.sizeof(pierce.pj_pairs) == 88
     assert ctypes.sizeof(pierce.pj_counters) == 16 * 8
+    assert ctypes.sizeof(pierce.pj_query) == 40
+    assert ctypes.sizeof(pierce.pj_query_stats) == 80
+
+
+_STRUCTS = ("pj_config", "pj_bvh_params", "pj_join_opts", "pj_pairs", "pj_counters",
+            "pj_dataset_info", "pj_tune_space", "pj_tune_entry", "pj_query", "pj_query_stats")
+
+
+def test_struct_layout_matches_the_c_compiler(tmp_path):
+    """Every struct's size and every field's offset as gcc lays out the
+    header, against the ctypes mirror."""
+    import shutil
+    import subprocess
+    gcc = shutil.which("gcc")
+    if gcc is None:
+        pytest.skip("no gcc")
+    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "pierce.h"',
+             'int main(void) {']
+    for st in _STRUCTS:
+        lines.append('printf("%s %%zu\\n", sizeof(%s));' % (st, st))
+        for f, _ in getattr(pierce, st)._fields_:
+            lines.append('printf("%s.%s %%zu\\n", offsetof(%s, %s));' % (st, f, st, f))
+    lines.append("return 0; }")
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines))
+    exe = tmp_path / "layout"
+    subprocess.run([gcc, "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)],
+                   check=True)
+    out = dict(l.split() for l in subprocess.run([str(exe)], capture_output=True, text=True,
+                                                  check=True).stdout.splitlines())
+    for st in _STRUCTS:
+        cls = getattr(pierce, st)
+        assert int(out[st]) == ctypes.sizeof(cls), st
+        for f, _ in cls._fields_:
+            assert int(out["%s.%s" % (st, f)]) == getattr(cls, f).offset, (st, f)
 
 
 def test_no_cpu_fallback_when_library_missing(monkeypatch, tmp_path):
