@@ -129,6 +129,28 @@ __global__ void k_convert_tris(const int32_t *tris_local, int64_t F,
 }
 
 // one block per mesh: closed bounding box of its vertices
+// per-mesh record (see Dataset::d_mrec); runs after the boxes and the
+// lexicographic order exist
+__global__ void k_mesh_rec(const float *aabb, const float *xyz, const int32_t *lexorder,
+                           const int64_t *voff, const int64_t *toff, int64_t M, float4 *rec) {
+  for (int64_t m = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; m < M;
+       m += (int64_t)gridDim.x * blockDim.x) {
+    const float *b = aabb + 6 * m;
+    const int64_t v0 = voff[m], nv = voff[m + 1] - v0;
+    float x = 0.f, y = 0.f, z = 0.f;
+    if (nv > 0) {
+      const int64_t g = lexorder[v0];
+      x = xyz[3 * g];
+      y = xyz[3 * g + 1];
+      z = xyz[3 * g + 2];
+    }
+    rec[3 * m] = make_float4(b[0], b[1], b[2], x);
+    rec[3 * m + 1] = make_float4(b[3], b[4], b[5], y);
+    rec[3 * m + 2] = make_float4(z, __int_as_float((int)toff[m]), __int_as_float((int)v0),
+                                 __int_as_float((int)nv));
+  }
+}
+
 __global__ void k_mesh_aabb(const float *xyz, const int64_t *voff, int64_t M,
                             float *aabb) {
   __shared__ float red[6][32];
@@ -254,6 +276,7 @@ static void free_dataset(Dataset *d) {
   cudaFree(d->d_aabb);
   cudaFree(d->d_lexorder);
   cudaFree(d->d_emask);
+  cudaFree(d->d_mrec);
 }
 
 // RAII for temporary device buffers of the load pipeline
@@ -301,7 +324,8 @@ static pj_status load_impl(Ctx *ctx, const float *xyz, int64_t V,
   PJ_CK(dalloc(&d->d_aabb, 6 * M));
   PJ_CK(dalloc(&d->d_lexorder, V));
   PJ_CK(dalloc(&d->d_emask, F));
-  d->bytes = 12 * V + 12 * F + 16 * (M + 1) + 24 * M + 4 * V + F;
+  PJ_CK(dalloc(&d->d_mrec, 3 * M));
+  d->bytes = 12 * V + 12 * F + 16 * (M + 1) + 24 * M + 4 * V + F + 48 * M;
 
   Tmp tmp;
   int32_t *tris_local = nullptr;
@@ -387,6 +411,11 @@ static pj_status load_impl(Ctx *ctx, const float *xyz, int64_t V,
     // mesh ids in the xyz-sorted order
     k_gather_u32<<<nblk(ctx, V), 256, 0, s>>>(km, ids2, km2, V);
     PJ_CK(cub::DeviceRadixSort::SortPairs(tstore, tb2, km2, km, ids2, d->d_lexorder, (int)V, 0, 32, s));
+    PJ_CK(cudaGetLastError());
+  }
+  if (M > 0) {
+    k_mesh_rec<<<nblk(ctx, M), 256, 0, s>>>(d->d_aabb, d->d_xyz, d->d_lexorder, d->d_voff,
+                                            d->d_toff, M, d->d_mrec);
     PJ_CK(cudaGetLastError());
   }
   PJ_CK(cudaMemcpyAsync(hf, d_flags, sizeof(hf), cudaMemcpyDeviceToHost, s));

@@ -63,6 +63,11 @@ struct Dataset {
   std::vector<float> h_aabb;    // M * 6, host copy (serving window selection)
   int32_t *d_lexorder = nullptr;  // V: global vertex ids, per mesh in (x,y,z) order
   uint8_t *d_emask = nullptr;   // F: owned-edge bits
+  // per-mesh record, three float4 (48 B), so that a kernel reaches a mesh's
+  // box, first lexicographic vertex and offsets in one aligned fetch:
+  //   (lo x y z, v0 x)  (hi x y z, v0 y)  (v0 z, first triangle, first vertex,
+  //   vertex count) -- the last three as int bits
+  float4 *d_mrec = nullptr;     // M * 3
   std::map<std::pair<int, int>, Bvh> bvhs;
   std::pair<int, int> last_bvh{0, 0};
   int64_t bytes = 0;

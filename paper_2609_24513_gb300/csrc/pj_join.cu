@@ -28,6 +28,34 @@ namespace pj {
 
 constexpr unsigned FULL = 0xffffffffu;
 
+// Programmatic dependent launch (sm_90 and later): a kernel launched with
+// launch_pdl may be scheduled while the previous kernel on the stream is
+// still draining.  Every kernel of the join calls pdl_wait() before its
+// first access to memory that an earlier kernel wrote (it returns once that
+// kernel has completed and its writes are visible; without the launch
+// attribute it returns at once), then pdl_trigger() to let the next kernel
+// be scheduled as this one's blocks retire.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_trigger() {
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+
+template <typename... KArgs, typename... Args>
+static cudaError_t launch_pdl(void (*kern)(KArgs...), int grid, int block, size_t smem,
+                              cudaStream_t s, Args... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)grid);
+  cfg.blockDim = dim3((unsigned)block);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, kern, static_cast<KArgs>(args)...);
+}
+
 // ---------------------------------------------------------------------------
 // Exclusive scan of int64 (three-phase: block scan, scan of block sums, add)
 // ---------------------------------------------------------------------------
@@ -61,6 +89,8 @@ __device__ __forceinline__ int64_t block_excl_scan(int64_t v, int64_t *total) {
 }
 
 __global__ void k_scan_blocks(const int64_t *in, int64_t *out, int64_t n, int64_t *bsum) {
+  pdl_wait();
+  pdl_trigger();
   int64_t i = blockIdx.x * (int64_t)SCAN_T + threadIdx.x;
   int64_t v = i < n ? in[i] : 0;
   int64_t tot;
@@ -70,16 +100,49 @@ __global__ void k_scan_blocks(const int64_t *in, int64_t *out, int64_t n, int64_
 }
 
 __global__ void k_scan_add(int64_t *out, int64_t n, const int64_t *boff) {
+  pdl_wait();
+  pdl_trigger();
   int64_t i = blockIdx.x * (int64_t)SCAN_T + threadIdx.x;
   if (i < n) out[i] += boff[blockIdx.x];
 }
 
 __global__ void k_scan_total(const int64_t *in, const int64_t *out, int64_t n, int64_t *total) {
+  pdl_wait();
+  pdl_trigger();
   *total = n > 0 ? out[n - 1] + in[n - 1] : 0;
+}
+
+// One block scans up to SCAN_T * SCAN_SMALL values: each thread sums a run
+// of consecutive values, the block scans the run sums, each thread writes its
+// run's exclusive prefixes; thread 0 also writes the total.
+constexpr int SCAN_SMALL = 32;
+
+__global__ void __launch_bounds__(SCAN_T) k_scan_small(const int64_t *in, int64_t *out, int64_t n,
+                                                       int64_t *total) {
+  pdl_wait();
+  pdl_trigger();
+  const int64_t per = (n + SCAN_T - 1) / SCAN_T;
+  const int64_t b = threadIdx.x * per, e = min(n, b + per);
+  int64_t sum = 0;
+  for (int64_t i = b; i < e; ++i) sum += in[i];
+  int64_t tot;
+  int64_t run = block_excl_scan(sum, &tot);
+  for (int64_t i = b; i < e; ++i) {
+    const int64_t v = in[i];
+    out[i] = run;
+    run += v;
+  }
+  if (threadIdx.x == 0) *total = tot;
 }
 
 pj_status scan_i64(Ctx *ctx, const int64_t *d_in, int64_t *d_out, int64_t n,
                    int64_t *d_total, cudaStream_t s) {
+  if (n <= (int64_t)SCAN_T * SCAN_SMALL) {
+    cudaError_t e = launch_pdl(k_scan_small, 1, SCAN_T, 0, s, d_in, d_out, n, d_total);
+    ++ctx->launches;
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "scan");
+    return PJ_OK;
+  }
   // level buffers: block sums and their scans
   std::vector<int64_t> sizes;
   int64_t m = n;
@@ -143,6 +206,8 @@ __global__ void __launch_bounds__(MBB_T) k_mbb(const float *aabbA, int64_t MA,
                                               const float *aabbB, int64_t MB, int self_join,
                                               int64_t *counts, const int64_t *offsets,
                                               int32_t *cand) {
+  pdl_wait();
+  pdl_trigger();
   const int lane = threadIdx.x & 31;
   const int64_t warps = (int64_t)gridDim.x * (MBB_T / 32);
   for (int64_t i = blockIdx.x * (int64_t)(MBB_T / 32) + (threadIdx.x >> 5); i < MA; i += warps) {
@@ -175,6 +240,8 @@ __global__ void __launch_bounds__(MBB_T) k_mbb(const float *aabbA, int64_t MA,
 // ---------------------------------------------------------------------------
 __global__ void k_check_cand(const int32_t *cand, const int32_t *off, int64_t n,
                              int64_t MA, int64_t MB, const float *aabbB, int *err) {
+  pdl_wait();
+  pdl_trigger();
   for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < n;
        c += (int64_t)gridDim.x * blockDim.x) {
     int a = cand[2 * c], b = cand[2 * c + 1];
@@ -204,6 +271,7 @@ struct Side {
   const float *aabb;
   const float *xyz;
   const int32_t *lexorder;
+  const float4 *mrec;        // per-mesh record: box, first lexicographic vertex, offsets
 };
 
 struct RefineArgs {
@@ -230,6 +298,11 @@ struct RefineArgs {
   const unsigned int *q_in_n;
   unsigned int *q_in_pos;
   unsigned int q_in_cap;
+  // parity rays handed over by the per-thread parity kernel (pass 1 only)
+  const uint4 *q_par;
+  const unsigned int *q_par_n;
+  unsigned int *q_par_pos;
+  unsigned int q_par_cap;
 };
 
 struct Cnt {
@@ -370,6 +443,25 @@ __device__ __forceinline__ void load_tri(const float4 *rec, int64_t s, F3 off, F
   b = add(mkf3(r0.w, r1.x, r1.y), off);
   c = add(mkf3(r1.z, r1.w, r2.x), off);
   own = __float_as_int(r2.y);
+}
+
+// element t of a small register array without dynamic indexing (which would
+// move the array to local memory)
+template <int N>
+__device__ __forceinline__ F3 sel_f3(const F3 (&a)[N], int t) {
+  F3 r = a[0];
+#pragma unroll
+  for (int k = 1; k < N; ++k)
+    if (t == k) r = a[k];
+  return r;
+}
+template <int N>
+__device__ __forceinline__ uint32_t sel_u32(const uint32_t (&a)[N], int t) {
+  uint32_t r = a[0];
+#pragma unroll
+  for (int k = 1; k < N; ++k)
+    if (t == k) r = a[k];
+  return r;
 }
 
 // warp-wide inclusive scan of small ints
@@ -784,6 +876,8 @@ __device__ __forceinline__ void bar_group(int id, int nthreads) {
 
 template <int W, bool EXACT>
 __global__ void __launch_bounds__(128, 4) k_refine(RefineArgs P) {
+  pdl_wait();
+  pdl_trigger();
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ int group_flag[4];
   __shared__ long long group_cand[4];
@@ -910,7 +1004,11 @@ struct WaveArgs {
   unsigned long long *counters;
   int *err;
   unsigned int q_cap;
+  int lshift;                // log2 of the leaf size L: 2L threads per leaf pair
   int64_t MA, MB;
+  uint4 *q_par;              // parity rays over the per-thread node budget
+  unsigned int *q_par_n;
+  unsigned int q_par_cap;
 };
 
 __device__ __forceinline__ F3 cand_offset(const WaveArgs &P, int64_t c) {
@@ -932,6 +1030,63 @@ __device__ __forceinline__ unsigned warp_append(unsigned *ctr, unsigned cnt, int
   return base + incl - cnt;
 }
 
+// Block-aggregated append of two per-thread counts to two queues (one atomic
+// per queue and block instead of one per warp: the queue counters are single
+// addresses that every block hits).  Every thread of the block calls it with
+// block-uniform control flow.  Per-thread counts are below 2^16 / blockDim.x.
+// Returns this thread's first index in each queue.
+__device__ __forceinline__ uint2 block_append2(unsigned *ctr0, unsigned cnt0, unsigned *ctr1,
+                                               unsigned cnt1) {
+  __shared__ unsigned s_off[32];
+  __shared__ unsigned s_base[2];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  const unsigned mine = cnt0 | (cnt1 << 16);
+  unsigned incl = mine;
+  for (int o = 1; o < 32; o <<= 1) {
+    const unsigned t = __shfl_up_sync(FULL, incl, o);
+    if (lane >= o) incl += t;
+  }
+  if (lane == 31) s_off[w] = incl;
+  __syncthreads();
+  if (w == 0) {
+    const unsigned v = lane < nw ? s_off[lane] : 0u;
+    unsigned inc = v;
+    for (int o = 1; o < 32; o <<= 1) {
+      const unsigned t = __shfl_up_sync(FULL, inc, o);
+      if (lane >= o) inc += t;
+    }
+    s_off[lane] = inc - v;
+    const unsigned tot = __shfl_sync(FULL, inc, 31);
+    if (lane == 0) s_base[0] = (tot & 0xFFFFu) ? atomicAdd(ctr0, tot & 0xFFFFu) : 0u;
+    if (lane == 1) s_base[1] = (tot >> 16) ? atomicAdd(ctr1, tot >> 16) : 0u;
+  }
+  __syncthreads();
+  const unsigned ex = s_off[w] + incl - mine;
+  const uint2 r = make_uint2(s_base[0] + (ex & 0xFFFFu), s_base[1] + (ex >> 16));
+  __syncthreads();  // s_off / s_base are reused by the next call
+  return r;
+}
+
+// Sum N per-thread counter values over the block and add them to the device
+// counters `slot[i]`: one atomic per block and counter.  Every thread of the
+// block calls it.
+template <int N>
+__device__ __forceinline__ void block_flush(unsigned long long *dst, const int (&slot)[N],
+                                            const unsigned long long (&v)[N]) {
+  __shared__ unsigned long long s_sum[N];
+  __syncwarp();
+  if (threadIdx.x < N) s_sum[threadIdx.x] = 0ull;
+  __syncthreads();
+  const int lane = threadIdx.x & 31;
+  for (int i = 0; i < N; ++i) {
+    unsigned long long x = v[i];
+    for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(FULL, x, o);
+    if (lane == 0 && x) atomicAdd(&s_sum[i], x);
+  }
+  __syncthreads();
+  if (threadIdx.x < N && s_sum[threadIdx.x]) atomicAdd(dst + slot[threadIdx.x], s_sum[threadIdx.x]);
+}
+
 __device__ __forceinline__ void flush_counters(unsigned long long *dst, const unsigned long long *v,
                                                int lane, int n) {
   for (int i = 0; i < n; ++i) {
@@ -943,10 +1098,14 @@ __device__ __forceinline__ void flush_counters(unsigned long long *dst, const un
 
 // root task of every candidate whose mesh boxes meet
 __global__ void k_wave_init(WaveArgs P, uint4 *q, unsigned *q_n) {
-  const int lane = threadIdx.x & 31;
+  pdl_wait();
+  pdl_trigger();
   const int64_t n = *P.n_cand;
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g - lane < n; g += stride) {
+  if (blockIdx.x == 0 && threadIdx.x == 0 && n > 0)
+    atomicAdd(P.counters + C_PAIRS, (unsigned long long)n);
+  for (int64_t g0 = blockIdx.x * (int64_t)blockDim.x; g0 < n; g0 += stride) {
+    const int64_t g = g0 + threadIdx.x;
     bool push = false;
     uint2 t = make_uint2(0u, 0u);
     if (g < n) {
@@ -954,23 +1113,21 @@ __global__ void k_wave_init(WaveArgs P, uint4 *q, unsigned *q_n) {
       if (ia >= 0 && ia < P.MA && ib >= 0 && ib < P.MB) {
         const F3 off = cand_offset(P, g);
         Box ba, bb;
-        ba.lo = ld3(P.A.aabb + 6 * (int64_t)ia);
-        ba.hi = ld3(P.A.aabb + 6 * (int64_t)ia + 3);
-        bb.lo = add(ld3(P.B.aabb + 6 * (int64_t)ib), off);
-        bb.hi = add(ld3(P.B.aabb + 6 * (int64_t)ib + 3), off);
+        const float4 a0 = P.A.mrec[3 * (int64_t)ia], a1 = P.A.mrec[3 * (int64_t)ia + 1];
+        const float4 b0 = P.B.mrec[3 * (int64_t)ib], b1 = P.B.mrec[3 * (int64_t)ib + 1];
+        ba.lo = mkf3(a0.x, a0.y, a0.z);
+        ba.hi = mkf3(a1.x, a1.y, a1.z);
+        bb.lo = add(mkf3(b0.x, b0.y, b0.z), off);
+        bb.hi = add(mkf3(b1.x, b1.y, b1.z), off);
         if (overlap(ba, bb)) {
           t = make_task((uint32_t)P.A.roots[ia], ba, (uint32_t)P.B.roots[ib], bb);
           push = true;
         }
       }
     }
-    unsigned pos = warp_append(q_n, push ? 1u : 0u, lane);
+    const unsigned pos = block_append2(q_n, push ? 1u : 0u, q_n, 0u).x;
     if (push && pos < P.q_cap) q[pos] = make_uint4((uint32_t)g, t.x, t.y, 0u);
     if (push && pos >= P.q_cap) atomicCAS(P.err, 0, DERR_QUEUE);
-    if (lane == 0) {
-      const int64_t m = n - (g - lane);
-      atomicAdd(P.counters + C_PAIRS, (unsigned long long)(m < 32 ? m : 32));
-    }
   }
 }
 
@@ -991,12 +1148,14 @@ template <int W>
 __global__ void __launch_bounds__(256) k_wave_expand(WaveArgs P, const uint4 *qin,
                                                      const unsigned *qin_n, uint4 *qout,
                                                      unsigned *qout_n, uint4 *lq, unsigned *lq_n) {
-  const int lane = threadIdx.x & 31;
+  pdl_wait();
+  pdl_trigger();
   const int64_t n = (int64_t)min(*qin_n, P.q_cap) * W;
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   const F3 zero = mkf3(0.f, 0.f, 0.f);
   unsigned long long cnt[3] = {0, 0, 0};  // node pairs, box tests, bytes
-  for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g - lane < n; g += stride) {
+  for (int64_t g0 = blockIdx.x * (int64_t)blockDim.x; g0 < n; g0 += stride) {
+    const int64_t g = g0 + threadIdx.x;
     unsigned task_mask = 0, leaf_mask = 0;
     uint4 e = make_uint4(0u, 0u, 0u, 0u);
     int i = 0;
@@ -1054,8 +1213,8 @@ __global__ void __launch_bounds__(256) k_wave_expand(WaveArgs P, const uint4 *qi
       }
     }
     // write the outputs (the B-side children are reloaded: L1 hits)
-    unsigned tpos = warp_append(qout_n, __popc(task_mask), lane);
-    unsigned lpos = warp_append(lq_n, __popc(leaf_mask), lane);
+    const uint2 pos = block_append2(qout_n, __popc(task_mask), lq_n, __popc(leaf_mask));
+    unsigned tpos = pos.x, lpos = pos.y;
     unsigned bits = task_mask | leaf_mask;
     while (bits) {
       const int j = __ffs(bits) - 1;
@@ -1086,29 +1245,28 @@ __global__ void __launch_bounds__(256) k_wave_expand(WaveArgs P, const uint4 *qi
       }
     }
   }
-  unsigned long long v[C_NUM] = {};
-  v[C_NODE_PAIRS] = cnt[0];
-  v[C_BOX_TESTS] = cnt[1];
-  v[C_BYTES] = cnt[2];
-  flush_counters(P.counters, v, lane, C_NUM);
+  const int slots[3] = {C_NODE_PAIRS, C_BOX_TESTS, C_BYTES};
+  block_flush<3>(P.counters, slots, cnt);
 }
 
-// Leaf pairs: 16 threads per pair (8 source triangles of each side); each
-// thread slab-tests its triangle's owned edges against the other leaf's box
-// and tests them exactly against the other leaf's triangles.
+// Leaf pairs: 2L threads per pair (the L source triangles of each side);
+// each thread slab-tests its triangle's owned edges against the other leaf's
+// box and tests them exactly against the other leaf's triangles.
 template <int W, bool EXACT>
-__global__ void __launch_bounds__(256) k_wave_leaf(WaveArgs P, const uint4 *lq, const unsigned *lq_n) {
-  const int lane = threadIdx.x & 31;
-  const int64_t n = (int64_t)min(*lq_n, P.q_cap) * 16;
+__global__ void __launch_bounds__(256, 3) k_wave_leaf(WaveArgs P, const uint4 *lq, const unsigned *lq_n) {
+  pdl_wait();
+  pdl_trigger();
+  const int sh = P.lshift + 1;               // 2L = 1 << sh threads per pair
+  const int64_t n = (int64_t)min(*lq_n, P.q_cap) << sh;
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   const F3 zero = mkf3(0.f, 0.f, 0.f);
   unsigned long long c_slab = 0, c_st = 0, c_fb = 0, c_bytes = 0, c_lp = 0;
   for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < n; g += stride) {
-    const uint4 e = lq[g >> 4];
-    const int u = (int)(g & 15);
+    const uint4 e = lq[g >> sh];
+    const int u = (int)(g & ((1 << sh) - 1));
     if (P.flags[e.x]) continue;
-    const bool dirA = u < 8;
-    const int k = u & 7;
+    const bool dirA = (u >> P.lshift) == 0;
+    const int k = u & ((1 << P.lshift) - 1);
     const uint32_t sslot = (dirA ? e.y : e.z) & kIdx, tslot = (dirA ? e.z : e.y) & kIdx;
     const Side &S = dirA ? P.A : P.B;
     const Side &T = dirA ? P.B : P.A;
@@ -1121,7 +1279,8 @@ __global__ void __launch_bounds__(256) k_wave_leaf(WaveArgs P, const uint4 *lq, 
     const F3 soff = dirA ? zero : off, toff = dirA ? off : zero;
     load_slot<W>(T.nodes, tslot / W, (int)(tslot % W), toff, tb, tdesc);
     if (u == 0) c_lp += 1;
-    const int64_t sbase = S.toff[dirA ? ia : ib], tbase = T.toff[dirA ? ib : ia];
+    const int64_t sbase = __float_as_int(S.mrec[3 * (int64_t)(dirA ? ia : ib) + 2].y);
+    const int64_t tbase = __float_as_int(T.mrec[3 * (int64_t)(dirA ? ib : ia) + 2].y);
     const int64_t s_rec = sbase + ((sdesc >> 3) & 0x0FFFFFFFu) + k;
     const int64_t t_first = tbase + ((tdesc >> 3) & 0x0FFFFFFFu);
     const int t_n = (int)(tdesc & 7u) + 1;
@@ -1165,24 +1324,23 @@ __global__ void __launch_bounds__(256) k_wave_leaf(WaveArgs P, const uint4 *lq, 
     }
     if (hit) P.flags[e.x] = 1;
   }
-  unsigned long long v[C_NUM] = {};
-  v[C_LEAF_PAIRS] = c_lp;
-  v[C_SLAB_TESTS] = c_slab;
-  v[C_SEGTRI] = c_st;
-  v[C_FALLBACK] = c_fb;
-  v[C_BYTES] = c_bytes;
-  // threads of a warp may have left the loop at different times: reconverge
-  __syncwarp();
-  flush_counters(P.counters, v, lane, C_NUM);
+  const int slots[5] = {C_LEAF_PAIRS, C_SLAB_TESTS, C_SEGTRI, C_FALLBACK, C_BYTES};
+  const unsigned long long v[5] = {c_lp, c_slab, c_st, c_fb, c_bytes};
+  block_flush<5>(P.counters, slots, v);
 }
 
 // Parity rays, one thread per (pair, direction): inside(B, A) for even
 // threads, inside(A, B) for odd ones.  Depth-first with a per-thread stack
-// (bounded by 1 + (W - 1) * depth).
+// (bounded by 1 + (W - 1) * depth).  A ray that needs more than
+// kParNodeBudget nodes (one that runs along a long tube, say) would hold its
+// whole block back; it is handed to the warp passes instead (-2).
+constexpr int kParNodeBudget = 32;
+constexpr uint32_t kParItem = 0xFFFFFFFEu;  // queue entry: (c, kParItem, direction)
+
 template <int W>
-__device__ int thread_parity(const Side &T, int it, F3 toff, F3 vf, int ax, int dir, uint32_t *stk,
-                             int cap, unsigned long long &nodes, unsigned long long &tris) {
-  const int64_t tbase = T.toff[it];
+__device__ int thread_parity(const Side &T, int it, int64_t tbase, F3 toff, F3 vf, int ax, int dir,
+                             uint32_t *stk, int cap, unsigned long long &nodes,
+                             unsigned long long &tris) {
   const I3 v = toi(vf);
   int sp = 0;
   stk[sp++] = (uint32_t)T.roots[it];
@@ -1190,30 +1348,49 @@ __device__ int thread_parity(const Side &T, int it, F3 toff, F3 vf, int ax, int 
   int par = 0;
   unsigned iters = 0;
   while (sp > 0) {
-    if (++iters > (1u << 24)) return -1;
+    if (++iters > (unsigned)kParNodeBudget) return -2;
     const uint32_t node = stk[--sp];
     nodes += 1;
-    for (int c = 0; c < W; ++c) {
-      Box b;
-      uint32_t ch;
-      load_slot<W>(T.nodes, node, c, toff, b, ch);
-      if (ch == kEmpty) continue;
-      if (!ray_axis_box(vf, b, ax, dir)) continue;
-      if (ch & kLeafBit) {
-        const int64_t first = tbase + ((ch >> 3) & 0x0FFFFFFFu);
-        const int cntl = (int)(ch & 7u) + 1;
-        for (int t = 0; t < cntl; ++t) {
-          F3 a, bb, cc;
-          int own;
-          load_tri(T.trirec, first + t, toff, a, bb, cc, own);
-          const I3 ai = toi(a), bi = toi(bb), ci = toi(cc);
+    // the node's W child slots as one batch of independent loads (a thread
+    // walks alone, so every serial load is a full memory latency)
+    uint32_t ch[W];
+    unsigned leaves = 0;
+    {
+      Box b[W];
+#pragma unroll
+      for (int c = 0; c < W; ++c) load_slot<W>(T.nodes, node, c, toff, b[c], ch[c]);
+#pragma unroll
+      for (int c = 0; c < W; ++c) {
+        if (ch[c] == kEmpty || !ray_axis_box(vf, b[c], ax, dir)) continue;
+        if (ch[c] & kLeafBit) {
+          leaves |= 1u << c;
+        } else {
+          if (sp >= cap) return -1;
+          stk[sp++] = ch[c];
+        }
+      }
+    }
+    while (leaves) {
+      const int c = __ffs(leaves) - 1;
+      leaves &= leaves - 1;
+      const uint32_t lc = sel_u32<W>(ch, c);
+      const int64_t first = tbase + ((lc >> 3) & 0x0FFFFFFFu);
+      const int cntl = (int)(lc & 7u) + 1;
+      for (int t0 = 0; t0 < cntl; t0 += 4) {
+        // up to four of the leaf's triangles per batch of loads
+        F3 ta[4], tb[4], tc[4];
+        int own;
+#pragma unroll
+        for (int t = 0; t < 4; ++t)
+          if (t0 + t < cntl) load_tri(T.trirec, first + t0 + t, toff, ta[t], tb[t], tc[t], own);
+        const int tn = min(4, cntl - t0);
+#pragma unroll 1
+        for (int t = 0; t < tn; ++t) {
+          const I3 ai = toi(sel_f3<4>(ta, t)), bi = toi(sel_f3<4>(tb, t)), ci = toi(sel_f3<4>(tc, t));
           on = on || on_triangle(v, ai, bi, ci);
           par ^= ray_axis_hit(v, ai, bi, ci, ax, dir) ? 1 : 0;
           tris += 1;
         }
-      } else {
-        if (sp >= cap) return -1;
-        stk[sp++] = ch;
       }
     }
   }
@@ -1222,9 +1399,11 @@ __device__ int thread_parity(const Side &T, int it, F3 toff, F3 vf, int ax, int 
 
 template <int W>
 __global__ void __launch_bounds__(128) k_wave_parity(WaveArgs P) {
-  constexpr int CAP = 1 + (W - 1) * 64;
+  pdl_wait();
+  pdl_trigger();
+  // the node budget bounds the stack: each pop pushes at most W - 1 more
+  constexpr int CAP = 1 + (W - 1) * kParNodeBudget;
   uint32_t stk[CAP];
-  const int lane = threadIdx.x & 31;
   const int64_t n = *P.n_cand * 2;
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   const F3 zero = mkf3(0.f, 0.f, 0.f);
@@ -1239,20 +1418,40 @@ __global__ void __launch_bounds__(128) k_wave_parity(WaveArgs P) {
     const Side &T = bInA ? P.A : P.B;
     const int iq = bInA ? ib : ia, it = bInA ? ia : ib;
     const F3 qoff = bInA ? off : zero, toff = bInA ? zero : off;
-    const int64_t v0 = Q.voff[iq], nv = Q.voff[iq + 1] - v0;
-    const F3 lo = add(ld3(T.aabb + 6 * (int64_t)it), toff), hi = add(ld3(T.aabb + 6 * (int64_t)it + 3), toff);
+    // one fetch per side: T's box and first triangle, Q's first lexicographic
+    // vertex and vertex range
+    const float4 t0 = T.mrec[3 * (int64_t)it], t1 = T.mrec[3 * (int64_t)it + 1];
+    const float4 t2 = T.mrec[3 * (int64_t)it + 2];
+    const float4 q0 = Q.mrec[3 * (int64_t)iq], q1 = Q.mrec[3 * (int64_t)iq + 1];
+    const float4 q2 = Q.mrec[3 * (int64_t)iq + 2];
+    const int64_t tbase = __float_as_int(t2.y);
+    const int64_t v0 = __float_as_int(q2.z), nv = __float_as_int(q2.w);
+    const F3 lo = add(mkf3(t0.x, t0.y, t0.z), toff), hi = add(mkf3(t1.x, t1.y, t1.z), toff);
+    bytes += 96;
     int res = 0;
     for (int64_t k = 0; k < nv; ++k) {
-      const int64_t vid = Q.lexorder[v0 + k];
-      const F3 v = add(ld3(Q.xyz + 3 * vid), qoff);
-      bytes += 16;
+      F3 v;
+      if (k == 0) {
+        v = add(mkf3(q0.w, q1.w, q2.x), qoff);
+      } else {
+        const int64_t vid = Q.lexorder[v0 + k];
+        v = add(ld3(Q.xyz + 3 * vid), qoff);
+        bytes += 16;
+      }
       if (v.x < lo.x || v.x > hi.x || v.y < lo.y || v.y > hi.y || v.z < lo.z || v.z > hi.z) break;
       rays += 1;
       const unsigned long long n0 = nodes, t0 = tris;
       int ax, dir;
       ray_axis_choice(v, lo, hi, ax, dir);
-      const int r = thread_parity<W>(T, it, toff, v, ax, dir, stk, CAP, nodes, tris);
+      const int r = thread_parity<W>(T, it, tbase, toff, v, ax, dir, stk, CAP, nodes, tris);
       bytes += (nodes - n0) * W * 32 + (tris - t0) * 48;
+      if (r == -2) {
+        // over the node budget: a warp redoes this direction from the start
+        const unsigned pos = atomicAdd(P.q_par_n, 1u);
+        if (pos < P.q_par_cap) P.q_par[pos] = make_uint4((uint32_t)c, kParItem, bInA ? 0u : 1u, 0u);
+        else atomicCAS(P.err, 0, DERR_QUEUE);
+        break;
+      }
       if (r < 0) {
         atomicCAS(P.err, 0, DERR_STACK);
         break;
@@ -1264,13 +1463,9 @@ __global__ void __launch_bounds__(128) k_wave_parity(WaveArgs P) {
     }
     if (res) P.flags[c] = 1;
   }
-  unsigned long long v[C_NUM] = {};
-  v[C_PARITY_RAYS] = rays;
-  v[C_PARITY_NODES] = nodes;
-  v[C_PARITY_TRIS] = tris;
-  v[C_BYTES] = bytes;
-  __syncwarp();
-  flush_counters(P.counters, v, lane, C_NUM);
+  const int slots[4] = {C_PARITY_RAYS, C_PARITY_NODES, C_PARITY_TRIS, C_BYTES};
+  const unsigned long long v[4] = {rays, nodes, tris, bytes};
+  block_flush<4>(P.counters, slots, v);
 }
 
 // Later passes: warps pop spilled (candidate, itemA, itemB) tasks and continue
@@ -1279,11 +1474,41 @@ __global__ void __launch_bounds__(128) k_wave_parity(WaveArgs P) {
 // to it).  Pairs already known to intersect are skipped.
 template <int W, bool EXACT>
 __global__ void __launch_bounds__(128, 4) k_refine_tasks(RefineArgs P) {
+  pdl_wait();
+  pdl_trigger();
   extern __shared__ __align__(16) unsigned char smem[];
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
   WarpMem sm = carve<W>(smem + (size_t)wib * warp_smem_bytes<W>(P.stack_cap), P.stack_cap);
   Cnt cnt;
   for (int i = 0; i < C_NUM; ++i) cnt.v[i] = 0;
+  // first the handed-over parity rays (the longest items), one warp each
+  const unsigned int np = P.q_par ? min(*P.q_par_n, P.q_par_cap) : 0u;
+  for (;;) {
+    unsigned int t = 0;
+    if (lane == 0 && np) t = atomicAdd(P.q_par_pos, 1u);
+    t = __shfl_sync(FULL, t, 0);
+    if (t >= np) break;
+    const uint4 e = P.q_par[t];
+    const uint32_t c = e.x;
+    volatile uint8_t *flag = P.flags + c;
+    int done = lane == 0 ? (int)*flag : 0;
+    if (__shfl_sync(FULL, done, 0)) continue;
+    const int ia = P.cand[2 * (int64_t)c], ib = P.cand[2 * (int64_t)c + 1];
+    F3 off = mkf3(0.f, 0.f, 0.f);
+    if (P.cand_off)
+      off = mkf3((float)P.cand_off[3 * (int64_t)c], (float)P.cand_off[3 * (int64_t)c + 1],
+                 (float)P.cand_off[3 * (int64_t)c + 2]);
+    const F3 zero = mkf3(0.f, 0.f, 0.f);
+    // direction 0: B's representative vertex against A; 1: A's against B
+    const int r = e.z == 0u
+        ? pair_inside<W>(P.B, ib, off, P.A, ia, zero, sm, lane, P.stack_cap, P.max_pop, cnt)
+        : pair_inside<W>(P.A, ia, zero, P.B, ib, off, sm, lane, P.stack_cap, P.max_pop, cnt);
+    if (r == 1) {
+      if (lane == 0) *flag = 1;
+    } else if (r < 0) {
+      if (lane == 0) atomicCAS(P.err, 0, DERR_STACK);
+    }
+  }
   const unsigned int n = min(*P.q_in_n, P.q_in_cap);
   for (;;) {
     unsigned int t = 0;
@@ -1331,6 +1556,8 @@ constexpr int CMP_T = 256, CMP_PER = 16, CMP_CHUNK = CMP_T * CMP_PER;
 
 __global__ void k_flag_count(const uint8_t *flags, const int64_t *n_dev, int64_t *bcount,
                              unsigned long long *hits) {
+  pdl_wait();
+  pdl_trigger();
   const int64_t n = *n_dev;
   int64_t base = blockIdx.x * (int64_t)CMP_CHUNK;
   int c = 0;
@@ -1352,6 +1579,8 @@ __global__ void k_flag_count(const uint8_t *flags, const int64_t *n_dev, int64_t
 
 __global__ void k_flag_emit(const uint8_t *flags, const int64_t *n_dev, const int32_t *cand,
                             const int64_t *boff, int32_t *out) {
+  pdl_wait();
+  pdl_trigger();
   const int64_t n = *n_dev;
   int64_t base = blockIdx.x * (int64_t)CMP_CHUNK + (int64_t)threadIdx.x * CMP_PER;
   int c = 0;
@@ -1480,6 +1709,7 @@ static Side make_side(Dataset *d, Bvh &b) {
   s.aabb = d->d_aabb;
   s.xyz = d->d_xyz;
   s.lexorder = d->d_lexorder;
+  s.mrec = d->d_mrec;
   return s;
 }
 
@@ -1612,8 +1842,14 @@ pj_status run_join(Ctx *ctx, Dataset *A, Dataset *B, const int32_t *cand,
   int wave_levels = o->wave_levels > 0 ? o->wave_levels : (o->wave_levels < 0 ? 0 : 12);
   if (std::max(bA.max_depth, bB.max_depth) > 64) wave_levels = 0;
   const unsigned int wq_cap = 1u << 23;
-  uint4 *wqa = nullptr, *wqb = nullptr, *wlq = nullptr;
-  unsigned int *wctr = reinterpret_cast<unsigned int *>(d_misc + 5);  // qa n/pos, qb n/pos, lq n
+  uint4 *wqa = nullptr, *wqb = nullptr, *wlq = nullptr, *wpar = nullptr;
+  // level counters, cleared by one memset: task count entering each level
+  // [0, levels], leaf pairs found at each level, then the position of the
+  // first warp pass in the last queue and the parity hand-over count/position
+  unsigned int *wctr = nullptr;
+  const int wctr_words = 2 * std::max(wave_levels, 0) + 8;
+  const unsigned int wpar_cap =
+      (unsigned int)std::min<int64_t>(std::max<int64_t>(2 * C, 1024), 1 << 22);
   int wave_grid[3] = {1, 1, 1};  // expand/init, leaf, parity: one resident wave
   if (wave_levels > 0 && o->launch_mode != PJ_LAUNCH_PER_PAIR) {
     int occ = 0;
@@ -1629,6 +1865,10 @@ pj_status run_join(Ctx *ctx, Dataset *A, Dataset *B, const int32_t *cand,
     if (!wqb) return st;
     wlq = (uint4 *)ws_get(ctx, "wave_leaf", sizeof(uint4) * (size_t)wq_cap, &st);
     if (!wlq) return st;
+    wpar = (uint4 *)ws_get(ctx, "wave_par", sizeof(uint4) * (size_t)wpar_cap, &st);
+    if (!wpar) return st;
+    wctr = (unsigned int *)ws_get(ctx, "wave_ctr", sizeof(unsigned int) * (size_t)wctr_words, &st);
+    if (!wctr) return st;
   }
   unsigned int *d_cycles = nullptr;
   if (o->record_cycles) {
@@ -1663,6 +1903,10 @@ pj_status run_join(Ctx *ctx, Dataset *A, Dataset *B, const int32_t *cand,
   args.q_in = nullptr;
   args.q_in_n = nullptr;
   args.q_in_pos = nullptr;
+  args.q_par = nullptr;
+  args.q_par_n = nullptr;
+  args.q_par_pos = nullptr;
+  args.q_par_cap = 0;
   int64_t blocks = 1;
   if (C > 0 && o->launch_mode != PJ_LAUNCH_PER_PAIR) {
     int occ = 0;
@@ -1690,7 +1934,8 @@ pj_status run_join(Ctx *ctx, Dataset *A, Dataset *B, const int32_t *cand,
         ctx->launches += C;
       } else if (wave_levels > 0) {
         // wavefront front end, then the warp passes over what is left
-        PJ_CK(cudaMemsetAsync(d_misc + 2, 0, 48, s));  // work, spill and wave counters
+        PJ_CK(cudaMemsetAsync(d_misc + 2, 0, 48, s));  // work and spill counters
+        PJ_CK(cudaMemsetAsync(wctr, 0, sizeof(unsigned int) * wctr_words, s));
         PJ_CK(cudaMemsetAsync(d_flags, 0, (size_t)C, s));
         WaveArgs wa;
         wa.A = args.A;
@@ -1702,24 +1947,27 @@ pj_status run_join(Ctx *ctx, Dataset *A, Dataset *B, const int32_t *cand,
         wa.counters = ctx->d_counters;
         wa.err = d_err;
         wa.q_cap = wq_cap;
+        wa.lshift = key.second == 1 ? 0 : (key.second == 2 ? 1 : (key.second == 4 ? 2 : 3));
         wa.MA = A->M;
         wa.MB = B->M;
+        unsigned int *qn = wctr, *ln = wctr + wave_levels + 1, *misc = ln + wave_levels;
+        wa.q_par = wpar;
+        wa.q_par_n = misc + 1;
+        wa.q_par_cap = wpar_cap;
         WaveExpandKernel kx = pick_wave_expand(W);
         WaveLeafKernel kl = pick_wave_leaf(W, exact);
         WaveParityKernel kp = pick_wave_parity(W);
         const int wblocks = wave_grid[0], lblocks = wave_grid[1], pblocks = wave_grid[2];
-        k_wave_init<<<wblocks, 256, 0, s>>>(wa, wqa, wctr);
-        kp<<<pblocks, 128, 0, s>>>(wa);
+        k_wave_init<<<wblocks, 256, 0, s>>>(wa, wqa, qn);
+        PJ_CK(launch_pdl(kp, pblocks, 128, 0, s, wa));
         if (timed) PJ_CK(cudaEventRecord(ev[4], s));
         uint4 *qin = wqa, *qout = wqb;
-        unsigned int *qin_n = wctr, *qout_n = wctr + 2;
         for (int lvl = 0; lvl < wave_levels; ++lvl) {
-          PJ_CK(cudaMemsetAsync(qout_n, 0, 4, s));
-          PJ_CK(cudaMemsetAsync(wctr + 4, 0, 4, s));
-          kx<<<wblocks, 256, 0, s>>>(wa, qin, qin_n, qout, qout_n, wlq, wctr + 4);
-          kl<<<lblocks, 256, 0, s>>>(wa, wlq, wctr + 4);
+          PJ_CK(launch_pdl(kx, wblocks, 256, 0, s, wa, (const uint4 *)qin,
+                           (const unsigned *)(qn + lvl), qout, qn + lvl + 1, wlq, ln + lvl));
+          PJ_CK(launch_pdl(kl, lblocks, 256, 0, s, wa, (const uint4 *)wlq,
+                           (const unsigned *)(ln + lvl)));
           std::swap(qin, qout);
-          std::swap(qin_n, qout_n);
         }
         if (timed) {
           PJ_CK(cudaEventRecord(ev[5], s));
@@ -1727,13 +1975,17 @@ pj_status run_join(Ctx *ctx, Dataset *A, Dataset *B, const int32_t *cand,
         }
         RefineArgs a1 = args;
         a1.q_in = qin;
-        a1.q_in_n = qin_n;
-        a1.q_in_pos = qin_n + 1;
+        a1.q_in_n = qn + wave_levels;
+        a1.q_in_pos = misc;
         a1.q_in_cap = wq_cap;
+        a1.q_par = wpar;
+        a1.q_par_n = misc + 1;
+        a1.q_par_pos = misc + 2;
+        a1.q_par_cap = wpar_cap;
         a1.q_out = budget1 > 0 ? q1 : nullptr;
         a1.q_out_n = qctr;
         a1.budget = budget1;
-        kern_tasks<<<(int)blocks, threads, smem, s>>>(a1);
+        PJ_CK(launch_pdl(kern_tasks, (int)blocks, threads, smem, s, a1));
         RefineArgs a2 = args;
         a2.q_in = q1;
         a2.q_in_n = qctr;
@@ -1741,7 +1993,7 @@ pj_status run_join(Ctx *ctx, Dataset *A, Dataset *B, const int32_t *cand,
         a2.q_out = q2;
         a2.q_out_n = qctr + 2;
         a2.budget = budget2;
-        kern_tasks<<<(int)blocks, threads, smem, s>>>(a2);
+        PJ_CK(launch_pdl(kern_tasks, (int)blocks, threads, smem, s, a2));
         RefineArgs a3 = args;
         a3.q_in = q2;
         a3.q_in_n = qctr + 2;
@@ -1749,7 +2001,7 @@ pj_status run_join(Ctx *ctx, Dataset *A, Dataset *B, const int32_t *cand,
         a3.q_out = nullptr;
         a3.q_out_n = nullptr;
         a3.budget = 0;
-        kern_tasks<<<(int)blocks, threads, smem, s>>>(a3);
+        PJ_CK(launch_pdl(kern_tasks, (int)blocks, threads, smem, s, a3));
         ctx->launches += 5 + 2 * wave_levels;
       } else {
         PJ_CK(cudaMemsetAsync(d_misc + 2, 0, 24, s));  // work counter, queue counters
@@ -1765,7 +2017,7 @@ pj_status run_join(Ctx *ctx, Dataset *A, Dataset *B, const int32_t *cand,
         a2.q_out = q2;
         a2.q_out_n = qctr + 2;
         a2.budget = budget2;
-        kern_tasks<<<(int)blocks, threads, smem, s>>>(a2);
+        PJ_CK(launch_pdl(kern_tasks, (int)blocks, threads, smem, s, a2));
         RefineArgs a3 = args;
         a3.q_in = q2;
         a3.q_in_n = qctr + 2;
@@ -1773,18 +2025,21 @@ pj_status run_join(Ctx *ctx, Dataset *A, Dataset *B, const int32_t *cand,
         a3.q_out = nullptr;
         a3.q_out_n = nullptr;
         a3.budget = 0;
-        kern_tasks<<<(int)blocks, threads, smem, s>>>(a3);
+        PJ_CK(launch_pdl(kern_tasks, (int)blocks, threads, smem, s, a3));
         ctx->launches += 3;
       }
       PJ_CK(cudaGetLastError());
     }
     if (timed) PJ_CK(cudaEventRecord(ev[2], s));
     // 3. compaction
-    k_flag_count<<<nchunks, CMP_T, 0, s>>>(d_flags, d_misc, bcount, ctx->d_counters + C_HITS);
+    PJ_CK(launch_pdl(k_flag_count, nchunks, CMP_T, 0, s, (const uint8_t *)d_flags,
+                     (const int64_t *)d_misc, bcount, ctx->d_counters + C_HITS));
     ++ctx->launches;
     pj_status st2 = scan_i64(ctx, bcount, boff, nchunks, d_misc + 1, s);
     if (st2 != PJ_OK) return st2;
-    k_flag_emit<<<nchunks, CMP_T, 0, s>>>(d_flags, d_misc, d_cand, boff, d_pairs);
+    PJ_CK(launch_pdl(k_flag_emit, nchunks, CMP_T, 0, s, (const uint8_t *)d_flags,
+                     (const int64_t *)d_misc, (const int32_t *)d_cand, (const int64_t *)boff,
+                     d_pairs));
     ++ctx->launches;
     PJ_CK(cudaGetLastError());
     return PJ_OK;
@@ -2015,6 +2270,10 @@ pj_status run_join_noalloc(Ctx *ctx, Dataset *A, Dataset *B, const int32_t *d_ca
   args.q_in_n = nullptr;
   args.q_in_pos = nullptr;
   args.q_in_cap = 0;
+  args.q_par = nullptr;
+  args.q_par_n = nullptr;
+  args.q_par_pos = nullptr;
+  args.q_par_cap = 0;
   args.n_cand = d_n;
   args.flags = d_flags;
   args.work = work;
