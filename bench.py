@@ -32,6 +32,7 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "candidate pairs refined/s & segment–tri tests/s; p50/p99 query latency"
+WAVE_LEVELS = 14          # breadth-first levels of the library's default join
 UNIT = "pairs/s"
 WORKLOAD = ("pathology join: 10,000 nuclei (icosphere L4/L5, 10% smooth radial noise, "
             "log-normal radius mean 1/200 box) x 500 vessels (16-sided capped tubes on cubic "
@@ -129,10 +130,11 @@ def make_workload(seed: int, n_nuclei: int = 10000, n_vessels: int = 500):
     return synth.pathology(seed, n_nuclei, n_vessels)
 
 
-def profile_traffic(kernel_src: str):
-    """DRAM bytes per refine launch from the committed ncu summary, if that
-    summary was taken on the current kernel source (else None)."""
-    p = os.path.join(ROOT, "profiles", "k_refine_pathology.md")
+def profile_traffic(kernel: str, kernel_src: str):
+    """DRAM bytes per launch of `kernel` on the pathology workload from the
+    committed ncu summary profiles/<kernel>_pathology.md, if that summary was
+    taken on the current kernel source (else None)."""
+    p = os.path.join(ROOT, "profiles", "%s_pathology.md" % kernel)
     if not os.path.exists(p):
         return None
     txt = open(p).read()
@@ -260,26 +262,40 @@ def run_ours(args, rank, world, local_rank):
     value = C_all / (ms_step / 1000.0)
     segtri_s = cnt["segtri_tests"] / (total_ms / 1000.0)
     launches = cnt["kernel_launches"]
-    # phase breakdown (same join, not replayed from a graph, so CUDA events
-    # separate the phases): parity rays, breadth-first front end, warp passes
+    # phase and kernel breakdown (same join, not replayed from a graph, with
+    # CUDA events on the join's stream between the phases and around every
+    # breadth-first launch)
     ctx.reset_counters()
-    ph = {"parity_ms": [], "front_ms": [], "tasks_ms": [], "refine_ms": []}
+    keys = ("parity_ms", "front_ms", "tasks_ms", "refine_ms", "expand_ms", "leaf_ms")
+    ph = {k: [] for k in keys}
     for _ in range(args.steps):
         flush.zero_()
-        res = pierce.pj_join_intersects_ex(ctx.h, ha, hb, **dict(opts, use_graph=False))
+        res = pierce.pj_join_intersects_ex(ctx.h, ha, hb, **dict(opts, use_graph=False,
+                                                                  kernel_times=True))
         for k in ph:
             ph[k].append(getattr(res, k))
         pierce.pj_free_pairs(ctx.h, res)
     torch.cuda.synchronize()
     pc = ctx.counters()
     phase_ms = {k: float(np.median(v)) for k, v in ph.items()}
-    bytes_tasks = pc["bytes_tasks"] / args.steps
-    bytes_all = pc["bytes_fetched"] / args.steps
+    per_step = {k: pc[k] / args.steps for k in ("bytes_fetched", "bytes_parity", "bytes_expand",
+                                                 "bytes_leaf", "bytes_tasks")}
     peak, peak_kind = measured_peaks()
-    # dominant kernel: the per-warp passes (k_refine_tasks, 3 launches a step)
-    tasks_ms = max(phase_ms["tasks_ms"], 1e-6)
-    achieved = bytes_tasks / (tasks_ms / 1000.0) / 1e9
-    traffic = profile_traffic(os.path.join(ROOT, "paper_2609_24513_gb300", "csrc", "pj_join.cu"))
+    levels = WAVE_LEVELS
+    # kernel families of one step: (step ms, algorithmic bytes, launches)
+    fam = {"k_wave_expand": (phase_ms["expand_ms"], per_step["bytes_expand"], levels),
+           "k_wave_leaf": (phase_ms["leaf_ms"], per_step["bytes_leaf"], levels),
+           "k_wave_parity+handover": (phase_ms["parity_ms"], per_step["bytes_parity"], 2),
+           "k_refine_tasks": (phase_ms["tasks_ms"], per_step["bytes_tasks"], 3)}
+    dom = max(fam, key=lambda k: fam[k][0])
+    d_ms, d_bytes, d_launch = fam[dom]
+    achieved = d_bytes / (max(d_ms, 1e-6) / 1000.0) / 1e9
+    traffic = profile_traffic(dom, os.path.join(ROOT, "paper_2609_24513_gb300", "csrc",
+                                                 "pj_join.cu"))
+    kernels = {k: {"ms_per_step": round(v[0], 4), "launches_per_step": v[2],
+                   "bytes_per_launch": v[1] / v[2],
+                   "achieved_gbs": v[1] / (max(v[0], 1e-6) / 1000.0) / 1e9}
+               for k, v in fam.items()}
     line_e2e = None
     cand_host = _candidates_host(ctx, ha, hb, C)
     if not args.no_e2e:
@@ -300,14 +316,15 @@ def run_ours(args, rank, world, local_rank):
             "gpu_launches": int(launches),
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "traffic": traffic,
-                         "kernel": "k_refine_tasks (3 launches per step)",
-                         "launch_ms": tasks_ms / 3.0, "bytes_per_launch": bytes_tasks / 3.0,
-                         "peak_source": peak_kind,
-                         "refinement_phase": {"ms": phase_ms["refine_ms"], "bytes": bytes_all,
-                                              "achieved_gbs": bytes_all / (phase_ms["refine_ms"] / 1000.0) / 1e9,
-                                              "parity_ms": phase_ms["parity_ms"],
-                                              "front_ms": phase_ms["front_ms"],
-                                              "tasks_ms": phase_ms["tasks_ms"]}},
+                         "kernel": dom, "launches_per_step": d_launch,
+                         "launch_ms": d_ms / d_launch, "bytes_per_launch": d_bytes / d_launch,
+                         "peak_source": peak_kind, "kernels": kernels,
+                         "refinement_phase": {
+                             "ms": phase_ms["refine_ms"], "bytes": per_step["bytes_fetched"],
+                             "achieved_gbs": per_step["bytes_fetched"] /
+                             (phase_ms["refine_ms"] / 1000.0) / 1e9,
+                             "parity_ms": phase_ms["parity_ms"], "front_ms": phase_ms["front_ms"],
+                             "tasks_ms": phase_ms["tasks_ms"]}},
             "e2e": line_e2e,
             "clocks": clk}
     if rank == 0 and world == 1 and not args.no_cpu_baseline:

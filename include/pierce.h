@@ -97,8 +97,10 @@ typedef struct {
                                second pass allows 8 times as many            */
   int32_t wave_levels;      /* BVH levels descended breadth-first, one thread
                                per child test, before the per-warp passes
-                               (0: 12; < 0: none)                            */
-  int32_t reserved;
+                               (0: 14; < 0: none)                            */
+  int32_t kernel_times;     /* 1: also time each breadth-first launch with CUDA
+                               events (pj_pairs.expand_ms / leaf_ms; events
+                               between launches cost a little overlap)       */
 } pj_join_opts;
 
 /* Result of a join.  Owned by the library until pj_free_pairs. */
@@ -121,6 +123,9 @@ typedef struct {
   float front_ms;           /* breadth-first front end (levels and leaf
                                pairs),                                       */
   float tasks_ms;           /* and the per-warp passes over what was left     */
+  float expand_ms;          /* with pj_join_opts.kernel_times: summed durations
+                               of the breadth-first node-pair launches,       */
+  float leaf_ms;            /* and of the breadth-first leaf-pair launches    */
   float reserved3;
   uint32_t *cycles;         /* device, C values (only with record_cycles):
                                clock64 cycles the refinement spent on each
@@ -146,6 +151,10 @@ typedef struct {
   uint64_t tasks_spilled;       /* traversal tasks handed to a later pass        */
   uint64_t tasks_resumed;       /* spilled tasks taken up by a later pass        */
   uint64_t bytes_tasks;         /* of bytes_fetched: the per-warp passes        */
+  uint64_t bytes_parity;        /* of bytes_fetched: the parity rays            */
+  uint64_t bytes_expand;        /* of bytes_fetched: breadth-first node pairs   */
+  uint64_t bytes_leaf;          /* of bytes_fetched: breadth-first leaf pairs   */
+  uint64_t parity_handed_over;  /* parity rays passed from a thread to a warp   */
 } pj_counters;
 
 /* Dataset summary. */

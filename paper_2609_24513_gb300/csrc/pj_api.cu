@@ -701,6 +701,10 @@ pj_status pj_get_counters(pj_ctx *h, pj_counters *out) {
   out->tasks_spilled = c[C_SPILLED];
   out->tasks_resumed = c[C_TASKS];
   out->bytes_tasks = c[C_BYTES_TASKS];
+  out->bytes_parity = c[C_BYTES_PARITY];
+  out->bytes_expand = c[C_BYTES_EXPAND];
+  out->bytes_leaf = c[C_BYTES_LEAF];
+  out->parity_handed_over = c[C_PAR_HANDOVER];
   return PJ_OK;
 }
 

@@ -77,7 +77,9 @@ struct Dataset {
 enum {
   C_PAIRS = 0, C_NODE_PAIRS, C_BOX_TESTS, C_LEAF_PAIRS, C_SLAB_TESTS,
   C_SEGTRI, C_FALLBACK, C_PARITY_RAYS, C_PARITY_NODES, C_PARITY_TRIS,
-  C_BYTES, C_HITS, C_SPILLED, C_TASKS, C_BYTES_TASKS, C_NUM = 16
+  C_BYTES, C_HITS, C_SPILLED, C_TASKS, C_BYTES_TASKS,
+  C_WARP_NUM = 16,  // the warp-traversal kernels keep these in registers
+  C_BYTES_PARITY = 16, C_BYTES_EXPAND, C_BYTES_LEAF, C_PAR_HANDOVER, C_NUM = 20
 };
 
 struct Workspace {

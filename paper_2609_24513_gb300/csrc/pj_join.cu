@@ -306,7 +306,7 @@ struct RefineArgs {
 };
 
 struct Cnt {
-  unsigned long long v[C_NUM];
+  unsigned long long v[C_WARP_NUM];
 };
 
 // Work handed from one refinement pass to the next: when a pair exceeds its
@@ -886,7 +886,7 @@ __global__ void __launch_bounds__(128, 4) k_refine(RefineArgs P) {
   const int grp = wib / k, rank = wib % k;
   WarpMem sm = carve<W>(smem + (size_t)wib * warp_smem_bytes<W>(P.stack_cap), P.stack_cap);
   Cnt cnt;
-  for (int i = 0; i < C_NUM; ++i) cnt.v[i] = 0;
+  for (int i = 0; i < C_WARP_NUM; ++i) cnt.v[i] = 0;
   const int64_t n = *P.n_cand;
   bool first = true;
   for (;;) {
@@ -978,7 +978,7 @@ __global__ void __launch_bounds__(128, 4) k_refine(RefineArgs P) {
     }
   }
   // flush counters (warp-aggregated)
-  for (int i = 0; i < C_NUM; ++i) {
+  for (int i = 0; i < C_WARP_NUM; ++i) {
     unsigned long long v = cnt.v[i];
     for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(FULL, v, o);
     if (lane == 0 && v) atomicAdd(P.counters + i, v);
@@ -1245,8 +1245,9 @@ __global__ void __launch_bounds__(256) k_wave_expand(WaveArgs P, const uint4 *qi
       }
     }
   }
-  const int slots[3] = {C_NODE_PAIRS, C_BOX_TESTS, C_BYTES};
-  block_flush<3>(P.counters, slots, cnt);
+  const int slots[4] = {C_NODE_PAIRS, C_BOX_TESTS, C_BYTES, C_BYTES_EXPAND};
+  const unsigned long long v[4] = {cnt[0], cnt[1], cnt[2], cnt[2]};
+  block_flush<4>(P.counters, slots, v);
 }
 
 // Leaf pairs: 2L threads per pair (the L source triangles of each side);
@@ -1324,9 +1325,9 @@ __global__ void __launch_bounds__(256, 3) k_wave_leaf(WaveArgs P, const uint4 *l
     }
     if (hit) P.flags[e.x] = 1;
   }
-  const int slots[5] = {C_LEAF_PAIRS, C_SLAB_TESTS, C_SEGTRI, C_FALLBACK, C_BYTES};
-  const unsigned long long v[5] = {c_lp, c_slab, c_st, c_fb, c_bytes};
-  block_flush<5>(P.counters, slots, v);
+  const int slots[6] = {C_LEAF_PAIRS, C_SLAB_TESTS, C_SEGTRI, C_FALLBACK, C_BYTES, C_BYTES_LEAF};
+  const unsigned long long v[6] = {c_lp, c_slab, c_st, c_fb, c_bytes, c_bytes};
+  block_flush<6>(P.counters, slots, v);
 }
 
 // Parity rays, one thread per (pair, direction): inside(B, A) for even
@@ -1334,7 +1335,7 @@ __global__ void __launch_bounds__(256, 3) k_wave_leaf(WaveArgs P, const uint4 *l
 // (bounded by 1 + (W - 1) * depth).  A ray that needs more than
 // kParNodeBudget nodes (one that runs along a long tube, say) would hold its
 // whole block back; it is handed to the warp passes instead (-2).
-constexpr int kParNodeBudget = 32;
+constexpr int kParNodeBudget = 4;
 constexpr uint32_t kParItem = 0xFFFFFFFEu;  // queue entry: (c, kParItem, direction)
 
 template <int W>
@@ -1407,7 +1408,7 @@ __global__ void __launch_bounds__(128) k_wave_parity(WaveArgs P) {
   const int64_t n = *P.n_cand * 2;
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   const F3 zero = mkf3(0.f, 0.f, 0.f);
-  unsigned long long rays = 0, nodes = 0, tris = 0, bytes = 0;
+  unsigned long long rays = 0, nodes = 0, tris = 0, bytes = 0, handed = 0;
   for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < n; g += stride) {
     const int64_t c = g >> 1;
     const bool bInA = (g & 1) == 0;
@@ -1447,6 +1448,7 @@ __global__ void __launch_bounds__(128) k_wave_parity(WaveArgs P) {
       bytes += (nodes - n0) * W * 32 + (tris - t0) * 48;
       if (r == -2) {
         // over the node budget: a warp redoes this direction from the start
+        handed += 1;
         const unsigned pos = atomicAdd(P.q_par_n, 1u);
         if (pos < P.q_par_cap) P.q_par[pos] = make_uint4((uint32_t)c, kParItem, bInA ? 0u : 1u, 0u);
         else atomicCAS(P.err, 0, DERR_QUEUE);
@@ -1463,9 +1465,10 @@ __global__ void __launch_bounds__(128) k_wave_parity(WaveArgs P) {
     }
     if (res) P.flags[c] = 1;
   }
-  const int slots[4] = {C_PARITY_RAYS, C_PARITY_NODES, C_PARITY_TRIS, C_BYTES};
-  const unsigned long long v[4] = {rays, nodes, tris, bytes};
-  block_flush<4>(P.counters, slots, v);
+  const int slots[6] = {C_PARITY_RAYS, C_PARITY_NODES, C_PARITY_TRIS, C_BYTES, C_BYTES_PARITY,
+                        C_PAR_HANDOVER};
+  const unsigned long long v[6] = {rays, nodes, tris, bytes, bytes, handed};
+  block_flush<6>(P.counters, slots, v);
 }
 
 // Later passes: warps pop spilled (candidate, itemA, itemB) tasks and continue
@@ -1480,7 +1483,7 @@ __global__ void __launch_bounds__(128, 4) k_refine_tasks(RefineArgs P) {
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
   WarpMem sm = carve<W>(smem + (size_t)wib * warp_smem_bytes<W>(P.stack_cap), P.stack_cap);
   Cnt cnt;
-  for (int i = 0; i < C_NUM; ++i) cnt.v[i] = 0;
+  for (int i = 0; i < C_WARP_NUM; ++i) cnt.v[i] = 0;
   // first the handed-over parity rays (the longest items), one warp each
   const unsigned int np = P.q_par ? min(*P.q_par_n, P.q_par_cap) : 0u;
   for (;;) {
@@ -1509,6 +1512,7 @@ __global__ void __launch_bounds__(128, 4) k_refine_tasks(RefineArgs P) {
       if (lane == 0) atomicCAS(P.err, 0, DERR_STACK);
     }
   }
+  const unsigned long long par_bytes = cnt.v[C_BYTES];
   const unsigned int n = min(*P.q_in_n, P.q_in_cap);
   for (;;) {
     unsigned int t = 0;
@@ -1541,8 +1545,13 @@ __global__ void __launch_bounds__(128, 4) k_refine_tasks(RefineArgs P) {
     }
     if (lane == 0) cnt.v[C_TASKS] += 1;
   }
-  cnt.v[C_BYTES_TASKS] = cnt.v[C_BYTES];
-  for (int i = 0; i < C_NUM; ++i) {
+  cnt.v[C_BYTES_TASKS] = cnt.v[C_BYTES] - par_bytes;
+  {
+    unsigned long long v = par_bytes;
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(FULL, v, o);
+    if (lane == 0 && v) atomicAdd(P.counters + C_BYTES_PARITY, v);
+  }
+  for (int i = 0; i < C_WARP_NUM; ++i) {
     unsigned long long v = cnt.v[i];
     for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(FULL, v, o);
     if (lane == 0 && v) atomicAdd(P.counters + i, v);
@@ -1839,7 +1848,7 @@ pj_status run_join(Ctx *ctx, Dataset *A, Dataset *B, const int32_t *cand,
   unsigned int *qctr = reinterpret_cast<unsigned int *>(d_misc + 3);  // q1 n/pos, q2 n/pos
   // wavefront front end: breadth-first levels before the warp passes (a
   // per-thread parity stack needs the BVH depth to stay within 64 levels)
-  int wave_levels = o->wave_levels > 0 ? o->wave_levels : (o->wave_levels < 0 ? 0 : 12);
+  int wave_levels = o->wave_levels > 0 ? o->wave_levels : (o->wave_levels < 0 ? 0 : 14);
   if (std::max(bA.max_depth, bB.max_depth) > 64) wave_levels = 0;
   const unsigned int wq_cap = 1u << 23;
   uint4 *wqa = nullptr, *wqb = nullptr, *wlq = nullptr, *wpar = nullptr;
@@ -1918,6 +1927,19 @@ pj_status run_join(Ctx *ctx, Dataset *A, Dataset *B, const int32_t *cand,
   if (o->launch_mode == PJ_LAUNCH_PER_PAIR && k != 1)
     return fail(ctx, PJ_ERR_INVALID_ARG, "per-pair launches use one warp per pair");
   const bool graph = o->use_graph != 0;
+  // optional per-launch events of the breadth-first levels (eager runs only)
+  std::vector<cudaEvent_t> kev;
+  struct KevGuard {
+    std::vector<cudaEvent_t> *v;
+    ~KevGuard() {
+      for (auto e : *v) cudaEventDestroy(e);
+    }
+  } kg{&kev};
+  bool kev_used = false;
+  if (o->kernel_times && wave_levels > 0) {
+    kev.resize(2 * (size_t)wave_levels + 1);
+    for (auto &e : kev) PJ_CK(cudaEventCreate(&e));
+  }
   // everything from here to the compacted pairs is a fixed sequence of
   // stream operations (no host synchronisation), so it can be captured
   auto device_part = [&](bool timed) -> pj_status {
@@ -1960,14 +1982,36 @@ pj_status run_join(Ctx *ctx, Dataset *A, Dataset *B, const int32_t *cand,
         const int wblocks = wave_grid[0], lblocks = wave_grid[1], pblocks = wave_grid[2];
         k_wave_init<<<wblocks, 256, 0, s>>>(wa, wqa, qn);
         PJ_CK(launch_pdl(kp, pblocks, 128, 0, s, wa));
+        // the rays over the per-thread node budget, one warp each, before
+        // the front end: a containment-only pair (no crossing to stop at)
+        // is the costliest kind to traverse, so its flag should be set early
+        RefineArgs ap = args;
+        ap.q_in = wqa;
+        ap.q_in_n = misc + 3;  // stays zero: no traversal tasks in this launch
+        ap.q_in_pos = misc + 4;
+        ap.q_out = nullptr;
+        ap.q_out_n = nullptr;
+        ap.budget = 0;
+        ap.q_par = wpar;
+        ap.q_par_n = misc + 1;
+        ap.q_par_pos = misc + 2;
+        ap.q_par_cap = wpar_cap;
+        PJ_CK(launch_pdl(kern_tasks, (int)blocks, threads, smem, s, ap));
         if (timed) PJ_CK(cudaEventRecord(ev[4], s));
         uint4 *qin = wqa, *qout = wqb;
+        const bool kt = timed && !kev.empty();
         for (int lvl = 0; lvl < wave_levels; ++lvl) {
+          if (kt) PJ_CK(cudaEventRecord(kev[2 * lvl], s));
           PJ_CK(launch_pdl(kx, wblocks, 256, 0, s, wa, (const uint4 *)qin,
                            (const unsigned *)(qn + lvl), qout, qn + lvl + 1, wlq, ln + lvl));
+          if (kt) PJ_CK(cudaEventRecord(kev[2 * lvl + 1], s));
           PJ_CK(launch_pdl(kl, lblocks, 256, 0, s, wa, (const uint4 *)wlq,
                            (const unsigned *)(ln + lvl)));
           std::swap(qin, qout);
+        }
+        if (kt) {
+          PJ_CK(cudaEventRecord(kev[2 * wave_levels], s));
+          kev_used = true;
         }
         if (timed) {
           PJ_CK(cudaEventRecord(ev[5], s));
@@ -1978,10 +2022,7 @@ pj_status run_join(Ctx *ctx, Dataset *A, Dataset *B, const int32_t *cand,
         a1.q_in_n = qn + wave_levels;
         a1.q_in_pos = misc;
         a1.q_in_cap = wq_cap;
-        a1.q_par = wpar;
-        a1.q_par_n = misc + 1;
-        a1.q_par_pos = misc + 2;
-        a1.q_par_cap = wpar_cap;
+        a1.q_par = nullptr;
         a1.q_out = budget1 > 0 ? q1 : nullptr;
         a1.q_out_n = qctr;
         a1.budget = budget1;
@@ -2002,7 +2043,7 @@ pj_status run_join(Ctx *ctx, Dataset *A, Dataset *B, const int32_t *cand,
         a3.q_out_n = nullptr;
         a3.budget = 0;
         PJ_CK(launch_pdl(kern_tasks, (int)blocks, threads, smem, s, a3));
-        ctx->launches += 5 + 2 * wave_levels;
+        ctx->launches += 6 + 2 * wave_levels;
       } else {
         PJ_CK(cudaMemsetAsync(d_misc + 2, 0, 24, s));  // work counter, queue counters
         RefineArgs a1 = args;
@@ -2108,6 +2149,17 @@ pj_status run_join(Ctx *ctx, Dataset *A, Dataset *B, const int32_t *cand,
   cudaEventElapsedTime(&ms, e0, e1);
   cudaEventElapsedTime(&out->mbb_ms, ev[0], ev[1]);
   out->parity_ms = out->front_ms = out->tasks_ms = -1.f;
+  out->expand_ms = out->leaf_ms = -1.f;
+  if (kev_used && !replayed) {
+    out->expand_ms = out->leaf_ms = 0.f;
+    for (int l = 0; l < wave_levels; ++l) {
+      float a = 0.f, b = 0.f;
+      cudaEventElapsedTime(&a, kev[2 * l], kev[2 * l + 1]);
+      cudaEventElapsedTime(&b, kev[2 * l + 1], kev[2 * l + 2]);
+      out->expand_ms += a;
+      out->leaf_ms += b;
+    }
+  }
   if (replayed) {
     // one graph launch: refinement and compaction are not separated
     cudaEventElapsedTime(&out->refine_ms, ev[1], ev[3]);

@@ -48,7 +48,7 @@ class pj_join_opts(ctypes.Structure):
                 ("launch_mode", ctypes.c_int32), ("use_graph", ctypes.c_int32),
                 ("out_host", ctypes.c_int32), ("keep_flags", ctypes.c_int32),
                 ("record_cycles", ctypes.c_int32), ("spill_budget", ctypes.c_int32),
-                ("wave_levels", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+                ("wave_levels", ctypes.c_int32), ("kernel_times", ctypes.c_int32)]
 
 
 class pj_pairs(ctypes.Structure):
@@ -58,7 +58,8 @@ class pj_pairs(ctypes.Structure):
                 ("device_ms", ctypes.c_float), ("mbb_ms", ctypes.c_float),
                 ("refine_ms", ctypes.c_float), ("compact_ms", ctypes.c_float),
                 ("parity_ms", ctypes.c_float), ("front_ms", ctypes.c_float),
-                ("tasks_ms", ctypes.c_float), ("reserved3", ctypes.c_float),
+                ("tasks_ms", ctypes.c_float), ("expand_ms", ctypes.c_float),
+                ("leaf_ms", ctypes.c_float), ("reserved3", ctypes.c_float),
                 ("cycles", ctypes.c_void_p), ("impl", ctypes.c_void_p)]
 
 
@@ -67,7 +68,8 @@ class pj_counters(ctypes.Structure):
         "pairs_refined", "node_pairs", "box_tests", "leaf_pairs", "edge_slab_tests",
         "segtri_tests", "exact_fallbacks", "parity_rays", "parity_nodes",
         "parity_tri_tests", "bytes_fetched", "pairs_hit", "kernel_launches",
-        "tasks_spilled", "tasks_resumed", "bytes_tasks")]
+        "tasks_spilled", "tasks_resumed", "bytes_tasks", "bytes_parity", "bytes_expand",
+        "bytes_leaf", "parity_handed_over")]
 
 
 class pj_dataset_info(ctypes.Structure):
@@ -261,7 +263,7 @@ def pj_join_intersects_ex(ctx, a: int, b: int, cand=None, cand_offsets=None, sel
                           width=0, leaf_size=0, warps_per_pair=0, leaf_mode=PJ_LEAF_FILTERED,
                           launch_mode=PJ_LAUNCH_PERSISTENT, use_graph=False, out_host=True,
                           keep_flags=False, record_cycles=False, spill_budget=0, wave_levels=0,
-                          stream=None):
+                          kernel_times=False, stream=None):
     """Run the join.  Returns the filled pj_pairs (free it with pj_free_pairs).
 
     cand / cand_offsets: None (device bounding-box filter join), numpy int32
@@ -276,7 +278,7 @@ def pj_join_intersects_ex(ctx, a: int, b: int, cand=None, cand_offsets=None, sel
         n = int(cand.shape[0])
     opts = pj_join_opts(width, leaf_size, warps_per_pair, leaf_mode, launch_mode,
                         int(use_graph), int(out_host), int(keep_flags), int(record_cycles),
-                        int(spill_budget), int(wave_levels), 0)
+                        int(spill_budget), int(wave_levels), int(kernel_times))
     res = pj_pairs()
     rc = load().pj_join_intersects_ex(ctx, a, b, _ptr(cand), _ptr(cand_offsets), n,
                                       1 if dev else 0, int(self_join), ctypes.byref(opts),
