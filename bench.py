@@ -32,7 +32,7 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "candidate pairs refined/s & segment–tri tests/s; p50/p99 query latency"
-WAVE_LEVELS = 14          # breadth-first levels of the library's default join
+FRONT_LEVELS = {"stream": -2, "wave": 14, "none": -1}   # front end -> pj_join_opts.wave_levels
 UNIT = "pairs/s"
 WORKLOAD = ("pathology join: 10,000 nuclei (icosphere L4/L5, 10% smooth radial noise, "
             "log-normal radius mean 1/200 box) x 500 vessels (16-sided capped tubes on cubic "
@@ -225,7 +225,8 @@ def run_ours(args, rank, world, local_rank):
     build_s = time.perf_counter() - t0
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
     opts = dict(width=args.width, leaf_size=args.leaf, warps_per_pair=args.warps,
-                use_graph=args.graph, out_host=False, stream=stream)
+                use_graph=args.graph, out_host=False, stream=stream,
+                wave_levels=FRONT_LEVELS[args.front])
 
     def step():
         res = pierce.pj_join_intersects_ex(ctx.h, ha, hb, **opts)
@@ -281,12 +282,19 @@ def run_ours(args, rank, world, local_rank):
     per_step = {k: pc[k] / args.steps for k in ("bytes_fetched", "bytes_parity", "bytes_expand",
                                                  "bytes_leaf", "bytes_tasks")}
     peak, peak_kind = measured_peaks()
-    levels = WAVE_LEVELS
     # kernel families of one step: (step ms, algorithmic bytes, launches)
-    fam = {"k_wave_expand": (phase_ms["expand_ms"], per_step["bytes_expand"], levels),
-           "k_wave_leaf": (phase_ms["leaf_ms"], per_step["bytes_leaf"], levels),
-           "k_wave_parity+handover": (phase_ms["parity_ms"], per_step["bytes_parity"], 2),
-           "k_refine_tasks": (phase_ms["tasks_ms"], per_step["bytes_tasks"], 3)}
+    if args.front == "stream":
+        fam = {"k_stream": (phase_ms["front_ms"],
+                            per_step["bytes_expand"] + per_step["bytes_leaf"], 1),
+               "k_wave_parity+handover": (phase_ms["parity_ms"], per_step["bytes_parity"], 2)}
+    elif args.front == "wave":
+        levels = FRONT_LEVELS["wave"]
+        fam = {"k_wave_expand": (phase_ms["expand_ms"], per_step["bytes_expand"], levels),
+               "k_wave_leaf": (phase_ms["leaf_ms"], per_step["bytes_leaf"], levels),
+               "k_wave_parity+handover": (phase_ms["parity_ms"], per_step["bytes_parity"], 2),
+               "k_refine_tasks": (phase_ms["tasks_ms"], per_step["bytes_tasks"], 3)}
+    else:
+        fam = {"k_refine+k_refine_tasks": (phase_ms["refine_ms"], per_step["bytes_fetched"], 3)}
     dom = max(fam, key=lambda k: fam[k][0])
     d_ms, d_bytes, d_launch = fam[dom]
     achieved = d_bytes / (max(d_ms, 1e-6) / 1000.0) / 1e9
@@ -307,6 +315,7 @@ def run_ours(args, rank, world, local_rank):
             "config": {"workload": WORKLOAD, "candidates_per_step": C, "pairs_per_step": K,
                        "bvh_width": args.width, "leaf_size": args.leaf,
                        "warps_per_pair": args.warps or 1, "cuda_graph": bool(args.graph),
+                       "front_end": args.front,
                        "l2": "256 MB buffer written between timed steps",
                        "setup_s": {"generate": round(gen_s, 2), "load": round(load_s, 3),
                                    "bvh_build": round(build_s, 3)}},
@@ -351,6 +360,7 @@ def _end_to_end(ctx, ha, hb, cand_host, args, flush, stream, dist, pierce):
         t0 = time.perf_counter()
         r = pierce.pj_join_intersects_ex(ctx.h, ha, hb, cand=cand_np, width=args.width,
                                          leaf_size=args.leaf, warps_per_pair=args.warps,
+                                         wave_levels=FRONT_LEVELS[args.front],
                                          out_host=True, stream=stream)
         pairs = pierce.pairs_to_numpy(r)
         pierce.pj_free_pairs(ctx.h, r)
@@ -622,6 +632,9 @@ def main():
     ap.add_argument("--leaf", type=int, default=4)
     ap.add_argument("--warps", type=int, default=0)
     ap.add_argument("--graph", type=int, default=1)
+    ap.add_argument("--front", default="wave", choices=sorted(FRONT_LEVELS),
+                    help="refinement front end: streaming persistent kernel, breadth-first "
+                         "levels, or none (per-warp passes only)")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--ref-step-s", type=float, default=10.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")

@@ -76,6 +76,7 @@ typedef struct {
 
 enum { PJ_LEAF_FILTERED = 0, PJ_LEAF_EXACT = 1 };
 enum { PJ_LAUNCH_PERSISTENT = 0, PJ_LAUNCH_PER_PAIR = 1 };
+enum { PJ_FRONT_NONE = -1, PJ_FRONT_STREAM = -2 };  /* pj_join_opts.wave_levels */
 
 /* Options of one join.  Zero-initialised = defaults. */
 typedef struct {
@@ -91,14 +92,20 @@ typedef struct {
   int32_t keep_flags;       /* 1: also return the per-candidate result bytes  */
   int32_t record_cycles;    /* 1: also return each candidate's SM clock cycles
                                (instrumentation of per-pair cost)            */
-  int32_t spill_budget;     /* SM clock cycles a warp spends on one pair in the
-                               first pass before handing the rest of it to
-                               later passes (0: 40,000; < 0: never); the
-                               second pass allows 8 times as many            */
-  int32_t wave_levels;      /* BVH levels descended breadth-first, one thread
-                               per child test, before the per-warp passes
-                               (0: 14; < 0: none)                            */
-  int32_t kernel_times;     /* 1: also time each breadth-first launch with CUDA
+  int32_t spill_budget;     /* per-warp passes (wave_levels != 0): SM clock
+                               cycles a warp spends on one pair in the first
+                               pass before handing the rest of it to later
+                               passes (0: 40,000; < 0: never); the second
+                               pass allows 8 times as many                   */
+  int32_t wave_levels;      /* refinement front end.  > 0: this many BVH
+                               levels breadth-first, one thread per child
+                               test, then the per-warp passes (0: 14 levels).
+                               PJ_FRONT_NONE: the per-warp passes alone.
+                               PJ_FRONT_STREAM: the streaming kernel (one
+                               persistent launch; warps keep the tasks of
+                               many pairs in shared memory and balance the
+                               load through a device task queue)            */
+  int32_t kernel_times;     /* 1: also time the front end's launches with CUDA
                                events (pj_pairs.expand_ms / leaf_ms; events
                                between launches cost a little overlap)       */
 } pj_join_opts;
@@ -120,12 +127,14 @@ typedef struct {
   float compact_ms;         /* of which: compaction                           */
   float parity_ms;          /* refinement phases (CUDA events; -1 when the
                                join was replayed from a graph): parity rays, */
-  float front_ms;           /* breadth-first front end (levels and leaf
-                               pairs),                                       */
+  float front_ms;           /* front end (the streaming launch, or the
+                               breadth-first levels and leaf pairs),         */
   float tasks_ms;           /* and the per-warp passes over what was left     */
-  float expand_ms;          /* with pj_join_opts.kernel_times: summed durations
-                               of the breadth-first node-pair launches,       */
-  float leaf_ms;            /* and of the breadth-first leaf-pair launches    */
+  float expand_ms;          /* with pj_join_opts.kernel_times: the streaming
+                               launch, or the summed durations of the
+                               breadth-first node-pair launches,              */
+  float leaf_ms;            /* and of the breadth-first leaf-pair launches
+                               (0 with the streaming front end)               */
   float reserved3;
   uint32_t *cycles;         /* device, C values (only with record_cycles):
                                clock64 cycles the refinement spent on each

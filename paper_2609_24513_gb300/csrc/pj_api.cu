@@ -85,6 +85,24 @@ void *ws_get(Ctx *ctx, const char *name, size_t bytes, pj_status *st) {
   return w.ptr;
 }
 
+void *ws_get_zeroed(Ctx *ctx, const char *name, size_t bytes, cudaStream_t s, pj_status *st) {
+  Workspace &w = cur_exec(ctx)->ws[name];
+  const void *before = w.ptr;
+  void *p = ws_get(ctx, name, bytes, st);
+  if (!p) return nullptr;
+  if (p != before || !w.zeroed) {
+    cudaError_t e = cudaMemsetAsync(p, 0, w.cap, s);
+    if (e != cudaSuccess) {
+      *st = cuda_fail(ctx, e, name);
+      return nullptr;
+    }
+    w.zeroed = true;
+  }
+  return p;
+}
+
+void ws_mark_dirty(Ctx *ctx, const char *name) { cur_exec(ctx)->ws[name].zeroed = false; }
+
 // ---------------------------------------------------------------------------
 // Load kernels
 // ---------------------------------------------------------------------------

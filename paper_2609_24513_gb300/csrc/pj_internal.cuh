@@ -85,6 +85,7 @@ enum {
 struct Workspace {
   void *ptr = nullptr;
   size_t cap = 0;
+  bool zeroed = false;  // ws_get_zeroed: all-zero as of the last use
 };
 
 // Scratch of one join in flight: workspaces (grown on demand), the device
@@ -138,6 +139,10 @@ pj_status fail(Ctx *c, pj_status code, const std::string &msg);
 pj_status cuda_fail(Ctx *c, cudaError_t e, const char *what);
 void clear_err(Ctx *c);
 void *ws_get(Ctx *c, const char *name, size_t bytes, pj_status *st);
+// A workspace whose users leave it all-zero: cleared on stream s when it is
+// (re)allocated or was marked dirty (a launch that used it failed).
+void *ws_get_zeroed(Ctx *c, const char *name, size_t bytes, cudaStream_t s, pj_status *st);
+void ws_mark_dirty(Ctx *c, const char *name);
 
 #define PJ_CK(call)                                   \
   do {                                                \
@@ -146,7 +151,7 @@ void *ws_get(Ctx *c, const char *name, size_t bytes, pj_status *st);
   } while (0)
 
 // device error codes written by kernels
-enum { DERR_NONE = 0, DERR_STACK = 1, DERR_QUEUE = 2, DERR_OFFSET = 3 };
+enum { DERR_NONE = 0, DERR_STACK = 1, DERR_QUEUE = 2, DERR_OFFSET = 3, DERR_TIMEOUT = 4 };
 
 // build.cu
 pj_status build_bvh(Ctx *ctx, Dataset *ds, int W, int L, cudaStream_t s);

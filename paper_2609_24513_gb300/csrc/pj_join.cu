@@ -432,6 +432,13 @@ __device__ __forceinline__ uint2 make_task(uint32_t a, const Box &ba, uint32_t b
   return make_uint2(a | (xa ? kExpand : 0u), b | (xb ? kExpand : 0u));
 }
 
+// Algorithmic bytes of one (node, node) step: the W child slots of each side
+// that expands, the one box slot of each side that does not (32 B a slot).
+template <int W>
+__device__ __forceinline__ unsigned node_pair_bytes(bool xa, bool xb) {
+  return (unsigned)((xa ? W : 1) + (xb ? W : 1)) * 32u;
+}
+
 __device__ __forceinline__ int task_tests(uint2 t, int W) {
   return ((t.x & kExpand) ? W : 1) * ((t.y & kExpand) ? W : 1);
 }
@@ -654,6 +661,7 @@ __device__ int pair_cross(const Side &A, const Side &B, int ia, int ib, F3 off,
       if (lane < npop) {
         sm.tq[lane] = t;
         sm.tpre[lane] = incl - nt;
+        cnt.v[C_BYTES] += node_pair_bytes<W>(t.x & kExpand, t.y & kExpand);
       }
       __syncwarp();
       sp -= npop;
@@ -711,7 +719,6 @@ __device__ int pair_cross(const Side &A, const Side &B, int ia, int ib, F3 off,
         if (both) sm.lq[nlq + __popc(m2 & lt)] = make_uint2(na, nb);
         sp += __popc(m1);
         nlq += __popc(m2);
-        if (act) cnt.v[C_BYTES] += 64;
       }
       if (lane == 0) {
         cnt.v[C_NODE_PAIRS] += npop;
@@ -1184,8 +1191,10 @@ __global__ void __launch_bounds__(256) k_wave_expand(WaveArgs P, const uint4 *qi
         item_box<W>(P.A.nodes, e.y, zero, ba);
         na = e.y & ~kExpand;
       }
-      if (i == 0) cnt[0] += 1;
-      cnt[2] += 32;
+      if (i == 0) {
+        cnt[0] += 1;
+        cnt[2] += node_pair_bytes<W>(xa, xb);
+      }
     }
     if (live) {
       if (xb) {
@@ -1195,7 +1204,6 @@ __global__ void __launch_bounds__(256) k_wave_expand(WaveArgs P, const uint4 *qi
           uint32_t cb;
           load_slot<W>(P.B.nodes, e.z & kIdx, j, off, bb, cb);
           cnt[1] += 1;
-          cnt[2] += 32;
           if (cb == kEmpty || !overlap(ba, bb)) continue;
           const bool lb = cb & kLeafBit;
           if ((na & kLeafBit) && lb) leaf_mask |= 1u << j;
@@ -1205,7 +1213,6 @@ __global__ void __launch_bounds__(256) k_wave_expand(WaveArgs P, const uint4 *qi
         Box bb;
         item_box<W>(P.B.nodes, e.z, off, bb);
         cnt[1] += 1;
-        cnt[2] += 32;
         if (overlap(ba, bb)) {
           if ((na & kLeafBit) && (e.z & kLeafBit)) leaf_mask = 1u;
           else task_mask = 1u;
@@ -1250,9 +1257,79 @@ __global__ void __launch_bounds__(256) k_wave_expand(WaveArgs P, const uint4 *qi
   block_flush<4>(P.counters, slots, v);
 }
 
-// Leaf pairs: 2L threads per pair (the L source triangles of each side);
-// each thread slab-tests its triangle's owned edges against the other leaf's
-// box and tests them exactly against the other leaf's triangles.
+// Per-thread counters of the leaf-pair work (32-bit: one thread's share of
+// one launch stays far below 2^32).
+struct LeafCnt {
+  unsigned lp = 0, slab = 0, st = 0, fb = 0, bytes = 0;
+};
+
+// One unit of a leaf pair e = (candidate, leaf item A, leaf item B): unit u
+// in [0, 2L) takes source triangle u mod L of side A (u < L) or of side B,
+// slab-tests its owned edges against the other leaf's box and tests them
+// exactly against the other leaf's triangles.  Returns true on a crossing.
+template <int W, bool EXACT>
+__device__ __forceinline__ bool leaf_unit(const WaveArgs &P, const uint4 e, const int u,
+                                          LeafCnt &cn) {
+  const F3 zero = mkf3(0.f, 0.f, 0.f);
+  const bool dirA = (u >> P.lshift) == 0;
+  const int k = u & ((1 << P.lshift) - 1);
+  const uint32_t sslot = (dirA ? e.y : e.z) & kIdx, tslot = (dirA ? e.z : e.y) & kIdx;
+  const Side &S = dirA ? P.A : P.B;
+  const Side &T = dirA ? P.B : P.A;
+  Box sbox, tb;
+  uint32_t sdesc, tdesc;
+  load_slot<W>(S.nodes, sslot / W, (int)(sslot % W), zero, sbox, sdesc);
+  if (k > (int)(sdesc & 7u)) return false;
+  const int ia = P.cand[2 * (int64_t)e.x], ib = P.cand[2 * (int64_t)e.x + 1];
+  const F3 off = cand_offset(P, e.x);
+  const F3 soff = dirA ? zero : off, toff = dirA ? off : zero;
+  load_slot<W>(T.nodes, tslot / W, (int)(tslot % W), toff, tb, tdesc);
+  if (u == 0) cn.lp += 1;
+  const int64_t sbase = __float_as_int(S.mrec[3 * (int64_t)(dirA ? ia : ib) + 2].y);
+  const int64_t tbase = __float_as_int(T.mrec[3 * (int64_t)(dirA ? ib : ia) + 2].y);
+  const int64_t s_rec = sbase + ((sdesc >> 3) & 0x0FFFFFFFu) + k;
+  const int64_t t_first = tbase + ((tdesc >> 3) & 0x0FFFFFFFu);
+  const int t_n = (int)(tdesc & 7u) + 1;
+  F3 v[3];
+  int own;
+  load_tri(S.trirec, s_rec, soff, v[0], v[1], v[2], own);
+  // the source triangle and the two leaf slots (source descriptor, target
+  // box and descriptor)
+  cn.bytes += 48 + 64;
+  for (int ek = 0; ek < 3; ++ek) {
+    if (!((own >> ek) & 1)) continue;
+    const F3 p = v[ek], qv = v[ek == 2 ? 0 : ek + 1];
+    Seg sg = make_seg(p, qv);
+    cn.slab += 1;
+    if (!slab_hit(sg, tb.lo, tb.hi)) continue;
+    const F3 elo = mkf3(fminf(p.x, qv.x), fminf(p.y, qv.y), fminf(p.z, qv.z));
+    const F3 ehi = mkf3(fmaxf(p.x, qv.x), fmaxf(p.y, qv.y), fmaxf(p.z, qv.z));
+    for (int t = 0; t < t_n; ++t) {
+      F3 a, b, c;
+      int town;
+      load_tri(T.trirec, t_first + t, toff, a, b, c, town);
+      cn.bytes += 48;
+      const float lx = fminf(a.x, fminf(b.x, c.x)), hx = fmaxf(a.x, fmaxf(b.x, c.x));
+      const float ly = fminf(a.y, fminf(b.y, c.y)), hy = fmaxf(a.y, fmaxf(b.y, c.y));
+      const float lz = fminf(a.z, fminf(b.z, c.z)), hz = fmaxf(a.z, fmaxf(b.z, c.z));
+      if (lx > ehi.x || elo.x > hx || ly > ehi.y || elo.y > hy || lz > ehi.z || elo.z > hz)
+        continue;
+      cn.st += 1;
+      bool r;
+      if (EXACT) {
+        r = segtri_exact_staged(p, qv, a, b, c);
+      } else {
+        bool ex = false;
+        r = segtri_filtered(p, qv, a, b, c, &ex);
+        cn.fb += ex ? 1 : 0;
+      }
+      if (r) return true;
+    }
+  }
+  return false;
+}
+
+// Leaf pairs: 2L threads per pair (the L source triangles of each side).
 template <int W, bool EXACT>
 __global__ void __launch_bounds__(256, 3) k_wave_leaf(WaveArgs P, const uint4 *lq, const unsigned *lq_n) {
   pdl_wait();
@@ -1260,73 +1337,15 @@ __global__ void __launch_bounds__(256, 3) k_wave_leaf(WaveArgs P, const uint4 *l
   const int sh = P.lshift + 1;               // 2L = 1 << sh threads per pair
   const int64_t n = (int64_t)min(*lq_n, P.q_cap) << sh;
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  const F3 zero = mkf3(0.f, 0.f, 0.f);
-  unsigned long long c_slab = 0, c_st = 0, c_fb = 0, c_bytes = 0, c_lp = 0;
+  LeafCnt cn;
   for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < n; g += stride) {
     const uint4 e = lq[g >> sh];
     const int u = (int)(g & ((1 << sh) - 1));
     if (P.flags[e.x]) continue;
-    const bool dirA = (u >> P.lshift) == 0;
-    const int k = u & ((1 << P.lshift) - 1);
-    const uint32_t sslot = (dirA ? e.y : e.z) & kIdx, tslot = (dirA ? e.z : e.y) & kIdx;
-    const Side &S = dirA ? P.A : P.B;
-    const Side &T = dirA ? P.B : P.A;
-    Box sbox, tb;
-    uint32_t sdesc, tdesc;
-    load_slot<W>(S.nodes, sslot / W, (int)(sslot % W), zero, sbox, sdesc);
-    if (k > (int)(sdesc & 7u)) continue;
-    const int ia = P.cand[2 * (int64_t)e.x], ib = P.cand[2 * (int64_t)e.x + 1];
-    const F3 off = cand_offset(P, e.x);
-    const F3 soff = dirA ? zero : off, toff = dirA ? off : zero;
-    load_slot<W>(T.nodes, tslot / W, (int)(tslot % W), toff, tb, tdesc);
-    if (u == 0) c_lp += 1;
-    const int64_t sbase = __float_as_int(S.mrec[3 * (int64_t)(dirA ? ia : ib) + 2].y);
-    const int64_t tbase = __float_as_int(T.mrec[3 * (int64_t)(dirA ? ib : ia) + 2].y);
-    const int64_t s_rec = sbase + ((sdesc >> 3) & 0x0FFFFFFFu) + k;
-    const int64_t t_first = tbase + ((tdesc >> 3) & 0x0FFFFFFFu);
-    const int t_n = (int)(tdesc & 7u) + 1;
-    F3 v[3];
-    int own;
-    load_tri(S.trirec, s_rec, soff, v[0], v[1], v[2], own);
-    c_bytes += 48 + 64;
-    bool hit = false;
-    for (int ek = 0; ek < 3 && !hit; ++ek) {
-      if (!((own >> ek) & 1)) continue;
-      const F3 p = v[ek], qv = v[ek == 2 ? 0 : ek + 1];
-      Seg sg = make_seg(p, qv);
-      c_slab += 1;
-      if (!slab_hit(sg, tb.lo, tb.hi)) continue;
-      const F3 elo = mkf3(fminf(p.x, qv.x), fminf(p.y, qv.y), fminf(p.z, qv.z));
-      const F3 ehi = mkf3(fmaxf(p.x, qv.x), fmaxf(p.y, qv.y), fmaxf(p.z, qv.z));
-      for (int t = 0; t < t_n; ++t) {
-        F3 a, b, c;
-        int town;
-        load_tri(T.trirec, t_first + t, toff, a, b, c, town);
-        c_bytes += 48;
-        const float lx = fminf(a.x, fminf(b.x, c.x)), hx = fmaxf(a.x, fmaxf(b.x, c.x));
-        const float ly = fminf(a.y, fminf(b.y, c.y)), hy = fmaxf(a.y, fmaxf(b.y, c.y));
-        const float lz = fminf(a.z, fminf(b.z, c.z)), hz = fmaxf(a.z, fmaxf(b.z, c.z));
-        if (lx > ehi.x || elo.x > hx || ly > ehi.y || elo.y > hy || lz > ehi.z || elo.z > hz)
-          continue;
-        c_st += 1;
-        bool r;
-        if (EXACT) {
-          r = segtri_exact_staged(p, qv, a, b, c);
-        } else {
-          bool ex = false;
-          r = segtri_filtered(p, qv, a, b, c, &ex);
-          c_fb += ex ? 1 : 0;
-        }
-        if (r) {
-          hit = true;
-          break;
-        }
-      }
-    }
-    if (hit) P.flags[e.x] = 1;
+    if (leaf_unit<W, EXACT>(P, e, u, cn)) P.flags[e.x] = 1;
   }
   const int slots[6] = {C_LEAF_PAIRS, C_SLAB_TESTS, C_SEGTRI, C_FALLBACK, C_BYTES, C_BYTES_LEAF};
-  const unsigned long long v[6] = {c_lp, c_slab, c_st, c_fb, c_bytes, c_bytes};
+  const unsigned long long v[6] = {cn.lp, cn.slab, cn.st, cn.fb, cn.bytes, cn.bytes};
   block_flush<6>(P.counters, slots, v);
 }
 
@@ -1559,6 +1578,536 @@ __global__ void __launch_bounds__(128, 4) k_refine_tasks(RefineArgs P) {
 }
 
 // ---------------------------------------------------------------------------
+// Streaming refinement.  A persistent kernel whose warps each keep a task
+// stack and a leaf-pair queue in shared memory holding the tasks of many
+// candidate pairs at once, so that every traversal round fills the warp:
+// W lanes per popped (node, node) task (lane i tests child i of one side
+// against the other side's children), 2L lanes per leaf pair.  A warp takes
+// 32 new candidates whenever its stack holds less than one round.
+//
+// Load balance.  A few pairs (a nucleus lying along a vessel wall over a
+// large area) cost thousands of times the mean, and a warp that holds one
+// would finish long after the others.  So the warps share a device task
+// queue: a warp with no input and no tasks left becomes hungry and claims
+// tasks from the queue; a straggler -- a warp that has not been able to take
+// new work for `give_after` SM cycles, while most warps take some every few
+// rounds -- that sees hungry warps gives the older half of its stack (the
+// larger subtrees) to the queue, and so does a warp whose stack is nearly
+// full.  A costly pair thus spreads over more and more warps.  At most
+// `hungry_max` warps wait for tasks (a warp that finds that many waiting
+// leaves): a heavy pair needs tens of helpers, not thousands of warps
+// polling the same words.  A crossing sets the candidate's flag; the tasks
+// of a flagged candidate are dropped when popped or claimed.
+//
+// Queue protocol.  Entries are uint4 (candidate, item A, item B, ready).  A
+// producer reserves slots with an atomic add on `tail`, writes the first
+// three words, fences, sets ready = 1, fences, and adds the count to
+// `avail` (entries published, not yet claimed).  A consumer takes k of them
+// by an atomic subtract on `avail` (undone if fewer than k were left), then
+// an atomic add on `head` gives it k slot positions; every reserved slot is
+// written without waiting on anything, so it waits for ready on each (a
+// bounded wait), reads the slot through L2 and sets ready back to 0: the
+// queue is all-zero again when the launch ends.  `active` counts the warps
+// that hold work.  A waiting warp leaves once `active` is 0 and nothing is
+// published, and a warp over the waiting cap leaves at once if nothing is
+// published.  No warp leaves while published entries wait (a consumer whose
+// subtract failed stays to retry), so whatever was pushed is taken by a
+// warp that is still there, if need be by its producer: leaving early costs
+// helpers, never work.  Every wait is bounded: on expiry the kernel records
+// an error and the host redoes the join by plain depth-first traversal.
+// ---------------------------------------------------------------------------
+// One leaf-pair unit (as leaf_unit) with every load issued as early as it
+// can be: the leaf slots and the pair's triangle bases (written at intake)
+// first, then the source triangle and the target leaf's triangles together,
+// then the tests from registers.  A warp of the streaming kernel does one
+// round at a time, so each serial load would be a full memory latency.
+template <int W, bool EXACT>
+__device__ __forceinline__ bool stream_leaf_unit(const WaveArgs &Q, const int2 *cbase,
+                                                 const uint4 e, const int u, LeafCnt &cn) {
+  const F3 zero = mkf3(0.f, 0.f, 0.f);
+  const bool dirA = (u >> Q.lshift) == 0;
+  const int k = u & ((1 << Q.lshift) - 1);
+  const uint32_t sslot = (dirA ? e.y : e.z) & kIdx, tslot = (dirA ? e.z : e.y) & kIdx;
+  const Side &S = dirA ? Q.A : Q.B;
+  const Side &T = dirA ? Q.B : Q.A;
+  const F3 off = cand_offset(Q, e.x);
+  const F3 soff = dirA ? zero : off, toff = dirA ? off : zero;
+  const uint32_t sdesc = __float_as_uint(
+      __ldg(S.nodes + (int64_t)(sslot / W) * Cfg<W>::SW + 8 * (sslot % W + 1) + 6));
+  Box tb;
+  uint32_t tdesc;
+  load_slot<W>(T.nodes, tslot / W, (int)(tslot % W), toff, tb, tdesc);
+  const int2 cb = cbase[e.x];
+  if (k > (int)(sdesc & 7u)) return false;
+  if (u == 0) cn.lp += 1;
+  const int64_t s_rec = (int64_t)(dirA ? cb.x : cb.y) + ((sdesc >> 3) & 0x0FFFFFFFu) + k;
+  const int64_t t_first = (int64_t)(dirA ? cb.y : cb.x) + ((tdesc >> 3) & 0x0FFFFFFFu);
+  const int t_n = (int)(tdesc & 7u) + 1;
+  F3 v[3];
+  int own;
+  load_tri(S.trirec, s_rec, soff, v[0], v[1], v[2], own);
+  cn.bytes += 48 + 64;
+  for (int t0 = 0; t0 < t_n; t0 += 4) {
+    // up to four target triangles per batch of loads
+    F3 ta[4], tbv[4], tc[4];
+    int town;
+#pragma unroll
+    for (int t = 0; t < 4; ++t)
+      if (t0 + t < t_n) load_tri(T.trirec, t_first + t0 + t, toff, ta[t], tbv[t], tc[t], town);
+    const int tn = min(4, t_n - t0);
+    for (int ek = 0; ek < 3; ++ek) {
+      if (!((own >> ek) & 1)) continue;
+      const F3 p = sel_f3<3>(v, ek), qv = sel_f3<3>(v, ek == 2 ? 0 : ek + 1);
+      if (t0 == 0) cn.slab += 1;
+      Seg sg = make_seg(p, qv);
+      if (!slab_hit(sg, tb.lo, tb.hi)) continue;
+      cn.bytes += 48u * tn;
+      const F3 elo = mkf3(fminf(p.x, qv.x), fminf(p.y, qv.y), fminf(p.z, qv.z));
+      const F3 ehi = mkf3(fmaxf(p.x, qv.x), fmaxf(p.y, qv.y), fmaxf(p.z, qv.z));
+#pragma unroll 1
+      for (int t = 0; t < tn; ++t) {
+        const F3 a = sel_f3<4>(ta, t), b = sel_f3<4>(tbv, t), c = sel_f3<4>(tc, t);
+        const float lx = fminf(a.x, fminf(b.x, c.x)), hx = fmaxf(a.x, fmaxf(b.x, c.x));
+        const float ly = fminf(a.y, fminf(b.y, c.y)), hy = fmaxf(a.y, fmaxf(b.y, c.y));
+        const float lz = fminf(a.z, fminf(b.z, c.z)), hz = fmaxf(a.z, fmaxf(b.z, c.z));
+        if (lx > ehi.x || elo.x > hx || ly > ehi.y || elo.y > hy || lz > ehi.z || elo.z > hz)
+          continue;
+        cn.st += 1;
+        bool r;
+        if (EXACT) {
+          r = segtri_exact_staged(p, qv, a, b, c);
+        } else {
+          bool ex = false;
+          r = segtri_filtered(p, qv, a, b, c, &ex);
+          cn.fb += ex ? 1 : 0;
+        }
+        if (r) return true;
+      }
+    }
+  }
+  return false;
+}
+
+template <int W>
+struct StreamCfg {
+  static constexpr int TPR = 32 / W;                               // tasks per round
+  static constexpr int SC = W == 8 ? 384 : 256;                    // stack entries
+  static constexpr int LQ = W == 8 ? 288 : (W == 4 ? 160 : 96);    // leaf-pair entries
+  static constexpr int warp_bytes = (SC + LQ) * 16;
+};
+
+// control words of one launch (zeroed before it), each on its own 128-byte
+// line: ctl[k * SQ_STRIDE]
+enum { SQ_INTAKE = 0, SQ_TAIL, SQ_HEAD, SQ_AVAIL, SQ_ACTIVE, SQ_HUNGRY, SQ_NUM };
+constexpr int SQ_STRIDE = 32;
+constexpr int SQ_WORDS = SQ_NUM * SQ_STRIDE;
+
+struct StreamArgs {
+  WaveArgs w;               // meshes, candidates, flags, counters, error word
+  unsigned int *ctl;        // SQ_* words
+  uint4 *dq;                // shared task queue (all-zero between launches)
+  int2 *cbase;              // per candidate: first triangle of each mesh
+  unsigned int dq_cap;
+  unsigned int spin_limit;  // bound on the polls of every wait (each sleeps <= 1 us)
+  unsigned int hungry_max;  // warps that may wait for queued tasks
+  long long give_after;     // SM cycles without new work that make a straggler
+};
+
+// the launch's control word k
+__device__ __forceinline__ unsigned *sq(const StreamArgs &P, int k) {
+  return P.ctl + k * SQ_STRIDE;
+}
+
+template <int W>
+__host__ __device__ constexpr int stream_warp_bytes() { return StreamCfg<W>::warp_bytes; }
+
+__device__ __forceinline__ unsigned ld_vol(const unsigned *p) {
+  return *reinterpret_cast<volatile const unsigned *>(p);
+}
+
+// give stk[0, n) to the queue (all lanes; n > 0); false if it is full
+__device__ __forceinline__ bool queue_push(const StreamArgs &P, const uint4 *stk, int n,
+                                           int lane) {
+  unsigned base = 0;
+  if (lane == 0) base = atomicAdd(sq(P, SQ_TAIL), (unsigned)n);
+  base = __shfl_sync(FULL, base, 0);
+  if ((uint64_t)base + (uint64_t)n > (uint64_t)P.dq_cap) return false;
+  for (int k = lane; k < n; k += 32) {
+    const uint4 v = stk[k];
+    uint4 *d = P.dq + base + k;
+    d->x = v.x;
+    d->y = v.y;
+    d->z = v.z;
+  }
+  __threadfence();
+  for (int k = lane; k < n; k += 32)
+    *reinterpret_cast<volatile unsigned *>(&P.dq[base + k].w) = 1u;
+  __threadfence();
+  __syncwarp();
+  if (lane == 0) atomicAdd(reinterpret_cast<int *>(sq(P, SQ_AVAIL)), n);
+  return true;
+}
+
+// drop stk[0, n) by moving stk[n, sp) down (all lanes)
+__device__ __forceinline__ void stack_drop_bottom(uint4 *stk, int n, int sp, int lane) {
+  __syncwarp();
+  for (int k0 = 0; k0 < sp - n; k0 += 32) {
+    const int k = k0 + lane;
+    const uint4 v = k < sp - n ? stk[n + k] : make_uint4(0u, 0u, 0u, 0u);
+    __syncwarp();
+    if (k < sp - n) stk[k] = v;
+    __syncwarp();
+  }
+}
+
+
+template <int W, bool EXACT>
+__global__ void __launch_bounds__(128, 4) k_stream(StreamArgs P) {
+  pdl_wait();
+  pdl_trigger();
+  using Cf = StreamCfg<W>;
+  extern __shared__ __align__(16) unsigned char smem[];
+  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+  uint4 *stk = reinterpret_cast<uint4 *>(smem) + (size_t)wib * (Cf::SC + Cf::LQ);
+  uint4 *lq = stk + Cf::SC;
+  const WaveArgs &Q = P.w;
+  const unsigned lt = (1u << lane) - 1u;
+  const int grp = lane / W, gi = lane - grp * W;  // task group, lane in the group
+  const int lsh = Q.lshift + 1;                   // 2L = 1 << lsh lanes per leaf pair
+  const int lpr = 32 >> lsh;                      // leaf pairs per round
+  const F3 zero = mkf3(0.f, 0.f, 0.f);
+  volatile const uint8_t *vflags = Q.flags;
+  const int64_t n_in = *Q.n_cand;
+  if (blockIdx.x == 0 && threadIdx.x == 0 && n_in > 0)
+    atomicAdd(Q.counters + C_PAIRS, (unsigned long long)n_in);
+  // counters: node pairs, box tests, tasks claimed from / given to the queue
+  unsigned c_np = 0, c_bt = 0, c_res = 0, c_sp = 0;
+  unsigned c_bx = 0;  // node bytes
+  LeafCnt lc;
+  int sp = 0, nlq = 0;
+  bool more = true;   // candidates may be left
+  long long t_new = clock64();  // when this warp last took (or tried to take) work
+  int err = DERR_NONE;
+  unsigned iters = 0;
+  // Every 4th iteration lane 0 reads the intake position (a warp busy with a
+  // costly pair takes no input and would not notice that it has run out) or,
+  // once it has, the hungry count; the next iteration uses the value, so the
+  // load overlaps one round of work.
+  unsigned peek = 0;
+  bool peeked = false, peek_more = false;
+  bool registered = true;  // counted in SQ_ACTIVE
+  if (lane == 0) atomicAdd(sq(P, SQ_ACTIVE), 1u);
+
+  // one round over up to lpr leaf pairs from the top of the queue
+  auto leaf_round = [&]() {
+    const int np = min(nlq, lpr);
+    const int p = lane >> lsh, u = lane & ((1 << lsh) - 1);
+    const bool act = p < np;
+    const uint4 e = act ? lq[nlq - 1 - p] : make_uint4(0u, 0u, 0u, 0u);
+    __syncwarp();
+    nlq -= np;
+    if (act && vflags[e.x] == 0) {
+      if (stream_leaf_unit<W, EXACT>(Q, P.cbase, e, u, lc)) Q.flags[e.x] = 1;
+    }
+  };
+
+  // give the older half of the stack to the queue
+  auto give_half = [&](int n) -> bool {
+    if (!queue_push(P, stk, n, lane)) return false;
+    c_sp += lane == 0 ? (unsigned)n : 0u;
+    stack_drop_bottom(stk, n, sp, lane);
+    sp -= n;
+    return true;
+  };
+
+  for (;;) {
+    if (++iters > (1u << 28)) {  // defensive bound: the work is finite
+      err = DERR_STACK;
+      break;
+    }
+    bool give = false;
+    if (peeked) {
+      peeked = false;
+      const unsigned v = __shfl_sync(FULL, peek, 0);
+      if (peek_more) {
+        if ((int64_t)v >= n_in) more = false;
+      } else {
+        give = v > 0 && __shfl_sync(FULL, (int)(clock64() - t_new > P.give_after), 0);
+      }
+    }
+    if ((iters & 3u) == 0) {
+      if (lane == 0) peek = ld_vol(sq(P, more ? SQ_INTAKE : SQ_HUNGRY));
+      peeked = true;
+      peek_more = more;
+    }
+    // 1. intake, while the stack holds less than one round
+    if (more && sp < Cf::TPR && nlq < lpr) {
+      unsigned base = 0;
+      if (lane == 0) base = atomicAdd(sq(P, SQ_INTAKE), 32u);
+      base = __shfl_sync(FULL, base, 0);
+      t_new = clock64();
+      if ((int64_t)base >= n_in) {
+        more = false;
+        continue;
+      }
+      const int64_t idx = (int64_t)base + lane;
+      bool push = false;
+      uint4 ent = make_uint4(0u, 0u, 0u, 0u);
+      if (idx < n_in && vflags[idx] == 0) {
+        const int ia = Q.cand[2 * idx], ib = Q.cand[2 * idx + 1];
+        if (ia >= 0 && ia < Q.MA && ib >= 0 && ib < Q.MB) {
+          const F3 off = cand_offset(Q, idx);
+          Box ba, bb;
+          const float4 a0 = Q.A.mrec[3 * (int64_t)ia], a1 = Q.A.mrec[3 * (int64_t)ia + 1];
+          const float4 b0 = Q.B.mrec[3 * (int64_t)ib], b1 = Q.B.mrec[3 * (int64_t)ib + 1];
+          const float ta = Q.A.mrec[3 * (int64_t)ia + 2].y, tbs = Q.B.mrec[3 * (int64_t)ib + 2].y;
+          const uint32_t ra = (uint32_t)Q.A.roots[ia], rb = (uint32_t)Q.B.roots[ib];
+          ba.lo = mkf3(a0.x, a0.y, a0.z);
+          ba.hi = mkf3(a1.x, a1.y, a1.z);
+          bb.lo = add(mkf3(b0.x, b0.y, b0.z), off);
+          bb.hi = add(mkf3(b1.x, b1.y, b1.z), off);
+          if (overlap(ba, bb)) {
+            const uint2 t = make_task(ra, ba, rb, bb);
+            ent = make_uint4((uint32_t)idx, t.x, t.y, 0u);
+            P.cbase[idx] = make_int2(__float_as_int(ta), __float_as_int(tbs));
+            push = true;
+          }
+        }
+      }
+      // room: sp < TPR <= 16 and 32 more stay below SC
+      const unsigned m = __ballot_sync(FULL, push);
+      if (push) stk[sp + __popc(m & lt)] = ent;
+      sp += __popc(m);
+      __syncwarp();
+      continue;
+    }
+    // 2. out of work: claim tasks from the queue, or leave
+    if (sp == 0 && nlq == 0) {
+      if (more) continue;
+      int64_t h = -1;
+      int k = 0;
+      if (lane == 0) {
+        __threadfence();  // this warp's pushes before it stops counting as active
+        atomicSub(sq(P, SQ_ACTIVE), 1u);
+        // over the cap a warp may leave only while nothing is published:
+        // entries it pushed itself might otherwise outlive every waiting warp
+        int *avail = reinterpret_cast<int *>(sq(P, SQ_AVAIL));
+        bool wait = atomicAdd(sq(P, SQ_HUNGRY), 1u) < P.hungry_max;
+        if (!wait) {
+          __threadfence();
+          wait = *reinterpret_cast<volatile int *>(avail) > 0;
+        }
+        unsigned nap = 128;
+        for (unsigned it = 0; wait; ++it) {
+          if (it >= P.spin_limit) {
+            err = DERR_TIMEOUT;
+            break;
+          }
+          if (ld_vol(reinterpret_cast<const unsigned *>(Q.err)) != 0u) break;  // failing
+          const int av = *reinterpret_cast<volatile int *>(avail);
+          if (av > 0) {
+            const int want = min(av, Cf::TPR);
+            if (atomicSub(avail, want) >= want) {
+              h = atomicAdd(sq(P, SQ_HEAD), (unsigned)want);
+              atomicAdd(sq(P, SQ_ACTIVE), 1u);
+              k = want;
+              break;
+            }
+            atomicAdd(avail, want);  // fewer were left: undo, retry
+            nap = 64;
+          } else {
+            __threadfence();
+            if (ld_vol(sq(P, SQ_ACTIVE)) == 0u) {
+              __threadfence();
+              if (*reinterpret_cast<volatile int *>(avail) <= 0) break;  // nothing left: leave
+            }
+          }
+          __nanosleep(nap);
+          nap = min(nap * 2, 1024u);
+        }
+        atomicSub(sq(P, SQ_HUNGRY), 1u);
+      }
+      err = __shfl_sync(FULL, err, 0);
+      h = __shfl_sync(FULL, h, 0);
+      k = __shfl_sync(FULL, k, 0);
+      registered = h >= 0;
+      if (h < 0) break;
+      t_new = clock64();
+      // take the claimed entries (their producers may still be writing them)
+      bool tpush = false, lpush = false;
+      uint4 ent = make_uint4(0u, 0u, 0u, 0u);
+      bool late = false;
+      if (lane < k) {
+        volatile unsigned *rdy = reinterpret_cast<volatile unsigned *>(&P.dq[h + lane].w);
+        unsigned it = 0;
+        while (*rdy == 0u) {
+          if (++it >= P.spin_limit) {
+            late = true;
+            break;
+          }
+          __nanosleep(64);
+        }
+        if (!late) {
+          __threadfence();
+          ent = __ldcg(P.dq + h + lane);
+          *rdy = 0u;
+          if (vflags[ent.x] == 0) {
+            const bool leafs = (ent.y & kLeafBit) && (ent.z & kLeafBit);
+            lpush = leafs;
+            tpush = !leafs;
+          }
+        }
+      }
+      if (__any_sync(FULL, late)) {
+        err = DERR_TIMEOUT;
+        break;
+      }
+      c_res += lane == 0 ? (unsigned)k : 0u;
+      const unsigned mt = __ballot_sync(FULL, tpush), ml = __ballot_sync(FULL, lpush);
+      if (tpush) stk[__popc(mt & lt)] = ent;
+      if (lpush) lq[__popc(ml & lt)] = ent;
+      sp = __popc(mt);
+      nlq = __popc(ml);
+      __syncwarp();
+      continue;
+    }
+    // 3. a straggler and hungry warps: give the older half of the stack
+    if (give && sp >= 2 * Cf::TPR) {
+      if (!give_half(sp / 2)) {
+        err = DERR_QUEUE;
+        break;
+      }
+    }
+    // 4. leaf pairs once a round's worth is queued (or nothing else is left)
+    if (nlq >= lpr || sp == 0) {
+      leaf_round();
+      continue;
+    }
+    // 5. expand round: pop up to TPR tasks whose children fit
+    int npop = min(Cf::TPR, sp);
+    while (npop > 0 && (sp - npop + npop * W * W > Cf::SC || nlq + npop * W * W > Cf::LQ)) --npop;
+    if (npop == 0) {
+      // the stack is nearly full: its older half goes to the queue
+      if (!give_half(Cf::SC / 2)) {
+        err = DERR_QUEUE;
+        break;
+      }
+      continue;
+    }
+    const bool act = grp < npop;
+    const uint4 t = act ? stk[sp - 1 - grp] : make_uint4(0u, 0u, 0u, 0u);
+    __syncwarp();
+    sp -= npop;
+    const bool xa = t.y & kExpand, xb = t.z & kExpand;
+    // every load of the round at once: the flag, the A slot, the B slots
+    // (all W when both sides expand, in batches of four)
+    const uint8_t fl = act ? vflags[t.x] : (uint8_t)1;
+    const F3 off = act ? cand_offset(Q, t.x) : zero;
+    Box ba;
+    uint32_t na = 0;
+    bool live = act;
+    if (act) {
+      if (xa) {
+        uint32_t ca;
+        load_slot<W>(Q.A.nodes, t.y & kIdx, gi, zero, ba, ca);
+        live = ca != kEmpty;
+        na = (ca & kLeafBit) ? (kLeafBit | ((t.y & kIdx) * W + gi)) : ca;
+      } else {
+        item_box<W>(Q.A.nodes, t.y, zero, ba);
+        na = t.y & ~kExpand;
+      }
+    }
+    constexpr int PB = W < 2 ? W : 2;  // B slots per batch of loads
+    const int nbj = (act && xa && xb) ? W : 1;
+    unsigned tmask = 0, lmask = 0;
+#pragma unroll
+    for (int j0 = 0; j0 < W; j0 += PB) {
+      Box bb[PB];
+      uint32_t cb[PB];
+#pragma unroll
+      for (int q = 0; q < PB; ++q) {
+        cb[q] = kEmpty;
+        if (!act || j0 + q >= nbj) continue;
+        if (xb) {
+          load_slot<W>(Q.B.nodes, t.z & kIdx, xa ? j0 + q : gi, off, bb[q], cb[q]);
+        } else {
+          item_box<W>(Q.B.nodes, t.z, off, bb[q]);
+          cb[q] = t.z & ~kExpand;
+        }
+      }
+      live = live && fl == 0;
+#pragma unroll
+      for (int q = 0; q < PB; ++q) {
+        const int j = j0 + q;
+        if (!live || j >= nbj) continue;
+        c_bt += 1;
+        if (cb[q] == kEmpty || !overlap(ba, bb[q])) continue;
+        if ((na & kLeafBit) && (cb[q] & kLeafBit)) lmask |= 1u << j;
+        else tmask |= 1u << j;
+      }
+    }
+    if (live && gi == 0) {
+      c_np += 1;
+      c_bx += node_pair_bytes<W>(xa, xb);
+    }
+    // positions of this lane's outputs (task and leaf counts packed)
+    const unsigned mine = (unsigned)__popc(tmask) | ((unsigned)__popc(lmask) << 16);
+    unsigned incl = mine;
+    for (int o = 1; o < 32; o <<= 1) {
+      const unsigned v = __shfl_up_sync(FULL, incl, o);
+      if (lane >= o) incl += v;
+    }
+    const unsigned tot = __shfl_sync(FULL, incl, 31);
+    const unsigned ex = incl - mine;
+    int tpos = sp + (int)(ex & 0xFFFFu), lpos = nlq + (int)(ex >> 16);
+    unsigned bits = tmask | lmask;
+    while (bits) {
+      const int j = __ffs(bits) - 1;
+      bits &= bits - 1;
+      Box bb;
+      uint32_t nb;
+      if (xb) {
+        uint32_t cb;
+        const int jj = xa ? j : gi;
+        load_slot<W>(Q.B.nodes, t.z & kIdx, jj, off, bb, cb);  // L1 hit
+        nb = (cb & kLeafBit) ? (kLeafBit | ((t.z & kIdx) * W + jj)) : cb;
+      } else {
+        item_box<W>(Q.B.nodes, t.z, off, bb);
+        nb = t.z & ~kExpand;
+      }
+      if ((tmask >> j) & 1u) {
+        const uint2 nt = make_task(na, ba, nb, bb);
+        stk[tpos++] = make_uint4(t.x, nt.x, nt.y, 0u);
+      } else {
+        lq[lpos++] = make_uint4(t.x, na, nb, 0u);
+      }
+    }
+    sp += (int)(tot & 0xFFFFu);
+    nlq += (int)(tot >> 16);
+    __syncwarp();
+  }
+  if (err != DERR_NONE && lane == 0) atomicCAS(Q.err, 0, err);
+  // a warp that stops with an error still counted as active lets the others
+  // go (they see the error word)
+  if (registered && lane == 0) {
+    __threadfence();
+    atomicSub(sq(P, SQ_ACTIVE), 1u);
+  }
+  // counters: one atomic per warp and counter
+  const unsigned long long cv[11] = {c_np, c_bt, lc.lp, lc.slab, lc.st, lc.fb,
+                                     (unsigned long long)c_bx + lc.bytes, c_bx, lc.bytes,
+                                     c_res, c_sp};
+  const int slot[11] = {C_NODE_PAIRS, C_BOX_TESTS, C_LEAF_PAIRS, C_SLAB_TESTS, C_SEGTRI,
+                        C_FALLBACK, C_BYTES, C_BYTES_EXPAND, C_BYTES_LEAF, C_TASKS, C_SPILLED};
+#pragma unroll
+  for (int i = 0; i < 11; ++i) {
+    unsigned long long v = cv[i];
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(FULL, v, o);
+    if (lane == 0 && v) atomicAdd(Q.counters + slot[i], v);
+  }
+}
+
+// ---------------------------------------------------------------------------
 // Compaction: flags -> (idA, idB) in candidate order
 // ---------------------------------------------------------------------------
 constexpr int CMP_T = 256, CMP_PER = 16, CMP_CHUNK = CMP_T * CMP_PER;
@@ -1700,6 +2249,16 @@ static WaveParityKernel pick_wave_parity(int W) {
   if (W == 2) return k_wave_parity<2>;
   if (W == 4) return k_wave_parity<4>;
   return k_wave_parity<8>;
+}
+
+typedef void (*StreamKernel)(StreamArgs);
+static StreamKernel pick_stream(int W, bool exact) {
+  if (W == 2) return exact ? k_stream<2, true> : k_stream<2, false>;
+  if (W == 4) return exact ? k_stream<4, true> : k_stream<4, false>;
+  return exact ? k_stream<8, true> : k_stream<8, false>;
+}
+static int stream_smem_per_warp(int W) {
+  return W == 2 ? stream_warp_bytes<2>() : (W == 4 ? stream_warp_bytes<4>() : stream_warp_bytes<8>());
 }
 
 static int smem_per_warp(int W, int cap) {
@@ -1846,21 +2405,45 @@ pj_status run_join(Ctx *ctx, Dataset *A, Dataset *B, const int32_t *cand,
   uint4 *q2 = (uint4 *)ws_get(ctx, "spill2", sizeof(uint4) * (size_t)q_cap, &st);
   if (!q2) return st;
   unsigned int *qctr = reinterpret_cast<unsigned int *>(d_misc + 3);  // q1 n/pos, q2 n/pos
-  // wavefront front end: breadth-first levels before the warp passes (a
-  // per-thread parity stack needs the BVH depth to stay within 64 levels)
-  int wave_levels = o->wave_levels > 0 ? o->wave_levels : (o->wave_levels < 0 ? 0 : 14);
-  if (std::max(bA.max_depth, bB.max_depth) > 64) wave_levels = 0;
+  // front end: wave_levels > 0 breadth-first levels (0: 14), PJ_FRONT_STREAM
+  // the streaming kernel, PJ_FRONT_NONE none (the per-warp passes from the
+  // candidates).  Both front ends start with the per-thread parity rays,
+  // whose stack needs the BVH depth to stay within 64 levels.
+  int wave_levels = o->wave_levels > 0 ? o->wave_levels : (o->wave_levels == 0 ? 14 : 0);
+  bool stream = o->wave_levels == PJ_FRONT_STREAM && o->launch_mode != PJ_LAUNCH_PER_PAIR;
+  if (std::max(bA.max_depth, bB.max_depth) > 64) {
+    wave_levels = 0;
+    stream = false;
+  }
   const unsigned int wq_cap = 1u << 23;
   uint4 *wqa = nullptr, *wqb = nullptr, *wlq = nullptr, *wpar = nullptr;
   // level counters, cleared by one memset: task count entering each level
   // [0, levels], leaf pairs found at each level, then the position of the
   // first warp pass in the last queue and the parity hand-over count/position
   unsigned int *wctr = nullptr;
-  const int wctr_words = 2 * std::max(wave_levels, 0) + 8;
+  const int wctr_words = 2 * std::max(wave_levels, 0) + SQ_WORDS + 8;
   const unsigned int wpar_cap =
       (unsigned int)std::min<int64_t>(std::max<int64_t>(2 * C, 1024), 1 << 22);
   int wave_grid[3] = {1, 1, 1};  // expand/init, leaf, parity: one resident wave
-  if (wave_levels > 0 && o->launch_mode != PJ_LAUNCH_PER_PAIR) {
+  bool front = (wave_levels > 0 || stream) && o->launch_mode != PJ_LAUNCH_PER_PAIR;
+  int stream_grid = 1, stream_smem = 0;
+  StreamKernel ks = pick_stream(W, exact);
+  // the streaming launch's shared task queue (all-zero between launches)
+  const unsigned int dq_cap = 1u << 22;
+  uint4 *dq = nullptr;
+  int2 *cbase = nullptr;
+  if (stream && front) {
+    dq = (uint4 *)ws_get_zeroed(ctx, "stream_queue", sizeof(uint4) * (size_t)dq_cap, s, &st);
+    if (!dq) return st;
+    cbase = (int2 *)ws_get(ctx, "cand_base", sizeof(int2) * (size_t)std::max<int64_t>(C, 1), &st);
+    if (!cbase) return st;
+    stream_smem = 4 * stream_smem_per_warp(W);
+    PJ_CK(cudaFuncSetAttribute(ks, cudaFuncAttributeMaxDynamicSharedMemorySize, stream_smem));
+    int occ = 0;
+    PJ_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, ks, 128, stream_smem));
+    stream_grid = std::max(1, occ) * ctx->num_sms;
+  }
+  if (front) {
     int occ = 0;
     PJ_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, pick_wave_expand(W), 256, 0));
     wave_grid[0] = std::max(1, occ) * ctx->num_sms;
@@ -1868,12 +2451,14 @@ pj_status run_join(Ctx *ctx, Dataset *A, Dataset *B, const int32_t *cand,
     wave_grid[1] = std::max(1, occ) * ctx->num_sms;
     PJ_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, pick_wave_parity(W), 128, 0));
     wave_grid[2] = std::max(1, occ) * ctx->num_sms;
-    wqa = (uint4 *)ws_get(ctx, "wave_a", sizeof(uint4) * (size_t)wq_cap, &st);
-    if (!wqa) return st;
-    wqb = (uint4 *)ws_get(ctx, "wave_b", sizeof(uint4) * (size_t)wq_cap, &st);
-    if (!wqb) return st;
-    wlq = (uint4 *)ws_get(ctx, "wave_leaf", sizeof(uint4) * (size_t)wq_cap, &st);
-    if (!wlq) return st;
+    if (!stream) {
+      wqa = (uint4 *)ws_get(ctx, "wave_a", sizeof(uint4) * (size_t)wq_cap, &st);
+      if (!wqa) return st;
+      wqb = (uint4 *)ws_get(ctx, "wave_b", sizeof(uint4) * (size_t)wq_cap, &st);
+      if (!wqb) return st;
+      wlq = (uint4 *)ws_get(ctx, "wave_leaf", sizeof(uint4) * (size_t)wq_cap, &st);
+      if (!wlq) return st;
+    }
     wpar = (uint4 *)ws_get(ctx, "wave_par", sizeof(uint4) * (size_t)wpar_cap, &st);
     if (!wpar) return st;
     wctr = (unsigned int *)ws_get(ctx, "wave_ctr", sizeof(unsigned int) * (size_t)wctr_words, &st);
@@ -1936,10 +2521,29 @@ pj_status run_join(Ctx *ctx, Dataset *A, Dataset *B, const int32_t *cand,
     }
   } kg{&kev};
   bool kev_used = false;
-  if (o->kernel_times && wave_levels > 0) {
-    kev.resize(2 * (size_t)wave_levels + 1);
+  if (o->kernel_times && front) {
+    kev.resize(stream ? 2 : 2 * (size_t)wave_levels + 1);
     for (auto &e : kev) PJ_CK(cudaEventCreate(&e));
   }
+  auto make_wave_args = [&]() {
+    WaveArgs wa;
+    wa.A = args.A;
+    wa.B = args.B;
+    wa.cand = d_cand;
+    wa.cand_off = d_off;
+    wa.n_cand = d_misc;
+    wa.flags = d_flags;
+    wa.counters = ctx->d_counters;
+    wa.err = d_err;
+    wa.q_cap = wq_cap;
+    wa.lshift = key.second == 1 ? 0 : (key.second == 2 ? 1 : (key.second == 4 ? 2 : 3));
+    wa.MA = A->M;
+    wa.MB = B->M;
+    wa.q_par = wpar;
+    wa.q_par_n = nullptr;
+    wa.q_par_cap = wpar_cap;
+    return wa;
+  };
   // everything from here to the compacted pairs is a fixed sequence of
   // stream operations (no host synchronisation), so it can be captured
   auto device_part = [&](bool timed) -> pj_status {
@@ -1954,26 +2558,59 @@ pj_status run_join(Ctx *ctx, Dataset *A, Dataset *B, const int32_t *cand,
         }
         args.single = -1;
         ctx->launches += C;
-      } else if (wave_levels > 0) {
+      } else if (front && stream) {
+        // parity rays (per thread, then the long ones per warp), then the
+        // streaming refinement in one persistent launch
+        PJ_CK(cudaMemsetAsync(wctr, 0, sizeof(unsigned int) * wctr_words, s));
+        PJ_CK(cudaMemsetAsync(d_flags, 0, (size_t)C, s));
+        WaveArgs wa = make_wave_args();
+        // words: [0, SQ_WORDS) the streaming launch's control words, then the
+        // parity hand-over fill and position, a zero count and the intake
+        // position of the hand-over launch
+        unsigned int *sc = wctr, *hc = wctr + SQ_WORDS;
+        wa.q_par_n = hc;
+        RefineArgs ap = args;
+        ap.q_in = q1;
+        ap.q_in_n = hc + 2;
+        ap.q_in_pos = hc + 3;
+        ap.q_out = nullptr;
+        ap.q_out_n = nullptr;
+        ap.budget = 0;
+        ap.q_par = wpar;
+        ap.q_par_n = hc;
+        ap.q_par_pos = hc + 1;
+        ap.q_par_cap = wpar_cap;
+        PJ_CK(launch_pdl(pick_wave_parity(W), wave_grid[2], 128, 0, s, wa));
+        PJ_CK(launch_pdl(kern_tasks, (int)blocks, threads, smem, s, ap));
+        if (timed) PJ_CK(cudaEventRecord(ev[4], s));
+        StreamArgs sa{};
+        sa.w = wa;
+        sa.ctl = sc;
+        sa.dq = dq;
+        sa.cbase = cbase;
+        sa.dq_cap = dq_cap;
+        sa.spin_limit = 1u << 19;
+        sa.hungry_max = 2u * (unsigned)ctx->num_sms;
+        sa.give_after = 20000;
+        const bool kt = timed && !kev.empty();
+        if (kt) PJ_CK(cudaEventRecord(kev[0], s));
+        PJ_CK(launch_pdl(ks, stream_grid, 128, stream_smem, s, sa));
+        if (kt) {
+          PJ_CK(cudaEventRecord(kev[1], s));
+          kev_used = true;
+        }
+        if (timed) {
+          PJ_CK(cudaEventRecord(ev[5], s));
+          phases = true;
+        }
+        ctx->launches += 3;
+      } else if (front) {
         // wavefront front end, then the warp passes over what is left
         PJ_CK(cudaMemsetAsync(d_misc + 2, 0, 48, s));  // work and spill counters
         PJ_CK(cudaMemsetAsync(wctr, 0, sizeof(unsigned int) * wctr_words, s));
         PJ_CK(cudaMemsetAsync(d_flags, 0, (size_t)C, s));
-        WaveArgs wa;
-        wa.A = args.A;
-        wa.B = args.B;
-        wa.cand = d_cand;
-        wa.cand_off = d_off;
-        wa.n_cand = d_misc;
-        wa.flags = d_flags;
-        wa.counters = ctx->d_counters;
-        wa.err = d_err;
-        wa.q_cap = wq_cap;
-        wa.lshift = key.second == 1 ? 0 : (key.second == 2 ? 1 : (key.second == 4 ? 2 : 3));
-        wa.MA = A->M;
-        wa.MB = B->M;
+        WaveArgs wa = make_wave_args();
         unsigned int *qn = wctr, *ln = wctr + wave_levels + 1, *misc = ln + wave_levels;
-        wa.q_par = wpar;
         wa.q_par_n = misc + 1;
         wa.q_par_cap = wpar_cap;
         WaveExpandKernel kx = pick_wave_expand(W);
@@ -2088,7 +2725,8 @@ pj_status run_join(Ctx *ctx, Dataset *A, Dataset *B, const int32_t *cand,
   char gk[256];
   snprintf(gk, sizeof(gk), "%p|%p|%p|%p|%p|%d|%d|%d|%d|%d|%lld|%d|%d", (void *)A, (void *)B,
            (void *)d_cand, (void *)d_off, (void *)d_cycles, W, key.second, (int)exact, k,
-           (int)o->launch_mode, (long long)C, (int)budget1, args.max_pop * 100 + wave_levels);
+           (int)o->launch_mode, (long long)C, (int)budget1,
+           args.max_pop * 1000 + wave_levels * 2 + (stream ? 1 : 0));
   bool replayed = false;
   if (graph) {
     auto it = ctx->graphs.find(gk);
@@ -2128,13 +2766,16 @@ pj_status run_join(Ctx *ctx, Dataset *A, Dataset *B, const int32_t *cand,
   PJ_CK(cudaStreamSynchronize(s));
   if (herr[1]) return fail(ctx, PJ_ERR_INVALID_ARG, "a candidate mesh id is out of range");
   if (herr[2]) return fail(ctx, PJ_ERR_INVALID_ARG, "a translated candidate mesh leaves the 2^18 grid");
-  if (herr[0] == DERR_STACK || herr[0] == DERR_QUEUE) {
-    // batched pops outgrew the stack, or a spill queue filled up: redo every
-    // pair in plain depth-first order (whose stack bound holds by
-    // construction) and in one pass
+  if (herr[0] == DERR_STACK || herr[0] == DERR_QUEUE || herr[0] == DERR_TIMEOUT) {
+    // batched pops outgrew the stack, a spill queue filled up or a bounded
+    // wait gave up: redo every pair in plain depth-first order (whose stack
+    // bound holds by construction) and in one pass
+    if (dq) ws_mark_dirty(ctx, "stream_queue");
     args.max_pop = 1;
     budget1 = 0;
     wave_levels = 0;
+    stream = false;
+    front = false;
     PJ_CK(cudaMemsetAsync(d_err, 0, sizeof(int) * 4, s));
     if ((st = device_part(true)) != PJ_OK) return st;
     PJ_CK(cudaEventRecord(e1, s));
@@ -2150,7 +2791,10 @@ pj_status run_join(Ctx *ctx, Dataset *A, Dataset *B, const int32_t *cand,
   cudaEventElapsedTime(&out->mbb_ms, ev[0], ev[1]);
   out->parity_ms = out->front_ms = out->tasks_ms = -1.f;
   out->expand_ms = out->leaf_ms = -1.f;
-  if (kev_used && !replayed) {
+  if (kev_used && !replayed && stream) {
+    cudaEventElapsedTime(&out->expand_ms, kev[0], kev[1]);
+    out->leaf_ms = 0.f;
+  } else if (kev_used && !replayed) {
     out->expand_ms = out->leaf_ms = 0.f;
     for (int l = 0; l < wave_levels; ++l) {
       float a = 0.f, b = 0.f;

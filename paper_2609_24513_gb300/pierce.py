@@ -20,6 +20,7 @@ PJ_OK = 0
 PJ_PENDING = 9
 PJ_LEAF_FILTERED, PJ_LEAF_EXACT = 0, 1
 PJ_LAUNCH_PERSISTENT, PJ_LAUNCH_PER_PAIR = 0, 1
+PJ_FRONT_NONE, PJ_FRONT_STREAM = -1, -2   # pj_join_opts.wave_levels
 
 _STATUS = {1: "PJ_ERR_INVALID_ARG", 2: "PJ_ERR_NOT_QUANTIZED", 3: "PJ_ERR_NOT_MANIFOLD",
            4: "PJ_ERR_NO_MEMORY", 5: "PJ_ERR_BUSY", 6: "PJ_ERR_TIMEOUT", 7: "PJ_ERR_CUDA",

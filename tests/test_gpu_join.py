@@ -52,7 +52,8 @@ def test_tiny_spheres_all_bvh_shapes(ctx, tiny, W, L):
 
 
 @pytest.mark.parametrize("mode", ["exact", "warps2", "warps4", "per_pair", "explicit", "graph",
-                                  "spill1", "spill3", "nospill", "nowave", "wave1", "wave9"])
+                                  "spill1", "spill3", "nospill", "nowave", "wave1", "wave9",
+                                  "stream", "stream_exact", "stream_graph"])
 def test_tiny_spheres_modes(ctx, tiny, mode):
     for A, B, ha, hb, exp in tiny:
         kw = {}
@@ -85,6 +86,14 @@ def test_tiny_spheres_modes(ctx, tiny, mode):
             kw["spill_budget"] = 1
         elif mode == "wave9":
             kw["wave_levels"] = 9
+            kw["use_graph"] = True
+        elif mode == "stream":
+            kw["wave_levels"] = pierce.PJ_FRONT_STREAM
+        elif mode == "stream_exact":
+            kw["wave_levels"] = pierce.PJ_FRONT_STREAM
+            kw["leaf_mode"] = pierce.PJ_LEAF_EXACT
+        elif mode == "stream_graph":
+            kw["wave_levels"] = pierce.PJ_FRONT_STREAM
             kw["use_graph"] = True
         got, _ = ctx.join(ha, hb, cand=cand, width=4, leaf_size=4, **kw)
         if mode == "explicit":
@@ -366,3 +375,44 @@ def test_autotune_picks_a_measured_configuration(ctx):
     assert np.array_equal(got, exp)
     with pytest.raises(pierce.PierceError):
         pierce.pj_autotune(ctx.h, ha, hb, widths=(3,))
+
+
+def _bipyramid(n, c, r, h, phase=0.0):
+    """Closed double cone over an n-gon: every triangle contains one of the
+    two apexes, so the boxes of any two triangles of one half meet."""
+    a = 2 * np.pi * (np.arange(n) + phase) / n
+    ring = np.stack([c[0] + r * np.cos(a), c[1] + r * np.sin(a), np.full(n, c[2])], 1)
+    V = np.vstack([ring, [c[0], c[1], c[2] + h], [c[0], c[1], c[2] - h]])
+    F = []
+    for i in range(n):
+        j = (i + 1) % n
+        F += [(n, i, j), (n + 1, j, i)]
+    return synth.quantize(V), np.array(F, dtype=np.int32)
+
+
+@pytest.mark.parametrize("W,L", [(8, 1), (4, 1), (2, 1), (4, 4)])
+def test_dense_overlap_stack_spills(ctx, W, L):
+    """Node pairs that all overlap: a bipyramid's triangles all touch an
+    apex, so against itself (or a twisted or shifted copy) nearly every
+    child pair of a (node, node) step survives.  A streaming warp's task
+    stack then overflows and hands its older half to the later passes.  The
+    identical copy does not intersect (no strict crossing, every vertex on
+    the other surface); the twisted and shifted ones do.  Oracle-checked."""
+    m = _bipyramid(1000, (0.5, 0.5, 0.5), 0.2, 0.2)
+    tw = _bipyramid(1000, (0.5, 0.5, 0.5), 0.2, 0.2, phase=0.5)
+    sh = synth.translate(m, (1.0, 0.0, 0.0))
+    A, B = synth.concat([m, m, m]), synth.concat([m, tw, sh])
+    cand = np.array([[0, 0], [1, 1], [2, 2]], dtype=np.int32)
+    exp = oracle.join(A, B, cand, tier=2)
+    assert exp.tolist() == [0, 1, 1]
+    ha, hb = _load(ctx, A, ((W, L),)), _load(ctx, B, ((W, L),))
+    ctx.reset_counters()
+    got, _ = ctx.join(ha, hb, cand=cand, width=W, leaf_size=L, wave_levels=pierce.PJ_FRONT_STREAM)
+    assert got.tolist() == [[1, 1], [2, 2]]
+    assert ctx.counters()["tasks_spilled"] > 0
+    for kw in (dict(), dict(spill_budget=-1), dict(spill_budget=1), dict(use_graph=True),
+               dict(wave_levels=-1), dict(leaf_mode=pierce.PJ_LEAF_EXACT),
+               dict(wave_levels=pierce.PJ_FRONT_STREAM, use_graph=True),
+               dict(wave_levels=pierce.PJ_FRONT_STREAM, leaf_mode=pierce.PJ_LEAF_EXACT)):
+        got, _ = ctx.join(ha, hb, cand=cand, width=W, leaf_size=L, **kw)
+        assert got.tolist() == [[1, 1], [2, 2]], kw

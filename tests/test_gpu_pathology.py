@@ -36,13 +36,19 @@ def test_candidates_match_oracle(workload):
     assert info["n_candidates"] == len(cand)
     assert np.array_equal(got, got_explicit)
     assert len(got) > 100
+    # the streaming front end (one persistent launch) returns the same pairs
+    for kw in (dict(), dict(use_graph=True), dict(leaf_mode=pierce.PJ_LEAF_EXACT)):
+        got_s, _ = ctx.join(ha, hb, wave_levels=pierce.PJ_FRONT_STREAM, **kw)
+        assert np.array_equal(got_s, got), kw
 
 
-@pytest.mark.parametrize("mode", ["bench", "exact_w8_l2"])
+@pytest.mark.parametrize("mode", ["bench", "stream", "exact_w8_l2"])
 def test_sampled_pairs_match_oracle(workload, mode):
     A, B, ctx, ha, hb = workload
     if mode == "bench":
         got, info = ctx.join(ha, hb, use_graph=True)
+    elif mode == "stream":
+        got, info = ctx.join(ha, hb, use_graph=True, wave_levels=pierce.PJ_FRONT_STREAM)
     else:
         ctx.build(ha, 8, 2)
         ctx.build(hb, 8, 2)

@@ -34,7 +34,8 @@ def test_batching_small_all_pairs(ctx):
         ctx.build(ha, W, L)
         ctx.build(hb, W, L)
         for kw in (dict(use_graph=True), dict(launch_mode=pierce.PJ_LAUNCH_PER_PAIR),
-                   dict(leaf_mode=pierce.PJ_LEAF_EXACT, wave_levels=-1, warps_per_pair=2)):
+                   dict(leaf_mode=pierce.PJ_LEAF_EXACT, wave_levels=-1, warps_per_pair=2),
+                   dict(wave_levels=pierce.PJ_FRONT_STREAM, use_graph=True)):
             flags, _ = _join_flags(ctx, ha, hb, cand, off, width=W, leaf_size=L, **kw)
             assert np.array_equal(flags, exp), (W, L, kw)
 
