@@ -1147,6 +1147,16 @@ __device__ __forceinline__ void item_box(const float *nodes, uint32_t item, F3 o
   else load_slot<W>(nodes, idx, -1, off, b, dummy);
 }
 
+// box and child word of an item's slot (the word is a leaf's descriptor;
+// for an internal node's own box it is unused)
+template <int W>
+__device__ __forceinline__ void item_box_w(const float *nodes, uint32_t item, F3 off, Box &b,
+                                           uint32_t &word) {
+  const uint32_t idx = item & kIdx;
+  if (item & kLeafBit) load_slot<W>(nodes, idx / W, (int)(idx % W), off, b, word);
+  else load_slot<W>(nodes, idx, -1, off, b, word);
+}
+
 // One breadth-first level: W threads per task; thread i tests child i of
 // the expanding side (against every child of the other side when both
 // expand).  Surviving children become tasks of the next level, or leaf
@@ -1580,10 +1590,14 @@ __global__ void __launch_bounds__(128, 4) k_refine_tasks(RefineArgs P) {
 // ---------------------------------------------------------------------------
 // Streaming refinement.  A persistent kernel whose warps each keep a task
 // stack and a leaf-pair queue in shared memory holding the tasks of many
-// candidate pairs at once, so that every traversal round fills the warp:
-// W lanes per popped (node, node) task (lane i tests child i of one side
-// against the other side's children), 2L lanes per leaf pair.  A warp takes
-// 32 new candidates whenever its stack holds less than one round.
+// candidate pairs at once, so that every traversal round is wide: an expand
+// round copies the nodes of 64 / W (node, node) tasks to shared memory with
+// asynchronous copies issued all at once and tests their child pairs with
+// W / 2 lanes per task; a leaf round does the same with the triangles of up
+// to 16 leaf pairs, filters (edge, triangle) tests by boxes and runs the
+// exact tests that remain one per lane.  A round thus waits for one memory
+// latency however many fetches it makes.  A warp takes 32 new candidates
+// whenever its stack holds less than one round.
 //
 // Load balance.  A few pairs (a nucleus lying along a vessel wall over a
 // large area) cost thousands of times the mean, and a warp that holds one
@@ -1616,84 +1630,44 @@ __global__ void __launch_bounds__(128, 4) k_refine_tasks(RefineArgs P) {
 // helpers, never work.  Every wait is bounded: on expiry the kernel records
 // an error and the host redoes the join by plain depth-first traversal.
 // ---------------------------------------------------------------------------
-// One leaf-pair unit (as leaf_unit) with every load issued as early as it
-// can be: the leaf slots and the pair's triangle bases (written at intake)
-// first, then the source triangle and the target leaf's triangles together,
-// then the tests from registers.  A warp of the streaming kernel does one
-// round at a time, so each serial load would be a full memory latency.
-template <int W, bool EXACT>
-__device__ __forceinline__ bool stream_leaf_unit(const WaveArgs &Q, const int2 *cbase,
-                                                 const uint4 e, const int u, LeafCnt &cn) {
-  const F3 zero = mkf3(0.f, 0.f, 0.f);
-  const bool dirA = (u >> Q.lshift) == 0;
-  const int k = u & ((1 << Q.lshift) - 1);
-  const uint32_t sslot = (dirA ? e.y : e.z) & kIdx, tslot = (dirA ? e.z : e.y) & kIdx;
-  const Side &S = dirA ? Q.A : Q.B;
-  const Side &T = dirA ? Q.B : Q.A;
-  const F3 off = cand_offset(Q, e.x);
-  const F3 soff = dirA ? zero : off, toff = dirA ? off : zero;
-  const uint32_t sdesc = __float_as_uint(
-      __ldg(S.nodes + (int64_t)(sslot / W) * Cfg<W>::SW + 8 * (sslot % W + 1) + 6));
-  Box tb;
-  uint32_t tdesc;
-  load_slot<W>(T.nodes, tslot / W, (int)(tslot % W), toff, tb, tdesc);
-  const int2 cb = cbase[e.x];
-  if (k > (int)(sdesc & 7u)) return false;
-  if (u == 0) cn.lp += 1;
-  const int64_t s_rec = (int64_t)(dirA ? cb.x : cb.y) + ((sdesc >> 3) & 0x0FFFFFFFu) + k;
-  const int64_t t_first = (int64_t)(dirA ? cb.y : cb.x) + ((tdesc >> 3) & 0x0FFFFFFFu);
-  const int t_n = (int)(tdesc & 7u) + 1;
-  F3 v[3];
-  int own;
-  load_tri(S.trirec, s_rec, soff, v[0], v[1], v[2], own);
-  cn.bytes += 48 + 64;
-  for (int t0 = 0; t0 < t_n; t0 += 4) {
-    // up to four target triangles per batch of loads
-    F3 ta[4], tbv[4], tc[4];
-    int town;
-#pragma unroll
-    for (int t = 0; t < 4; ++t)
-      if (t0 + t < t_n) load_tri(T.trirec, t_first + t0 + t, toff, ta[t], tbv[t], tc[t], town);
-    const int tn = min(4, t_n - t0);
-    for (int ek = 0; ek < 3; ++ek) {
-      if (!((own >> ek) & 1)) continue;
-      const F3 p = sel_f3<3>(v, ek), qv = sel_f3<3>(v, ek == 2 ? 0 : ek + 1);
-      if (t0 == 0) cn.slab += 1;
-      Seg sg = make_seg(p, qv);
-      if (!slab_hit(sg, tb.lo, tb.hi)) continue;
-      cn.bytes += 48u * tn;
-      const F3 elo = mkf3(fminf(p.x, qv.x), fminf(p.y, qv.y), fminf(p.z, qv.z));
-      const F3 ehi = mkf3(fmaxf(p.x, qv.x), fmaxf(p.y, qv.y), fmaxf(p.z, qv.z));
-#pragma unroll 1
-      for (int t = 0; t < tn; ++t) {
-        const F3 a = sel_f3<4>(ta, t), b = sel_f3<4>(tbv, t), c = sel_f3<4>(tc, t);
-        const float lx = fminf(a.x, fminf(b.x, c.x)), hx = fmaxf(a.x, fmaxf(b.x, c.x));
-        const float ly = fminf(a.y, fminf(b.y, c.y)), hy = fmaxf(a.y, fmaxf(b.y, c.y));
-        const float lz = fminf(a.z, fminf(b.z, c.z)), hz = fmaxf(a.z, fmaxf(b.z, c.z));
-        if (lx > ehi.x || elo.x > hx || ly > ehi.y || elo.y > hy || lz > ehi.z || elo.z > hz)
-          continue;
-        cn.st += 1;
-        bool r;
-        if (EXACT) {
-          r = segtri_exact_staged(p, qv, a, b, c);
-        } else {
-          bool ex = false;
-          r = segtri_filtered(p, qv, a, b, c, &ex);
-          cn.fb += ex ? 1 : 0;
-        }
-        if (r) return true;
-      }
-    }
-  }
-  return false;
+// 16-byte asynchronous copy global -> shared (bypassing L1), and the wait
+// for all of this thread's copies
+__device__ __forceinline__ void cp_async16(float4 *dst, const float4 *src) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(d), "l"(src) : "memory");
 }
+__device__ __forceinline__ void cp_async_wait_all() {
+  asm volatile("cp.async.commit_group;\n\tcp.async.wait_group 0;" ::: "memory");
+}
+
+// a staged triangle record (three float4, as in the BVH's triangle records)
+__device__ __forceinline__ void stage_tri(const float4 *stage, int i, F3 off, F3 &a, F3 &b,
+                                          F3 &c, int &own) {
+  const float4 r0 = stage[3 * i], r1 = stage[3 * i + 1], r2 = stage[3 * i + 2];
+  a = add(mkf3(r0.x, r0.y, r0.z), off);
+  b = add(mkf3(r0.w, r1.x, r1.y), off);
+  c = add(mkf3(r1.z, r1.w, r2.x), off);
+  own = __float_as_int(r2.y);
+}
+
+// Leaf rounds stage the triangles of up to kLeafPairs leaf pairs (at most
+// 48 / L) in shared memory: kStageF4 float4 = 4.5 KB per warp, which also
+// holds an expand round's nodes (64 / W tasks x 2 nodes x W slots).
+constexpr int kLeafPairs = 12;
+constexpr int kStageF4 = 288;
+constexpr int kListMax = 384;  // queued (edge, triangle) tests: 32 units x 3 edges x 4 tests
 
 template <int W>
 struct StreamCfg {
-  static constexpr int TPR = 32 / W;                               // tasks per round
-  static constexpr int SC = W == 8 ? 384 : 256;                    // stack entries
-  static constexpr int LQ = W == 8 ? 288 : (W == 4 ? 160 : 96);    // leaf-pair entries
-  static constexpr int warp_bytes = (SC + LQ) * 16;
+  static constexpr int NT = 64 / W;                                // tasks per expand round
+  static constexpr int SC = W == 8 ? 384 : 224;                    // stack entries
+  static constexpr int LQ = 64;                                    // leaf-pair entries
+  // per warp: stack, leaf queue (uint4 entries), triangle stage, boxes of
+  // the staged triangles and of the leaves, pair offsets, pair entries, hit
+  // words, test list
+  static constexpr int warp_bytes = (SC + LQ) * 16 + kStageF4 * 16 + kStageF4 / 3 * 6 * 4 +
+                                    kLeafPairs * 2 * 6 * 4 + kLeafPairs * 3 * 4 +
+                                    kLeafPairs * 16 + kLeafPairs * 4 + kListMax * 2;
 };
 
 // control words of one launch (zeroed before it), each on its own 128-byte
@@ -1768,13 +1742,21 @@ __global__ void __launch_bounds__(128, 4) k_stream(StreamArgs P) {
   using Cf = StreamCfg<W>;
   extern __shared__ __align__(16) unsigned char smem[];
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
-  uint4 *stk = reinterpret_cast<uint4 *>(smem) + (size_t)wib * (Cf::SC + Cf::LQ);
+  uint4 *stk = reinterpret_cast<uint4 *>(smem + (size_t)wib * Cf::warp_bytes);
   uint4 *lq = stk + Cf::SC;
+  float4 *stage = reinterpret_cast<float4 *>(lq + Cf::LQ);
+  float *s_tbox = reinterpret_cast<float *>(stage + kStageF4);  // per staged triangle
+  float *s_box = s_tbox + kStageF4 / 3 * 6;                       // per leaf
+  float *s_off = s_box + kLeafPairs * 2 * 6;
+  uint4 *s_pe = reinterpret_cast<uint4 *>(s_off + kLeafPairs * 3);
+  volatile unsigned *s_hit = reinterpret_cast<volatile unsigned *>(s_pe + kLeafPairs);
+  unsigned short *s_list = reinterpret_cast<unsigned short *>(
+      const_cast<unsigned *>(s_hit) + kLeafPairs);
   const WaveArgs &Q = P.w;
   const unsigned lt = (1u << lane) - 1u;
-  const int grp = lane / W, gi = lane - grp * W;  // task group, lane in the group
-  const int lsh = Q.lshift + 1;                   // 2L = 1 << lsh lanes per leaf pair
-  const int lpr = 32 >> lsh;                      // leaf pairs per round
+  const int L = 1 << Q.lshift;                    // leaf size
+  const int pmax = min(kLeafPairs, 48 / L);       // leaf pairs per round
+  const int upi = L == 8 ? 16 : 32;               // leaf units per filter iteration
   const F3 zero = mkf3(0.f, 0.f, 0.f);
   volatile const uint8_t *vflags = Q.flags;
   const int64_t n_in = *Q.n_cand;
@@ -1798,17 +1780,186 @@ __global__ void __launch_bounds__(128, 4) k_stream(StreamArgs P) {
   bool registered = true;  // counted in SQ_ACTIVE
   if (lane == 0) atomicAdd(sq(P, SQ_ACTIVE), 1u);
 
-  // one round over up to lpr leaf pairs from the top of the queue
+  // one leaf round: the triangles of up to np leaf pairs from the top of the
+  // queue are copied to shared memory (cp.async, all at once), each leaf's
+  // box is taken from its triangles, every owned edge is slab-tested against
+  // the other leaf's box and box-tested against its triangles, and the
+  // surviving (edge, triangle) tests run one per lane.
   auto leaf_round = [&]() {
-    const int np = min(nlq, lpr);
-    const int p = lane >> lsh, u = lane & ((1 << lsh) - 1);
-    const bool act = p < np;
-    const uint4 e = act ? lq[nlq - 1 - p] : make_uint4(0u, 0u, 0u, 0u);
+    const int np = min(nlq, pmax);
+    if (lane < np) {
+      const uint4 e = lq[nlq - 1 - lane];
+      const bool alive = vflags[e.x] == 0;
+      const F3 o = alive ? cand_offset(Q, e.x) : zero;
+      s_pe[lane] = e;
+      s_hit[lane] = alive ? 0u : 1u;
+      s_off[3 * lane] = o.x;
+      s_off[3 * lane + 1] = o.y;
+      s_off[3 * lane + 2] = o.z;
+      if (alive) {
+        lc.lp += 1;
+        lc.bytes += 48u * ((e.w & 7u) + ((e.w >> 8) & 7u) + 2u);
+      }
+    }
     __syncwarp();
     nlq -= np;
-    if (act && vflags[e.x] == 0) {
-      if (stream_leaf_unit<W, EXACT>(Q, P.cbase, e, u, lc)) Q.flags[e.x] = 1;
+    // stage: chunk f = ((p * 2 + side) * L + t) * 3 + k
+    const int nch = np * 2 * L * 3;
+    for (int f = lane; f < nch; f += 32) {
+      const int k = f % 3, r = f / 3;
+      const int t = r % L, ps = r / L, side = ps & 1, p = ps >> 1;
+      if (s_hit[p]) continue;
+      const uint4 e = s_pe[p];
+      const int n = (int)((side ? e.w >> 8 : e.w) & 7u) + 1;
+      if (t >= n) continue;
+      const float4 *src = (side ? Q.B.trirec : Q.A.trirec) + 3 * ((int64_t)(side ? e.z : e.y) + t) + k;
+      cp_async16(stage + f, src);
     }
+    cp_async_wait_all();
+    __syncwarp();
+    // boxes of the staged triangles, then of the leaves (B's translated by
+    // the pair's offset)
+    for (int i = lane; i < np * 2 * L; i += 32) {
+      const int t = i % L, ps = i / L, side = ps & 1, p = ps >> 1;
+      if (s_hit[p]) continue;
+      const uint4 e = s_pe[p];
+      if (t > (int)((side ? e.w >> 8 : e.w) & 7u)) continue;
+      const F3 o = side ? mkf3(s_off[3 * p], s_off[3 * p + 1], s_off[3 * p + 2]) : zero;
+      F3 a, b, c;
+      int own;
+      stage_tri(stage, i, o, a, b, c, own);
+      float *bp = s_tbox + 6 * i;
+      bp[0] = fminf(a.x, fminf(b.x, c.x));
+      bp[1] = fminf(a.y, fminf(b.y, c.y));
+      bp[2] = fminf(a.z, fminf(b.z, c.z));
+      bp[3] = fmaxf(a.x, fmaxf(b.x, c.x));
+      bp[4] = fmaxf(a.y, fmaxf(b.y, c.y));
+      bp[5] = fmaxf(a.z, fmaxf(b.z, c.z));
+    }
+    __syncwarp();
+    if (lane < 2 * np) {
+      const int p = lane >> 1, side = lane & 1;
+      if (!s_hit[p]) {
+        const uint4 e = s_pe[p];
+        const int n = (int)((side ? e.w >> 8 : e.w) & 7u) + 1;
+        float b[6] = {3.4e38f, 3.4e38f, 3.4e38f, -3.4e38f, -3.4e38f, -3.4e38f};
+        for (int t = 0; t < n; ++t) {
+          const float *tp = s_tbox + 6 * (lane * L + t);
+          b[0] = fminf(b[0], tp[0]);
+          b[1] = fminf(b[1], tp[1]);
+          b[2] = fminf(b[2], tp[2]);
+          b[3] = fmaxf(b[3], tp[3]);
+          b[4] = fmaxf(b[4], tp[4]);
+          b[5] = fmaxf(b[5], tp[5]);
+        }
+        float *bp = s_box + 6 * lane;
+#pragma unroll
+        for (int q = 0; q < 6; ++q) bp[q] = b[q];
+      }
+    }
+    __syncwarp();
+    // the queued (edge, triangle) tests, one per lane: code = p | dir << 4 |
+    // s << 5 | k << 8 | t << 10
+    int nlist = 0;
+    auto flush = [&]() {
+      for (int i0 = 0; i0 < nlist; i0 += 32) {
+        const int i = i0 + lane;
+        if (i < nlist) {
+          const unsigned code = s_list[i];
+          const int p = code & 15, dir = (code >> 4) & 1, si = (code >> 5) & 7;
+          const int k = (code >> 8) & 3, t = (code >> 10) & 7;
+          if (!s_hit[p]) {
+            const F3 o = mkf3(s_off[3 * p], s_off[3 * p + 1], s_off[3 * p + 2]);
+            F3 v0, v1, v2, a, b, c;
+            int own, town;
+            stage_tri(stage, (p * 2 + dir) * L + si, dir ? o : zero, v0, v1, v2, own);
+            stage_tri(stage, (p * 2 + (dir ^ 1)) * L + t, dir ? zero : o, a, b, c, town);
+            const F3 pp = k == 0 ? v0 : (k == 1 ? v1 : v2);
+            const F3 qq = k == 0 ? v1 : (k == 1 ? v2 : v0);
+            lc.st += 1;
+            bool r;
+            if (EXACT) {
+              r = segtri_exact_staged(pp, qq, a, b, c);
+            } else {
+              bool ex = false;
+              r = segtri_filtered(pp, qq, a, b, c, &ex);
+              lc.fb += ex ? 1 : 0;
+            }
+            if (r) {
+              s_hit[p] = 1u;
+              Q.flags[s_pe[p].x] = 1;
+            }
+          }
+        }
+        __syncwarp();
+      }
+      nlist = 0;
+    };
+    // units (p, dir, source triangle): the source's owned edges against the
+    // target leaf
+    const int nu = np * 2 * L;
+    for (int u0 = 0; u0 < nu; u0 += upi) {
+      const int u = lane < upi ? u0 + lane : nu;
+      unsigned mask = 0;  // bit k * L + t: edge k against target triangle t
+      int p = 0, dir = 0, si = 0;
+      if (u < nu) {
+        si = u % L;
+        const int pd = u / L;
+        dir = pd & 1;
+        p = pd >> 1;
+        const uint4 e = s_pe[p];
+        const int ns = (int)((dir ? e.w >> 8 : e.w) & 7u) + 1;
+        const int nt = (int)((dir ? e.w : e.w >> 8) & 7u) + 1;
+        if (!s_hit[p] && si < ns) {
+          const F3 o = mkf3(s_off[3 * p], s_off[3 * p + 1], s_off[3 * p + 2]);
+          F3 v[3];
+          int own;
+          stage_tri(stage, (p * 2 + dir) * L + si, dir ? o : zero, v[0], v[1], v[2], own);
+          const float *bp = s_box + 6 * (p * 2 + (dir ^ 1));
+          const F3 tlo = mkf3(bp[0], bp[1], bp[2]), thi = mkf3(bp[3], bp[4], bp[5]);
+          const float *tbx = s_tbox + 6 * ((p * 2 + (dir ^ 1)) * L);
+          // box filters only (no slab test: its reciprocals cost more here
+          // than the exact tests it would save, which run one per lane)
+#pragma unroll
+          for (int k = 0; k < 3; ++k) {
+            if (!((own >> k) & 1)) continue;
+            const F3 pp = sel_f3<3>(v, k), qq = sel_f3<3>(v, k == 2 ? 0 : k + 1);
+            const F3 elo = mkf3(fminf(pp.x, qq.x), fminf(pp.y, qq.y), fminf(pp.z, qq.z));
+            const F3 ehi = mkf3(fmaxf(pp.x, qq.x), fmaxf(pp.y, qq.y), fmaxf(pp.z, qq.z));
+            lc.slab += 1;
+            // the edge's box against the leaf's, then against each triangle's
+            if (elo.x > thi.x || tlo.x > ehi.x || elo.y > thi.y || tlo.y > ehi.y ||
+                elo.z > thi.z || tlo.z > ehi.z)
+              continue;
+#pragma unroll
+            for (int t = 0; t < 8; ++t) {
+              if (t >= nt) break;
+              const float *tp = tbx + 6 * t;
+              if (tp[0] > ehi.x || elo.x > tp[3] || tp[1] > ehi.y || elo.y > tp[4] ||
+                  tp[2] > ehi.z || elo.z > tp[5])
+                continue;
+              mask |= 1u << (k * L + t);
+            }
+          }
+        }
+      }
+      // append this lane's tests (at most 3 L), flushing first if they would
+      // not fit
+      const int cnt = __popc(mask);
+      const int incl = warp_scan_incl(cnt, lane);
+      const int tot = __shfl_sync(FULL, incl, 31);
+      if (nlist + tot > kListMax) flush();
+      int pos = nlist + incl - cnt;
+      while (mask) {
+        const int b = __ffs(mask) - 1;
+        mask &= mask - 1;
+        const int k = b / L, t = b - k * L;
+        s_list[pos++] = (unsigned short)(p | (dir << 4) | (si << 5) | (k << 8) | (t << 10));
+      }
+      nlist += tot;
+      __syncwarp();
+    }
+    flush();
   };
 
   // give the older half of the stack to the queue
@@ -1841,7 +1992,7 @@ __global__ void __launch_bounds__(128, 4) k_stream(StreamArgs P) {
       peek_more = more;
     }
     // 1. intake, while the stack holds less than one round
-    if (more && sp < Cf::TPR && nlq < lpr) {
+    if (more && sp < Cf::NT && nlq < pmax) {
       unsigned base = 0;
       if (lane == 0) base = atomicAdd(sq(P, SQ_INTAKE), 32u);
       base = __shfl_sync(FULL, base, 0);
@@ -1874,7 +2025,7 @@ __global__ void __launch_bounds__(128, 4) k_stream(StreamArgs P) {
           }
         }
       }
-      // room: sp < TPR <= 16 and 32 more stay below SC
+      // room: sp < NT <= 32 and 32 more stay below SC
       const unsigned m = __ballot_sync(FULL, push);
       if (push) stk[sp + __popc(m & lt)] = ent;
       sp += __popc(m);
@@ -1906,7 +2057,7 @@ __global__ void __launch_bounds__(128, 4) k_stream(StreamArgs P) {
           if (ld_vol(reinterpret_cast<const unsigned *>(Q.err)) != 0u) break;  // failing
           const int av = *reinterpret_cast<volatile int *>(avail);
           if (av > 0) {
-            const int want = min(av, Cf::TPR);
+            const int want = min(av, Cf::NT);
             if (atomicSub(avail, want) >= want) {
               h = atomicAdd(sq(P, SQ_HEAD), (unsigned)want);
               atomicAdd(sq(P, SQ_ACTIVE), 1u);
@@ -1934,7 +2085,7 @@ __global__ void __launch_bounds__(128, 4) k_stream(StreamArgs P) {
       if (h < 0) break;
       t_new = clock64();
       // take the claimed entries (their producers may still be writing them)
-      bool tpush = false, lpush = false;
+      bool tpush = false;
       uint4 ent = make_uint4(0u, 0u, 0u, 0u);
       bool late = false;
       if (lane < k) {
@@ -1951,11 +2102,7 @@ __global__ void __launch_bounds__(128, 4) k_stream(StreamArgs P) {
           __threadfence();
           ent = __ldcg(P.dq + h + lane);
           *rdy = 0u;
-          if (vflags[ent.x] == 0) {
-            const bool leafs = (ent.y & kLeafBit) && (ent.z & kLeafBit);
-            lpush = leafs;
-            tpush = !leafs;
-          }
+          tpush = vflags[ent.x] == 0;  // (a leaf pair goes to the leaf queue when popped)
         }
       }
       if (__any_sync(FULL, late)) {
@@ -1963,29 +2110,34 @@ __global__ void __launch_bounds__(128, 4) k_stream(StreamArgs P) {
         break;
       }
       c_res += lane == 0 ? (unsigned)k : 0u;
-      const unsigned mt = __ballot_sync(FULL, tpush), ml = __ballot_sync(FULL, lpush);
+      const unsigned mt = __ballot_sync(FULL, tpush);
       if (tpush) stk[__popc(mt & lt)] = ent;
-      if (lpush) lq[__popc(ml & lt)] = ent;
       sp = __popc(mt);
-      nlq = __popc(ml);
+      nlq = 0;
       __syncwarp();
       continue;
     }
     // 3. a straggler and hungry warps: give the older half of the stack
-    if (give && sp >= 2 * Cf::TPR) {
+    if (give && sp >= Cf::NT) {
       if (!give_half(sp / 2)) {
         err = DERR_QUEUE;
         break;
       }
     }
     // 4. leaf pairs once a round's worth is queued (or nothing else is left)
-    if (nlq >= lpr || sp == 0) {
+    if (nlq >= pmax || sp == 0) {
       leaf_round();
       continue;
     }
-    // 5. expand round: pop up to TPR tasks whose children fit
-    int npop = min(Cf::TPR, sp);
-    while (npop > 0 && (sp - npop + npop * W * W > Cf::SC || nlq + npop * W * W > Cf::LQ)) --npop;
+    // 5. expand round: up to NT tasks; their nodes are copied to shared
+    // memory (cp.async, all at once), then 32 / NT lanes per task test its
+    // child pairs.  Leaf pairs that do not fit in the leaf queue go on the
+    // stack as (leaf, leaf) tasks.
+    constexpr int NT = Cf::NT;          // tasks per round
+    constexpr int LPT = 32 / NT;        // lanes per task
+    static_assert(W * W / LPT <= 32, "a lane's child pairs must fit one mask word");
+    int npop = min(NT, sp);
+    while (npop > 0 && sp - npop + npop * W * W > Cf::SC) --npop;
     if (npop == 0) {
       // the stack is nearly full: its older half goes to the queue
       if (!give_half(Cf::SC / 2)) {
@@ -1994,61 +2146,63 @@ __global__ void __launch_bounds__(128, 4) k_stream(StreamArgs P) {
       }
       continue;
     }
-    const bool act = grp < npop;
-    const uint4 t = act ? stk[sp - 1 - grp] : make_uint4(0u, 0u, 0u, 0u);
-    __syncwarp();
-    sp -= npop;
+    const int ti = lane / LPT, gi = lane - ti * LPT;  // task of this lane, rank in it
+    const bool act = ti < npop;
+    const uint4 t = act ? stk[sp - 1 - ti] : make_uint4(0u, 0u, 0u, 0u);
     const bool xa = t.y & kExpand, xb = t.z & kExpand;
-    // every load of the round at once: the flag, the A slot, the B slots
-    // (all W when both sides expand, in batches of four)
+    // stage: task i, side s, slot j (of W) at float4 index ((i * 2 + s) * W + j) * 2;
+    // one lane per (task, side) copies the W child slots of an expanding
+    // node, or the one slot of the item's own box
+    for (int is = lane; is < npop * 2; is += 32) {
+      const int side = is & 1, i = is >> 1;
+      const uint4 e = stk[sp - 1 - i];
+      const uint32_t item = side ? e.z : e.y;
+      const bool x = item & kExpand;
+      const uint32_t idx = item & kIdx;
+      int64_t word;  // float offset of the first slot in the node array
+      if (x) word = (int64_t)idx * Cfg<W>::SW + 8;
+      else if (item & kLeafBit) word = (int64_t)(idx / W) * Cfg<W>::SW + 8 * (idx % W + 1);
+      else word = (int64_t)idx * Cfg<W>::SW;
+      const float4 *src = reinterpret_cast<const float4 *>((side ? Q.B.nodes : Q.A.nodes) + word);
+      float4 *dst = stage + 2 * is * W;
+      const int n = x ? 2 * W : 2;
+      for (int h = 0; h < n; ++h) cp_async16(dst + h, src + h);
+    }
     const uint8_t fl = act ? vflags[t.x] : (uint8_t)1;
     const F3 off = act ? cand_offset(Q, t.x) : zero;
-    Box ba;
-    uint32_t na = 0;
-    bool live = act;
-    if (act) {
-      if (xa) {
-        uint32_t ca;
-        load_slot<W>(Q.A.nodes, t.y & kIdx, gi, zero, ba, ca);
-        live = ca != kEmpty;
-        na = (ca & kLeafBit) ? (kLeafBit | ((t.y & kIdx) * W + gi)) : ca;
-      } else {
-        item_box<W>(Q.A.nodes, t.y, zero, ba);
-        na = t.y & ~kExpand;
-      }
-    }
-    constexpr int PB = W < 2 ? W : 2;  // B slots per batch of loads
-    const int nbj = (act && xa && xb) ? W : 1;
-    unsigned tmask = 0, lmask = 0;
-#pragma unroll
-    for (int j0 = 0; j0 < W; j0 += PB) {
-      Box bb[PB];
-      uint32_t cb[PB];
-#pragma unroll
-      for (int q = 0; q < PB; ++q) {
-        cb[q] = kEmpty;
-        if (!act || j0 + q >= nbj) continue;
-        if (xb) {
-          load_slot<W>(Q.B.nodes, t.z & kIdx, xa ? j0 + q : gi, off, bb[q], cb[q]);
-        } else {
-          item_box<W>(Q.B.nodes, t.z, off, bb[q]);
-          cb[q] = t.z & ~kExpand;
-        }
-      }
-      live = live && fl == 0;
-#pragma unroll
-      for (int q = 0; q < PB; ++q) {
-        const int j = j0 + q;
-        if (!live || j >= nbj) continue;
-        c_bt += 1;
-        if (cb[q] == kEmpty || !overlap(ba, bb[q])) continue;
-        if ((na & kLeafBit) && (cb[q] & kLeafBit)) lmask |= 1u << j;
-        else tmask |= 1u << j;
-      }
-    }
+    const int2 cbv = act ? P.cbase[t.x] : make_int2(0, 0);  // for leaf pairs
+    cp_async_wait_all();
+    __syncwarp();
+    sp -= npop;
+    const bool live = act && fl == 0;
+    const int NA = xa ? W : 1, NB = xb ? W : 1;
     if (live && gi == 0) {
       c_np += 1;
       c_bx += node_pair_bytes<W>(xa, xb);
+    }
+    // this lane's child pairs q = gi + k LPT, k < W * W / LPT <= 16 (a = q / NB,
+    // b = q % NB); bit k of the masks
+    unsigned tmask = 0, lmask = 0;
+    if (live) {
+      for (int q = gi, k = 0; q < NA * NB; q += LPT, ++k) {
+        const int a = q / NB, b = q - a * NB;
+        const float4 a0 = stage[((ti * 2) * W + a) * 2], a1 = stage[((ti * 2) * W + a) * 2 + 1];
+        const float4 b0 = stage[((ti * 2 + 1) * W + b) * 2];
+        const float4 b1 = stage[((ti * 2 + 1) * W + b) * 2 + 1];
+        const uint32_t wa = __float_as_uint(a1.z), wb = __float_as_uint(b1.z);
+        c_bt += 1;
+        if ((xa && wa == kEmpty) || (xb && wb == kEmpty)) continue;
+        Box ba, bb;
+        ba.lo = mkf3(a0.x, a0.y, a0.z);
+        ba.hi = mkf3(a0.w, a1.x, a1.y);
+        bb.lo = add(mkf3(b0.x, b0.y, b0.z), off);
+        bb.hi = add(mkf3(b0.w, b1.x, b1.y), off);
+        if (!overlap(ba, bb)) continue;
+        const bool la = xa ? (wa & kLeafBit) != 0 : (t.y & kLeafBit) != 0;
+        const bool lb = xb ? (wb & kLeafBit) != 0 : (t.z & kLeafBit) != 0;
+        if (la && lb) lmask |= 1u << k;
+        else tmask |= 1u << k;
+      }
     }
     // positions of this lane's outputs (task and leaf counts packed)
     const unsigned mine = (unsigned)__popc(tmask) | ((unsigned)__popc(lmask) << 16);
@@ -2059,31 +2213,48 @@ __global__ void __launch_bounds__(128, 4) k_stream(StreamArgs P) {
     }
     const unsigned tot = __shfl_sync(FULL, incl, 31);
     const unsigned ex = incl - mine;
-    int tpos = sp + (int)(ex & 0xFFFFu), lpos = nlq + (int)(ex >> 16);
+    const int tt = (int)(tot & 0xFFFFu), tl = (int)(tot >> 16);
+    const int room = Cf::LQ - nlq;  // leaf pairs past it go on the stack
+    int tpos = sp + (int)(ex & 0xFFFFu), lr = (int)(ex >> 16);
     unsigned bits = tmask | lmask;
     while (bits) {
-      const int j = __ffs(bits) - 1;
+      const int k = __ffs(bits) - 1;
       bits &= bits - 1;
-      Box bb;
-      uint32_t nb;
-      if (xb) {
-        uint32_t cb;
-        const int jj = xa ? j : gi;
-        load_slot<W>(Q.B.nodes, t.z & kIdx, jj, off, bb, cb);  // L1 hit
-        nb = (cb & kLeafBit) ? (kLeafBit | ((t.z & kIdx) * W + jj)) : cb;
-      } else {
-        item_box<W>(Q.B.nodes, t.z, off, bb);
-        nb = t.z & ~kExpand;
-      }
-      if ((tmask >> j) & 1u) {
+      const int q = gi + k * LPT;
+      const int a = q / NB, b = q - a * NB;
+      const float4 a0 = stage[((ti * 2) * W + a) * 2], a1 = stage[((ti * 2) * W + a) * 2 + 1];
+      const float4 b0 = stage[((ti * 2 + 1) * W + b) * 2];
+      const float4 b1 = stage[((ti * 2 + 1) * W + b) * 2 + 1];
+      const uint32_t wa = __float_as_uint(a1.z), wb = __float_as_uint(b1.z);
+      // the child items: a leaf slot id or a node index (expanding side),
+      // else the task's item itself
+      const uint32_t na = xa ? ((wa & kLeafBit) ? (kLeafBit | ((t.y & kIdx) * W + a)) : wa)
+                             : (t.y & ~kExpand);
+      const uint32_t nb = xb ? ((wb & kLeafBit) ? (kLeafBit | ((t.z & kIdx) * W + b)) : wb)
+                             : (t.z & ~kExpand);
+      if ((tmask >> k) & 1u) {
+        Box ba, bb;
+        ba.lo = mkf3(a0.x, a0.y, a0.z);
+        ba.hi = mkf3(a0.w, a1.x, a1.y);
+        bb.lo = add(mkf3(b0.x, b0.y, b0.z), off);
+        bb.hi = add(mkf3(b0.w, b1.x, b1.y), off);
         const uint2 nt = make_task(na, ba, nb, bb);
         stk[tpos++] = make_uint4(t.x, nt.x, nt.y, 0u);
+      } else if (lr < room) {
+        // leaf pair: absolute first triangles and counts (wa / wb are the
+        // leaves' descriptors: for a side that does not expand, its slot's
+        // child word)
+        lq[nlq + lr] = make_uint4(t.x, (uint32_t)cbv.x + ((wa >> 3) & 0x0FFFFFFFu),
+                                  (uint32_t)cbv.y + ((wb >> 3) & 0x0FFFFFFFu),
+                                  (wa & 7u) | ((wb & 7u) << 8));
+        ++lr;
       } else {
-        lq[lpos++] = make_uint4(t.x, na, nb, 0u);
+        stk[sp + tt + (lr - room)] = make_uint4(t.x, na, nb, 0u);
+        ++lr;
       }
     }
-    sp += (int)(tot & 0xFFFFu);
-    nlq += (int)(tot >> 16);
+    sp += tt + max(0, tl - room);
+    nlq += min(tl, room);
     __syncwarp();
   }
   if (err != DERR_NONE && lane == 0) atomicCAS(Q.err, 0, err);

@@ -49,6 +49,8 @@ def test_tiny_spheres_all_bvh_shapes(ctx, tiny, W, L):
         got, info = ctx.join(ha, hb, width=W, leaf_size=L)
         assert info["n_candidates"] == len(oracle.mbb_candidates(A, B))
         assert np.array_equal(got, exp)
+        got, _ = ctx.join(ha, hb, width=W, leaf_size=L, wave_levels=pierce.PJ_FRONT_STREAM)
+        assert np.array_equal(got, exp), "stream"
 
 
 @pytest.mark.parametrize("mode", ["exact", "warps2", "warps4", "per_pair", "explicit", "graph",
