@@ -629,10 +629,10 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--seed", type=int, default=2001)
     ap.add_argument("--width", type=int, default=4)
-    ap.add_argument("--leaf", type=int, default=4)
+    ap.add_argument("--leaf", type=int, default=2)
     ap.add_argument("--warps", type=int, default=0)
     ap.add_argument("--graph", type=int, default=1)
-    ap.add_argument("--front", default="wave", choices=sorted(FRONT_LEVELS),
+    ap.add_argument("--front", default="stream", choices=sorted(FRONT_LEVELS),
                     help="refinement front end: streaming persistent kernel, breadth-first "
                          "levels, or none (per-warp passes only)")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)

@@ -97,14 +97,15 @@ typedef struct {
                                pass before handing the rest of it to later
                                passes (0: 40,000; < 0: never); the second
                                pass allows 8 times as many                   */
-  int32_t wave_levels;      /* refinement front end.  > 0: this many BVH
-                               levels breadth-first, one thread per child
-                               test, then the per-warp passes (0: 14 levels).
-                               PJ_FRONT_NONE: the per-warp passes alone.
-                               PJ_FRONT_STREAM: the streaming kernel (one
-                               persistent launch; warps keep the tasks of
-                               many pairs in shared memory and balance the
-                               load through a device task queue)            */
+  int32_t wave_levels;      /* refinement front end.  0 or PJ_FRONT_STREAM:
+                               the streaming kernel (one persistent launch;
+                               warps keep the tasks of many pairs in shared
+                               memory, stage nodes and triangles with
+                               asynchronous copies and balance the load
+                               through a device task queue).  > 0: this many
+                               BVH levels breadth-first, one thread per child
+                               test, then the per-warp passes.
+                               PJ_FRONT_NONE: the per-warp passes alone      */
   int32_t kernel_times;     /* 1: also time the front end's launches with CUDA
                                events (pj_pairs.expand_ms / leaf_ms; events
                                between launches cost a little overlap)       */

@@ -1653,14 +1653,14 @@ __device__ __forceinline__ void stage_tri(const float4 *stage, int i, F3 off, F3
 // Leaf rounds stage the triangles of up to kLeafPairs leaf pairs (at most
 // 48 / L) in shared memory: kStageF4 float4 = 4.5 KB per warp, which also
 // holds an expand round's nodes (64 / W tasks x 2 nodes x W slots).
-constexpr int kLeafPairs = 12;
+constexpr int kLeafPairs = 24;
 constexpr int kStageF4 = 288;
 constexpr int kListMax = 384;  // queued (edge, triangle) tests: 32 units x 3 edges x 4 tests
 
 template <int W>
 struct StreamCfg {
   static constexpr int NT = 64 / W;                                // tasks per expand round
-  static constexpr int SC = W == 8 ? 384 : 224;                    // stack entries
+  static constexpr int SC = W == 8 ? 384 : 192;                    // stack entries
   static constexpr int LQ = 64;                                    // leaf-pair entries
   // per warp: stack, leaf queue (uint4 entries), triangle stage, boxes of
   // the staged triangles and of the leaves, pair offsets, pair entries, hit
@@ -1716,7 +1716,8 @@ __device__ __forceinline__ bool queue_push(const StreamArgs &P, const uint4 *stk
   __threadfence();
   for (int k = lane; k < n; k += 32)
     *reinterpret_cast<volatile unsigned *>(&P.dq[base + k].w) = 1u;
-  __threadfence();
+  // no fence needed before publishing: a consumer waits for each slot's
+  // ready flag, which may become visible after the count
   __syncwarp();
   if (lane == 0) atomicAdd(reinterpret_cast<int *>(sq(P, SQ_AVAIL)), n);
   return true;
@@ -1755,7 +1756,7 @@ __global__ void __launch_bounds__(128, 4) k_stream(StreamArgs P) {
   const WaveArgs &Q = P.w;
   const unsigned lt = (1u << lane) - 1u;
   const int L = 1 << Q.lshift;                    // leaf size
-  const int pmax = min(kLeafPairs, 48 / L);       // leaf pairs per round
+  const int pmax = min(kLeafPairs, 48 / L);       // leaf pairs per round (<= 32)
   const int upi = L == 8 ? 16 : 32;               // leaf units per filter iteration
   const F3 zero = mkf3(0.f, 0.f, 0.f);
   volatile const uint8_t *vflags = Q.flags;
@@ -1787,33 +1788,42 @@ __global__ void __launch_bounds__(128, 4) k_stream(StreamArgs P) {
   // surviving (edge, triangle) tests run one per lane.
   auto leaf_round = [&]() {
     const int np = min(nlq, pmax);
+    uint4 pe = make_uint4(0u, 0u, 0u, 0u);
     if (lane < np) {
-      const uint4 e = lq[nlq - 1 - lane];
-      const bool alive = vflags[e.x] == 0;
-      const F3 o = alive ? cand_offset(Q, e.x) : zero;
-      s_pe[lane] = e;
-      s_hit[lane] = alive ? 0u : 1u;
-      s_off[3 * lane] = o.x;
-      s_off[3 * lane + 1] = o.y;
-      s_off[3 * lane + 2] = o.z;
-      if (alive) {
-        lc.lp += 1;
-        lc.bytes += 48u * ((e.w & 7u) + ((e.w >> 8) & 7u) + 2u);
-      }
+      pe = lq[nlq - 1 - lane];
+      s_pe[lane] = pe;
     }
     __syncwarp();
     nlq -= np;
+    // the pair's flag and offset load while the triangles are copied (a
+    // pair found intersecting meanwhile is copied for nothing)
+    uint8_t pfl = 1;
+    F3 po = zero;
+    if (lane < np) {
+      pfl = vflags[pe.x];
+      po = cand_offset(Q, pe.x);
+    }
     // stage: chunk f = ((p * 2 + side) * L + t) * 3 + k
     const int nch = np * 2 * L * 3;
     for (int f = lane; f < nch; f += 32) {
       const int k = f % 3, r = f / 3;
       const int t = r % L, ps = r / L, side = ps & 1, p = ps >> 1;
-      if (s_hit[p]) continue;
       const uint4 e = s_pe[p];
       const int n = (int)((side ? e.w >> 8 : e.w) & 7u) + 1;
       if (t >= n) continue;
       const float4 *src = (side ? Q.B.trirec : Q.A.trirec) + 3 * ((int64_t)(side ? e.z : e.y) + t) + k;
       cp_async16(stage + f, src);
+    }
+    if (lane < np) {
+      const bool alive = pfl == 0;
+      s_hit[lane] = alive ? 0u : 1u;
+      s_off[3 * lane] = po.x;
+      s_off[3 * lane + 1] = po.y;
+      s_off[3 * lane + 2] = po.z;
+      if (alive) {
+        lc.lp += 1;
+        lc.bytes += 48u * ((pe.w & 7u) + ((pe.w >> 8) & 7u) + 2u);
+      }
     }
     cp_async_wait_all();
     __syncwarp();
@@ -1837,14 +1847,14 @@ __global__ void __launch_bounds__(128, 4) k_stream(StreamArgs P) {
       bp[5] = fmaxf(a.z, fmaxf(b.z, c.z));
     }
     __syncwarp();
-    if (lane < 2 * np) {
-      const int p = lane >> 1, side = lane & 1;
+    for (int ps = lane; ps < 2 * np; ps += 32) {
+      const int p = ps >> 1, side = ps & 1;
       if (!s_hit[p]) {
         const uint4 e = s_pe[p];
         const int n = (int)((side ? e.w >> 8 : e.w) & 7u) + 1;
         float b[6] = {3.4e38f, 3.4e38f, 3.4e38f, -3.4e38f, -3.4e38f, -3.4e38f};
         for (int t = 0; t < n; ++t) {
-          const float *tp = s_tbox + 6 * (lane * L + t);
+          const float *tp = s_tbox + 6 * (ps * L + t);
           b[0] = fminf(b[0], tp[0]);
           b[1] = fminf(b[1], tp[1]);
           b[2] = fminf(b[2], tp[2]);
@@ -1852,22 +1862,22 @@ __global__ void __launch_bounds__(128, 4) k_stream(StreamArgs P) {
           b[4] = fmaxf(b[4], tp[4]);
           b[5] = fmaxf(b[5], tp[5]);
         }
-        float *bp = s_box + 6 * lane;
+        float *bp = s_box + 6 * ps;
 #pragma unroll
         for (int q = 0; q < 6; ++q) bp[q] = b[q];
       }
     }
     __syncwarp();
-    // the queued (edge, triangle) tests, one per lane: code = p | dir << 4 |
-    // s << 5 | k << 8 | t << 10
+    // the queued (edge, triangle) tests, one per lane: code = p | dir << 5 |
+    // s << 6 | k << 9 | t << 11
     int nlist = 0;
     auto flush = [&]() {
       for (int i0 = 0; i0 < nlist; i0 += 32) {
         const int i = i0 + lane;
         if (i < nlist) {
           const unsigned code = s_list[i];
-          const int p = code & 15, dir = (code >> 4) & 1, si = (code >> 5) & 7;
-          const int k = (code >> 8) & 3, t = (code >> 10) & 7;
+          const int p = code & 31, dir = (code >> 5) & 1, si = (code >> 6) & 7;
+          const int k = (code >> 9) & 3, t = (code >> 11) & 7;
           if (!s_hit[p]) {
             const F3 o = mkf3(s_off[3 * p], s_off[3 * p + 1], s_off[3 * p + 2]);
             F3 v0, v1, v2, a, b, c;
@@ -1954,7 +1964,7 @@ __global__ void __launch_bounds__(128, 4) k_stream(StreamArgs P) {
         const int b = __ffs(mask) - 1;
         mask &= mask - 1;
         const int k = b / L, t = b - k * L;
-        s_list[pos++] = (unsigned short)(p | (dir << 4) | (si << 5) | (k << 8) | (t << 10));
+        s_list[pos++] = (unsigned short)(p | (dir << 5) | (si << 6) | (k << 9) | (t << 11));
       }
       nlist += tot;
       __syncwarp();
@@ -2576,12 +2586,13 @@ pj_status run_join(Ctx *ctx, Dataset *A, Dataset *B, const int32_t *cand,
   uint4 *q2 = (uint4 *)ws_get(ctx, "spill2", sizeof(uint4) * (size_t)q_cap, &st);
   if (!q2) return st;
   unsigned int *qctr = reinterpret_cast<unsigned int *>(d_misc + 3);  // q1 n/pos, q2 n/pos
-  // front end: wave_levels > 0 breadth-first levels (0: 14), PJ_FRONT_STREAM
-  // the streaming kernel, PJ_FRONT_NONE none (the per-warp passes from the
+  // front end: 0 or PJ_FRONT_STREAM the streaming kernel, > 0 that many
+  // breadth-first levels, PJ_FRONT_NONE none (the per-warp passes from the
   // candidates).  Both front ends start with the per-thread parity rays,
   // whose stack needs the BVH depth to stay within 64 levels.
-  int wave_levels = o->wave_levels > 0 ? o->wave_levels : (o->wave_levels == 0 ? 14 : 0);
-  bool stream = o->wave_levels == PJ_FRONT_STREAM && o->launch_mode != PJ_LAUNCH_PER_PAIR;
+  int wave_levels = o->wave_levels > 0 ? o->wave_levels : 0;
+  bool stream = (o->wave_levels == 0 || o->wave_levels == PJ_FRONT_STREAM) &&
+                o->launch_mode != PJ_LAUNCH_PER_PAIR;
   if (std::max(bA.max_depth, bB.max_depth) > 64) {
     wave_levels = 0;
     stream = false;
@@ -2751,6 +2762,8 @@ pj_status run_join(Ctx *ctx, Dataset *A, Dataset *B, const int32_t *cand,
         ap.q_par_n = hc;
         ap.q_par_pos = hc + 1;
         ap.q_par_cap = wpar_cap;
+        // the long rays go to warps before the traversal: a containment-only
+        // pair (no crossing to stop at) is the costliest kind to traverse
         PJ_CK(launch_pdl(pick_wave_parity(W), wave_grid[2], 128, 0, s, wa));
         PJ_CK(launch_pdl(kern_tasks, (int)blocks, threads, smem, s, ap));
         if (timed) PJ_CK(cudaEventRecord(ev[4], s));
