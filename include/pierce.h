@@ -109,6 +109,11 @@ typedef struct {
   int32_t kernel_times;     /* 1: also time the front end's launches with CUDA
                                events (pj_pairs.expand_ms / leaf_ms; events
                                between launches cost a little overlap)       */
+  int32_t wait_polls;       /* streaming kernel: bound on the polls of each of
+                               its waits (0: 2^19, about half a second); a
+                               wait that runs out sets an error word and the
+                               join is redone by plain depth-first traversal
+                               (same result, slower)                        */
 } pj_join_opts;
 
 /* Result of a join.  Owned by the library until pj_free_pairs. */

@@ -91,6 +91,19 @@ __device__ __forceinline__ int cert(float v, float e) {
   return v > e ? 1 : (v < -e ? -1 : 0);
 }
 
+// Orientations the filter cannot decide are most often exact zeros of a
+// simple kind, which plain comparisons certify: four points in one
+// axis-aligned plane (walls, floors and roofs of grid-aligned solids that
+// touch) or a fourth point equal to one of the first three (shared
+// vertices).  Either makes the determinant exactly 0, the value the int64
+// path would compute.
+__device__ __forceinline__ bool zero_orient(F3 a, F3 b, F3 c, F3 d) {
+  return (a.x == b.x && b.x == c.x && c.x == d.x) || (a.y == b.y && b.y == c.y && c.y == d.y) ||
+         (a.z == b.z && b.z == c.z && c.z == d.z) ||
+         (d.x == a.x && d.y == a.y && d.z == a.z) || (d.x == b.x && d.y == b.y && d.z == b.z) ||
+         (d.x == c.x && d.y == c.y && d.z == c.z);
+}
+
 // ---------------------------------------------------------------------------
 // int64 orientation (exact).  Differences are below 2^19 in magnitude (grid
 // 2^18, translated candidates stay on the grid), 2x2 minors below 2^39 and a
@@ -152,6 +165,7 @@ __device__ __forceinline__ bool segtri_filtered(F3 p, F3 q, F3 a, F3 b, F3 c, bo
   dot_p(A, bc, dv, ev);
   int sp = -cert(dv, ev);
   if (sp == 0) {
+    if (zero_orient(a, b, c, p)) return false;
     *exact = true;
     const I3 pi = toi(p);
     sp = -sgn64(dot64(isub(toi(a), pi), cross64(isub(toi(b), pi), isub(toi(c), pi))));
@@ -162,6 +176,7 @@ __device__ __forceinline__ bool segtri_filtered(F3 p, F3 q, F3 a, F3 b, F3 c, bo
   dot_p(Aq, bcq, dv, ev);
   int sq = -cert(dv, ev);
   if (sq == 0) {
+    if (zero_orient(a, b, c, q)) return false;
     *exact = true;
     const I3 qi = toi(q);
     sq = -sgn64(dot64(isub(toi(a), qi), cross64(isub(toi(b), qi), isub(toi(c), qi))));
@@ -175,6 +190,7 @@ __device__ __forceinline__ bool segtri_filtered(F3 p, F3 q, F3 a, F3 b, F3 c, bo
     dot_p(d, ab, dv, ev);
     su = cert(dv, ev);
     if (su == 0) {
+      if (zero_orient(p, q, a, b)) return false;
       *exact = true;
       const I3 pi = toi(p);
       su = sgn64(dot64(isub(toi(q), pi), cross64(isub(toi(a), pi), isub(toi(b), pi))));
@@ -186,6 +202,7 @@ __device__ __forceinline__ bool segtri_filtered(F3 p, F3 q, F3 a, F3 b, F3 c, bo
     int sv = cert(dv, ev);
     if (sv == -su) return false;
     if (sv == 0) {
+      if (zero_orient(p, q, b, c)) return false;
       *exact = true;
       const I3 pi = toi(p);
       sv = sgn64(dot64(isub(toi(q), pi), cross64(isub(toi(b), pi), isub(toi(c), pi))));
@@ -197,6 +214,7 @@ __device__ __forceinline__ bool segtri_filtered(F3 p, F3 q, F3 a, F3 b, F3 c, bo
     dot_p(d, ca, dv, ev);
     int sw = cert(dv, ev);
     if (sw == 0) {
+      if (zero_orient(p, q, c, a)) return false;
       *exact = true;
       const I3 pi = toi(p);
       sw = sgn64(dot64(isub(toi(q), pi), cross64(isub(toi(c), pi), isub(toi(a), pi))));

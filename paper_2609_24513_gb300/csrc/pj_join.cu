@@ -2507,10 +2507,15 @@ pj_status run_join(Ctx *ctx, Dataset *A, Dataset *B, const int32_t *cand,
   PJ_CK(cudaMemsetAsync(d_err, 0, sizeof(int) * 4, s));
   PJ_CK(cudaEventRecord(e0, s));
 
-  // 1. candidates
+  // 1. candidates.  C is the candidate count, Ccap what buffers and launches
+  // are sized for: when every pair of the two datasets fits a modest buffer,
+  // the device box join's count stays on the device (every later kernel
+  // reads it there) and C is read back with the result, so the join runs
+  // without a host round trip in the middle.
   int32_t *d_cand = nullptr;
   int32_t *d_off = nullptr;
-  int64_t C = 0;
+  int64_t C = 0, Ccap = 0;
+  bool count_on_host = true;
   if (n_cand < 0) {
     // bounding-box filter join on the device
     const int64_t MA = A->M, MB = B->M;
@@ -2523,16 +2528,22 @@ pj_status run_join(Ctx *ctx, Dataset *A, Dataset *B, const int32_t *cand,
     ++ctx->launches;
     PJ_CK(cudaGetLastError());
     if ((st = scan_i64(ctx, counts, offs, MA, d_misc, s)) != PJ_OK) return st;
-    PJ_CK(cudaMemcpyAsync(h_misc, d_misc, 8, cudaMemcpyDeviceToHost, s));
-    PJ_CK(cudaStreamSynchronize(s));
-    C = h_misc[0];
-    d_cand = (int32_t *)ws_get(ctx, "cand", sizeof(int32_t) * 2 * (size_t)std::max<int64_t>(C, 1), &st);
+    const int64_t all = self_join ? MA * (MA - 1) / 2 : MA * MB;
+    if (all <= (int64_t(1) << 24) && o->launch_mode != PJ_LAUNCH_PER_PAIR) {
+      Ccap = std::max<int64_t>(all, 1);
+      count_on_host = false;
+    } else {
+      PJ_CK(cudaMemcpyAsync(h_misc, d_misc, 8, cudaMemcpyDeviceToHost, s));
+      PJ_CK(cudaStreamSynchronize(s));
+      C = Ccap = h_misc[0];
+    }
+    d_cand = (int32_t *)ws_get(ctx, "cand", sizeof(int32_t) * 2 * (size_t)std::max<int64_t>(Ccap, 1), &st);
     if (!d_cand) return st;
     k_mbb<true><<<nb, MBB_T, 0, s>>>(A->d_aabb, MA, B->d_aabb, MB, self_join, nullptr, offs, d_cand);
     ++ctx->launches;
     PJ_CK(cudaGetLastError());
   } else {
-    C = n_cand;
+    C = Ccap = n_cand;
     if (cand_on_device) {
       d_cand = const_cast<int32_t *>(cand);
       d_off = const_cast<int32_t *>(cand_off);
@@ -2555,11 +2566,11 @@ pj_status run_join(Ctx *ctx, Dataset *A, Dataset *B, const int32_t *cand,
           d_cand, d_off, C, A->M, B->M, B->d_aabb, d_err);
     if (C > 0) ++ctx->launches;
   }
-  uint8_t *d_flags = (uint8_t *)ws_get(ctx, "flags", (size_t)std::max<int64_t>(C, 1), &st);
+  uint8_t *d_flags = (uint8_t *)ws_get(ctx, "flags", (size_t)std::max<int64_t>(Ccap, 1), &st);
   if (!d_flags) return st;
-  int32_t *d_pairs = (int32_t *)ws_get(ctx, "pairs", sizeof(int32_t) * 2 * (size_t)std::max<int64_t>(C, 1), &st);
+  int32_t *d_pairs = (int32_t *)ws_get(ctx, "pairs", sizeof(int32_t) * 2 * (size_t)std::max<int64_t>(Ccap, 1), &st);
   if (!d_pairs) return st;
-  int nchunks = (int)std::max<int64_t>(1, (C + CMP_CHUNK - 1) / CMP_CHUNK);
+  int nchunks = (int)std::max<int64_t>(1, (Ccap + CMP_CHUNK - 1) / CMP_CHUNK);
   int64_t *bcount = (int64_t *)ws_get(ctx, "cmp_counts", sizeof(int64_t) * nchunks, &st);
   if (!bcount) return st;
   int64_t *boff = (int64_t *)ws_get(ctx, "cmp_offs", sizeof(int64_t) * nchunks, &st);
@@ -2605,7 +2616,7 @@ pj_status run_join(Ctx *ctx, Dataset *A, Dataset *B, const int32_t *cand,
   unsigned int *wctr = nullptr;
   const int wctr_words = 2 * std::max(wave_levels, 0) + SQ_WORDS + 8;
   const unsigned int wpar_cap =
-      (unsigned int)std::min<int64_t>(std::max<int64_t>(2 * C, 1024), 1 << 22);
+      (unsigned int)std::min<int64_t>(std::max<int64_t>(2 * Ccap, 1024), 1 << 22);
   int wave_grid[3] = {1, 1, 1};  // expand/init, leaf, parity: one resident wave
   bool front = (wave_levels > 0 || stream) && o->launch_mode != PJ_LAUNCH_PER_PAIR;
   int stream_grid = 1, stream_smem = 0;
@@ -2617,7 +2628,7 @@ pj_status run_join(Ctx *ctx, Dataset *A, Dataset *B, const int32_t *cand,
   if (stream && front) {
     dq = (uint4 *)ws_get_zeroed(ctx, "stream_queue", sizeof(uint4) * (size_t)dq_cap, s, &st);
     if (!dq) return st;
-    cbase = (int2 *)ws_get(ctx, "cand_base", sizeof(int2) * (size_t)std::max<int64_t>(C, 1), &st);
+    cbase = (int2 *)ws_get(ctx, "cand_base", sizeof(int2) * (size_t)std::max<int64_t>(Ccap, 1), &st);
     if (!cbase) return st;
     stream_smem = 4 * stream_smem_per_warp(W);
     PJ_CK(cudaFuncSetAttribute(ks, cudaFuncAttributeMaxDynamicSharedMemorySize, stream_smem));
@@ -2648,7 +2659,7 @@ pj_status run_join(Ctx *ctx, Dataset *A, Dataset *B, const int32_t *cand,
   }
   unsigned int *d_cycles = nullptr;
   if (o->record_cycles) {
-    d_cycles = (unsigned int *)ws_get(ctx, "cycles", sizeof(unsigned int) * (size_t)std::max<int64_t>(C, 1), &st);
+    d_cycles = (unsigned int *)ws_get(ctx, "cycles", sizeof(unsigned int) * (size_t)std::max<int64_t>(Ccap, 1), &st);
     if (!d_cycles) return st;
   }
   RefineArgs args;
@@ -2684,11 +2695,11 @@ pj_status run_join(Ctx *ctx, Dataset *A, Dataset *B, const int32_t *cand,
   args.q_par_pos = nullptr;
   args.q_par_cap = 0;
   int64_t blocks = 1;
-  if (C > 0 && o->launch_mode != PJ_LAUNCH_PER_PAIR) {
+  if (Ccap > 0 && o->launch_mode != PJ_LAUNCH_PER_PAIR) {
     int occ = 0;
     PJ_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, threads, smem));
     if (occ < 1) return fail(ctx, PJ_ERR_INTERNAL, "refinement kernel does not fit on an SM");
-    blocks = std::min<int64_t>((int64_t)occ * ctx->num_sms, (C * k * 32 + threads - 1) / threads);
+    blocks = std::min<int64_t>((int64_t)occ * ctx->num_sms, (Ccap * k * 32 + threads - 1) / threads);
     blocks = std::max<int64_t>(blocks, 1);
   }
   if (o->launch_mode == PJ_LAUNCH_PER_PAIR && k != 1)
@@ -2729,7 +2740,7 @@ pj_status run_join(Ctx *ctx, Dataset *A, Dataset *B, const int32_t *cand,
   // everything from here to the compacted pairs is a fixed sequence of
   // stream operations (no host synchronisation), so it can be captured
   auto device_part = [&](bool timed) -> pj_status {
-    if (C > 0) {
+    if (Ccap > 0) {
       if (o->launch_mode == PJ_LAUNCH_PER_PAIR) {
         args.q_out = nullptr;
         args.q_out_n = nullptr;
@@ -2744,7 +2755,7 @@ pj_status run_join(Ctx *ctx, Dataset *A, Dataset *B, const int32_t *cand,
         // parity rays (per thread, then the long ones per warp), then the
         // streaming refinement in one persistent launch
         PJ_CK(cudaMemsetAsync(wctr, 0, sizeof(unsigned int) * wctr_words, s));
-        PJ_CK(cudaMemsetAsync(d_flags, 0, (size_t)C, s));
+        PJ_CK(cudaMemsetAsync(d_flags, 0, (size_t)Ccap, s));
         WaveArgs wa = make_wave_args();
         // words: [0, SQ_WORDS) the streaming launch's control words, then the
         // parity hand-over fill and position, a zero count and the intake
@@ -2773,7 +2784,7 @@ pj_status run_join(Ctx *ctx, Dataset *A, Dataset *B, const int32_t *cand,
         sa.dq = dq;
         sa.cbase = cbase;
         sa.dq_cap = dq_cap;
-        sa.spin_limit = 1u << 19;
+        sa.spin_limit = o->wait_polls > 0 ? (unsigned)o->wait_polls : (1u << 19);
         sa.hungry_max = 2u * (unsigned)ctx->num_sms;
         sa.give_after = 20000;
         const bool kt = timed && !kev.empty();
@@ -2792,7 +2803,7 @@ pj_status run_join(Ctx *ctx, Dataset *A, Dataset *B, const int32_t *cand,
         // wavefront front end, then the warp passes over what is left
         PJ_CK(cudaMemsetAsync(d_misc + 2, 0, 48, s));  // work and spill counters
         PJ_CK(cudaMemsetAsync(wctr, 0, sizeof(unsigned int) * wctr_words, s));
-        PJ_CK(cudaMemsetAsync(d_flags, 0, (size_t)C, s));
+        PJ_CK(cudaMemsetAsync(d_flags, 0, (size_t)Ccap, s));
         WaveArgs wa = make_wave_args();
         unsigned int *qn = wctr, *ln = wctr + wave_levels + 1, *misc = ln + wave_levels;
         wa.q_par_n = misc + 1;
@@ -2909,8 +2920,9 @@ pj_status run_join(Ctx *ctx, Dataset *A, Dataset *B, const int32_t *cand,
   char gk[256];
   snprintf(gk, sizeof(gk), "%p|%p|%p|%p|%p|%d|%d|%d|%d|%d|%lld|%d|%d", (void *)A, (void *)B,
            (void *)d_cand, (void *)d_off, (void *)d_cycles, W, key.second, (int)exact, k,
-           (int)o->launch_mode, (long long)C, (int)budget1,
+           (int)o->launch_mode, (long long)Ccap, (int)budget1,
            args.max_pop * 1000 + wave_levels * 2 + (stream ? 1 : 0));
+  snprintf(gk + strlen(gk), sizeof(gk) - strlen(gk), "|%d", (int)o->wait_polls);
   bool replayed = false;
   if (graph) {
     auto it = ctx->graphs.find(gk);
@@ -2944,7 +2956,7 @@ pj_status run_join(Ctx *ctx, Dataset *A, Dataset *B, const int32_t *cand,
     }
   }
   PJ_CK(cudaEventRecord(e1, s));
-  PJ_CK(cudaMemcpyAsync(h_misc + 1, d_misc + 1, 8, cudaMemcpyDeviceToHost, s));
+  PJ_CK(cudaMemcpyAsync(h_misc, d_misc, 16, cudaMemcpyDeviceToHost, s));
   int herr[4];
   PJ_CK(cudaMemcpyAsync(herr, d_err, sizeof(herr), cudaMemcpyDeviceToHost, s));
   PJ_CK(cudaStreamSynchronize(s));
@@ -2963,13 +2975,14 @@ pj_status run_join(Ctx *ctx, Dataset *A, Dataset *B, const int32_t *cand,
     PJ_CK(cudaMemsetAsync(d_err, 0, sizeof(int) * 4, s));
     if ((st = device_part(true)) != PJ_OK) return st;
     PJ_CK(cudaEventRecord(e1, s));
-    PJ_CK(cudaMemcpyAsync(h_misc + 1, d_misc + 1, 8, cudaMemcpyDeviceToHost, s));
+    PJ_CK(cudaMemcpyAsync(h_misc, d_misc, 16, cudaMemcpyDeviceToHost, s));
     PJ_CK(cudaMemcpyAsync(herr, d_err, sizeof(herr), cudaMemcpyDeviceToHost, s));
     PJ_CK(cudaStreamSynchronize(s));
     replayed = false;
   }
   if (herr[0]) return fail(ctx, PJ_ERR_INTERNAL, "traversal stack capacity exceeded");
   const int64_t K = h_misc[1];
+  if (!count_on_host) C = h_misc[0];  // the device box join's count
   float ms = 0.f;
   cudaEventElapsedTime(&ms, e0, e1);
   cudaEventElapsedTime(&out->mbb_ms, ev[0], ev[1]);

@@ -49,7 +49,8 @@ class pj_join_opts(ctypes.Structure):
                 ("launch_mode", ctypes.c_int32), ("use_graph", ctypes.c_int32),
                 ("out_host", ctypes.c_int32), ("keep_flags", ctypes.c_int32),
                 ("record_cycles", ctypes.c_int32), ("spill_budget", ctypes.c_int32),
-                ("wave_levels", ctypes.c_int32), ("kernel_times", ctypes.c_int32)]
+                ("wave_levels", ctypes.c_int32), ("kernel_times", ctypes.c_int32),
+                ("wait_polls", ctypes.c_int32)]
 
 
 class pj_pairs(ctypes.Structure):
@@ -264,7 +265,7 @@ def pj_join_intersects_ex(ctx, a: int, b: int, cand=None, cand_offsets=None, sel
                           width=0, leaf_size=0, warps_per_pair=0, leaf_mode=PJ_LEAF_FILTERED,
                           launch_mode=PJ_LAUNCH_PERSISTENT, use_graph=False, out_host=True,
                           keep_flags=False, record_cycles=False, spill_budget=0, wave_levels=0,
-                          kernel_times=False, stream=None):
+                          kernel_times=False, wait_polls=0, stream=None):
     """Run the join.  Returns the filled pj_pairs (free it with pj_free_pairs).
 
     cand / cand_offsets: None (device bounding-box filter join), numpy int32
@@ -279,7 +280,7 @@ def pj_join_intersects_ex(ctx, a: int, b: int, cand=None, cand_offsets=None, sel
         n = int(cand.shape[0])
     opts = pj_join_opts(width, leaf_size, warps_per_pair, leaf_mode, launch_mode,
                         int(use_graph), int(out_host), int(keep_flags), int(record_cycles),
-                        int(spill_budget), int(wave_levels), int(kernel_times))
+                        int(spill_budget), int(wave_levels), int(kernel_times), int(wait_polls))
     res = pj_pairs()
     rc = load().pj_join_intersects_ex(ctx, a, b, _ptr(cand), _ptr(cand_offsets), n,
                                       1 if dev else 0, int(self_join), ctypes.byref(opts),

@@ -300,6 +300,23 @@ def test_segtri_batch_matches_oracle(ctx):
         q = np.rint(m + 50 * n + rng.integers(-1, 2, size=3))
         near.append(np.clip(np.stack([p, q, a, b, c]), 0, synth.QMAX))
     groups.append(np.array(near, dtype=np.int64))
+    # exact zeros at full-range coordinates, which the filter cannot certify
+    # by magnitude: all five points (or p or q with the triangle) in one
+    # axis-aligned plane, and edges starting at a triangle vertex
+    zeros = []
+    for i in range(3000):
+        X = rng.integers(0, synth.QMAX + 1, size=(5, 3))
+        k = int(rng.integers(0, 3))
+        kind = i % 3
+        if kind == 0:
+            X[:, k] = X[0, k]                       # everything in the plane x_k = const
+        elif kind == 1:
+            X[[0, 2, 3, 4], k] = X[2, k]            # p and the triangle in the plane
+            X[1] = X[0] + rng.integers(-5000, 5000, size=3)
+        else:
+            X[0] = X[2 + int(rng.integers(0, 3))]   # p is a triangle vertex
+        zeros.append(np.clip(X, 0, synth.QMAX))
+    groups.append(np.array(zeros, dtype=np.int64))
     P = np.concatenate(groups).astype(np.int64)
     exp = np.array([oracle.segtri_strict(*x) for x in P], dtype=np.uint8)
     pq = torch.from_numpy(P[:, :2].reshape(-1, 6).astype(np.float32)).cuda()
@@ -418,3 +435,23 @@ def test_dense_overlap_stack_spills(ctx, W, L):
                dict(wave_levels=pierce.PJ_FRONT_STREAM, leaf_mode=pierce.PJ_LEAF_EXACT)):
         got, _ = ctx.join(ha, hb, cand=cand, width=W, leaf_size=L, **kw)
         assert got.tolist() == [[1, 1], [2, 2]], kw
+
+
+def test_stream_wait_timeout_falls_back(ctx, tiny):
+    """Every bounded wait of the streaming kernel limited to one poll: idle
+    warps give up at once, the kernel records the error word, and the host
+    redoes the join by plain depth-first traversal -- the same pairs, more
+    kernel launches.  (The wait runs out on purpose; nothing faults.)"""
+    A, B, ha, hb, exp = tiny[0]
+    before = ctx.counters()["kernel_launches"]
+    got, _ = ctx.join(ha, hb, width=4, leaf_size=4, wave_levels=pierce.PJ_FRONT_STREAM)
+    normal = ctx.counters()["kernel_launches"] - before
+    before = ctx.counters()["kernel_launches"]
+    got2, _ = ctx.join(ha, hb, width=4, leaf_size=4, wave_levels=pierce.PJ_FRONT_STREAM,
+                       wait_polls=1)
+    redone = ctx.counters()["kernel_launches"] - before
+    assert np.array_equal(got, exp) and np.array_equal(got2, exp)
+    assert redone > normal
+    # the queue is clean again afterwards: the next join is exact and fast-path
+    got3, _ = ctx.join(ha, hb, width=4, leaf_size=4, wave_levels=pierce.PJ_FRONT_STREAM)
+    assert np.array_equal(got3, exp)
