@@ -45,6 +45,8 @@ pj_status exec_init(Ctx *ctx, Exec *e) {
   cudaError_t r = cudaMalloc(&e->d_err, sizeof(int) * 4);
   if (r == cudaSuccess) r = cudaMemset(e->d_err, 0, sizeof(int) * 4);
   if (r == cudaSuccess) r = cudaMallocHost(&e->h_pinned, 4096);
+  for (auto &ev : e->ev)
+    if (r == cudaSuccess) r = cudaEventCreate(&ev);
   if (r != cudaSuccess) return cuda_fail(ctx, r, "exec_init");
   return PJ_OK;
 }
@@ -54,8 +56,11 @@ void exec_free(Exec *e) {
   e->ws.clear();
   cudaFree(e->d_err);
   cudaFreeHost(e->h_pinned);
+  for (auto &ev : e->ev)
+    if (ev) cudaEventDestroy(ev);
   e->d_err = nullptr;
   e->h_pinned = nullptr;
+  for (auto &ev : e->ev) ev = nullptr;
 }
 
 void *ws_get(Ctx *ctx, const char *name, size_t bytes, pj_status *st) {

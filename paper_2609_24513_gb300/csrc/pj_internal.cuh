@@ -97,6 +97,7 @@ struct Exec {
   void *h_pinned = nullptr;  // 4 KiB pinned host scratch
   std::string err;           // last failure message of a serving thread
   bool borrow_out = false;   // join results stay in the workspaces (serving)
+  cudaEvent_t ev[6] = {};    // a join's phase events, created once
 };
 
 struct Serve;  // serving state (pj_serve.cu)

@@ -16,6 +16,8 @@
 //   - Result materialisation (Sec. 3.5) is one flag per candidate followed
 //     by a prefix-sum compaction, so nothing needs deduplication.
 #include <algorithm>
+#include <map>
+#include <tuple>
 #include <mutex>
 #include <cstdio>
 #include <cstring>
@@ -1659,7 +1661,11 @@ constexpr int kListMax = 384;  // queued (edge, triangle) tests: 32 units x 3 ed
 
 template <int W>
 struct StreamCfg {
-  static constexpr int NT = 64 / W;                                // tasks per expand round
+  static constexpr int NT = W == 2 ? 16 : 64 / W;                  // tasks per expand round
+  // staged node region of one (task, side): W slots of two float4 plus one
+  // float4 of padding, so that regions start on different shared-memory banks
+  static constexpr int RS = 2 * W + 1;
+  static_assert(NT * 2 * RS <= kStageF4, "an expand round's nodes must fit the stage");
   static constexpr int SC = W == 8 ? 384 : 192;                    // stack entries
   static constexpr int LQ = 64;                                    // leaf-pair entries
   // per warp: stack, leaf queue (uint4 entries), triangle stage, boxes of
@@ -2160,7 +2166,7 @@ __global__ void __launch_bounds__(128, 4) k_stream(StreamArgs P) {
     const bool act = ti < npop;
     const uint4 t = act ? stk[sp - 1 - ti] : make_uint4(0u, 0u, 0u, 0u);
     const bool xa = t.y & kExpand, xb = t.z & kExpand;
-    // stage: task i, side s, slot j (of W) at float4 index ((i * 2 + s) * W + j) * 2;
+    // stage: task i, side s, slot j (of W) at float4 index (i * 2 + s) * RS + 2 j;
     // one lane per (task, side) copies the W child slots of an expanding
     // node, or the one slot of the item's own box
     for (int is = lane; is < npop * 2; is += 32) {
@@ -2174,7 +2180,7 @@ __global__ void __launch_bounds__(128, 4) k_stream(StreamArgs P) {
       else if (item & kLeafBit) word = (int64_t)(idx / W) * Cfg<W>::SW + 8 * (idx % W + 1);
       else word = (int64_t)idx * Cfg<W>::SW;
       const float4 *src = reinterpret_cast<const float4 *>((side ? Q.B.nodes : Q.A.nodes) + word);
-      float4 *dst = stage + 2 * is * W;
+      float4 *dst = stage + is * Cf::RS;
       const int n = x ? 2 * W : 2;
       for (int h = 0; h < n; ++h) cp_async16(dst + h, src + h);
     }
@@ -2196,9 +2202,9 @@ __global__ void __launch_bounds__(128, 4) k_stream(StreamArgs P) {
     if (live) {
       for (int q = gi, k = 0; q < NA * NB; q += LPT, ++k) {
         const int a = q / NB, b = q - a * NB;
-        const float4 a0 = stage[((ti * 2) * W + a) * 2], a1 = stage[((ti * 2) * W + a) * 2 + 1];
-        const float4 b0 = stage[((ti * 2 + 1) * W + b) * 2];
-        const float4 b1 = stage[((ti * 2 + 1) * W + b) * 2 + 1];
+        const float4 a0 = stage[(ti * 2) * Cf::RS + 2 * a], a1 = stage[(ti * 2) * Cf::RS + 2 * a + 1];
+        const float4 b0 = stage[(ti * 2 + 1) * Cf::RS + 2 * b];
+        const float4 b1 = stage[(ti * 2 + 1) * Cf::RS + 2 * b + 1];
         const uint32_t wa = __float_as_uint(a1.z), wb = __float_as_uint(b1.z);
         c_bt += 1;
         if ((xa && wa == kEmpty) || (xb && wb == kEmpty)) continue;
@@ -2232,9 +2238,9 @@ __global__ void __launch_bounds__(128, 4) k_stream(StreamArgs P) {
       bits &= bits - 1;
       const int q = gi + k * LPT;
       const int a = q / NB, b = q - a * NB;
-      const float4 a0 = stage[((ti * 2) * W + a) * 2], a1 = stage[((ti * 2) * W + a) * 2 + 1];
-      const float4 b0 = stage[((ti * 2 + 1) * W + b) * 2];
-      const float4 b1 = stage[((ti * 2 + 1) * W + b) * 2 + 1];
+      const float4 a0 = stage[(ti * 2) * Cf::RS + 2 * a], a1 = stage[(ti * 2) * Cf::RS + 2 * a + 1];
+      const float4 b0 = stage[(ti * 2 + 1) * Cf::RS + 2 * b];
+      const float4 b1 = stage[(ti * 2 + 1) * Cf::RS + 2 * b + 1];
       const uint32_t wa = __float_as_uint(a1.z), wb = __float_as_uint(b1.z);
       // the child items: a leaf slot id or a node index (expanding side),
       // else the task's item itself
@@ -2462,6 +2468,40 @@ static Side make_side(Dataset *d, Bvh &b) {
   return s;
 }
 
+// Blocks of `kern` resident per SM at (block, dynamic shared memory).  The
+// first query for a kernel on a device also raises its dynamic shared-memory
+// limit to the device's maximum, so that every later launch fits.  Both
+// calls cost microseconds of host time ahead of a join's first launch, so
+// the answers are kept per device, kernel and shape.
+static cudaError_t occupancy(int device, const void *kern, int block, size_t smem, int *occ) {
+  static std::mutex mu;
+  static std::map<std::tuple<int, const void *, int, size_t>, int> cache;
+  static std::map<std::pair<int, const void *>, bool> raised;
+  std::lock_guard<std::mutex> lk(mu);
+  const auto key = std::make_tuple(device, kern, block, smem);
+  auto it = cache.find(key);
+  if (it != cache.end()) {
+    *occ = it->second;
+    return cudaSuccess;
+  }
+  cudaError_t e = cudaSuccess;
+  if (!raised[std::make_pair(device, kern)]) {
+    // the limit covers dynamic memory only: the device's maximum less the
+    // kernel's static shared memory
+    int optin = 0;
+    cudaFuncAttributes fa{};
+    e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, device);
+    if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, kern);
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               optin - (int)fa.sharedSizeBytes);
+    if (e == cudaSuccess) raised[std::make_pair(device, kern)] = true;
+  }
+  if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(occ, kern, block, smem);
+  if (e == cudaSuccess) cache[key] = *occ;
+  return e;
+}
+
 pj_status run_join(Ctx *ctx, Dataset *A, Dataset *B, const int32_t *cand,
                    const int32_t *cand_off, int64_t n_cand, int cand_on_device,
                    int self_join, const pj_join_opts *o, cudaStream_t s, pj_pairs *out) {
@@ -2487,14 +2527,7 @@ pj_status run_join(Ctx *ctx, Dataset *A, Dataset *B, const int32_t *cand,
 
   // events: 0 start, 1 candidates ready, 2 refinement done, 3 end,
   // 4 parity done, 5 front end done (wavefront path, not in graph replays)
-  cudaEvent_t ev[6];
-  for (auto &e : ev) cudaEventCreate(&e);
-  struct EvGuard {
-    cudaEvent_t *e;
-    ~EvGuard() {
-      for (int i = 0; i < 6; ++i) cudaEventDestroy(e[i]);
-    }
-  } eg{ev};
+  cudaEvent_t *ev = cur_exec(ctx)->ev;
   bool phases = false;
   cudaEvent_t e0 = ev[0], e1 = ev[3];
   // the legacy default stream cannot be captured into a graph: order the
@@ -2588,8 +2621,11 @@ pj_status run_join(Ctx *ctx, Dataset *A, Dataset *B, const int32_t *cand,
   const int smem = per_warp * (threads / 32);
   RefineKernel kern = pick_kernel(W, exact);
   RefineKernel kern_tasks = pick_task_kernel(W, exact);
-  PJ_CK(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
-  PJ_CK(cudaFuncSetAttribute(kern_tasks, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+  {
+    int occ_k = 0;
+    PJ_CK(occupancy(ctx->device, (const void *)kern, threads, smem, &occ_k));
+    PJ_CK(occupancy(ctx->device, (const void *)kern_tasks, threads, smem, &occ_k));
+  }
   // spill queues between the refinement passes
   const unsigned int q_cap = 1u << 22;
   uint4 *q1 = (uint4 *)ws_get(ctx, "spill1", sizeof(uint4) * (size_t)q_cap, &st);
@@ -2631,18 +2667,17 @@ pj_status run_join(Ctx *ctx, Dataset *A, Dataset *B, const int32_t *cand,
     cbase = (int2 *)ws_get(ctx, "cand_base", sizeof(int2) * (size_t)std::max<int64_t>(Ccap, 1), &st);
     if (!cbase) return st;
     stream_smem = 4 * stream_smem_per_warp(W);
-    PJ_CK(cudaFuncSetAttribute(ks, cudaFuncAttributeMaxDynamicSharedMemorySize, stream_smem));
     int occ = 0;
-    PJ_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, ks, 128, stream_smem));
+    PJ_CK(occupancy(ctx->device, (const void *)ks, 128, stream_smem, &occ));
     stream_grid = std::max(1, occ) * ctx->num_sms;
   }
   if (front) {
     int occ = 0;
-    PJ_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, pick_wave_expand(W), 256, 0));
+    PJ_CK(occupancy(ctx->device, (const void *)pick_wave_expand(W), 256, 0, &occ));
     wave_grid[0] = std::max(1, occ) * ctx->num_sms;
-    PJ_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, pick_wave_leaf(W, exact), 256, 0));
+    PJ_CK(occupancy(ctx->device, (const void *)pick_wave_leaf(W, exact), 256, 0, &occ));
     wave_grid[1] = std::max(1, occ) * ctx->num_sms;
-    PJ_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, pick_wave_parity(W), 128, 0));
+    PJ_CK(occupancy(ctx->device, (const void *)pick_wave_parity(W), 128, 0, &occ));
     wave_grid[2] = std::max(1, occ) * ctx->num_sms;
     if (!stream) {
       wqa = (uint4 *)ws_get(ctx, "wave_a", sizeof(uint4) * (size_t)wq_cap, &st);
@@ -2697,7 +2732,7 @@ pj_status run_join(Ctx *ctx, Dataset *A, Dataset *B, const int32_t *cand,
   int64_t blocks = 1;
   if (Ccap > 0 && o->launch_mode != PJ_LAUNCH_PER_PAIR) {
     int occ = 0;
-    PJ_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, threads, smem));
+    PJ_CK(occupancy(ctx->device, (const void *)kern, threads, smem, &occ));
     if (occ < 1) return fail(ctx, PJ_ERR_INTERNAL, "refinement kernel does not fit on an SM");
     blocks = std::min<int64_t>((int64_t)occ * ctx->num_sms, (Ccap * k * 32 + threads - 1) / threads);
     blocks = std::max<int64_t>(blocks, 1);
@@ -3145,9 +3180,8 @@ pj_status run_join_noalloc(Ctx *ctx, Dataset *A, Dataset *B, const int32_t *d_ca
   if (per_warp * 4 > 200 * 1024) return fail(ctx, PJ_ERR_INTERNAL, "BVH too deep for the traversal stack");
   const int smem = per_warp * (threads / 32);
   RefineKernel kern = pick_kernel(W, false);
-  PJ_CK(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
   int occ = 0;
-  PJ_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, threads, smem));
+  PJ_CK(occupancy(ctx->device, (const void *)kern, threads, smem, &occ));
   if (occ < 1) return fail(ctx, PJ_ERR_INTERNAL, "refinement kernel does not fit on an SM");
   RefineArgs args;
   args.A = make_side(A, bA);
