@@ -75,6 +75,10 @@ typedef struct {
 } pj_bvh_params;
 
 enum { PJ_LEAF_FILTERED = 0, PJ_LEAF_EXACT = 1 };
+/* pj_segtri_batch only: the FP32 filter with the static bound of the five
+ * points' box (the form the streaming kernel uses, with one bound per leaf
+ * pair) */
+enum { PJ_LEAF_STATIC = 2 };
 enum { PJ_LAUNCH_PERSISTENT = 0, PJ_LAUNCH_PER_PAIR = 1 };
 enum { PJ_FRONT_NONE = -1, PJ_FRONT_STREAM = -2 };  /* pj_join_opts.wave_levels */
 
@@ -416,7 +420,8 @@ pj_status pj_reset_counters(pj_ctx *ctx);
 /* Leaf predicate on explicit segments and triangles (all device pointers,
  * float32 integer-valued coordinates): res[k] = 1 if the open segment
  * (p[k], q[k]) crosses the open triangle (a[k], b[k], c[k]) transversally.
- * pq: n x 6 (p then q), abc: n x 9.  mode: PJ_LEAF_FILTERED or
+ * pq: n x 6 (p then q), abc: n x 9.  mode: PJ_LEAF_FILTERED (per-test
+ * error bound), PJ_LEAF_STATIC (static bound of the points' box) or
  * PJ_LEAF_EXACT.  n_fallback (host, may be NULL) receives how many tests the
  * FP32 filter could not decide. */
 pj_status pj_segtri_batch(pj_ctx *ctx, const float *pq, const float *abc,

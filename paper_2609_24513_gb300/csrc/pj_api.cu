@@ -745,7 +745,8 @@ pj_status pj_segtri_batch(pj_ctx *h, const float *pq, const float *abc, int64_t 
                           int32_t mode, uint8_t *res, int64_t *n_fallback, void *stream) {
   Ctx *ctx = reinterpret_cast<Ctx *>(h);
   if (!ctx || n < 0 || (n > 0 && (!pq || !abc || !res))) return PJ_ERR_INVALID_ARG;
-  if (mode != PJ_LEAF_FILTERED && mode != PJ_LEAF_EXACT) return PJ_ERR_INVALID_ARG;
+  if (mode != PJ_LEAF_FILTERED && mode != PJ_LEAF_EXACT && mode != PJ_LEAF_STATIC)
+    return PJ_ERR_INVALID_ARG;
   std::lock_guard<std::mutex> lk(ctx->mu);
   clear_err(ctx);
   cudaSetDevice(ctx->device);

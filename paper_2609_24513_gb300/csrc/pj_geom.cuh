@@ -230,6 +230,79 @@ __device__ __forceinline__ bool segtri_filtered(F3 p, F3 q, F3 a, F3 b, F3 c, bo
 // relative error below 2^-22.9 and keeps its sign; comparing
 // t_enter <= t_exit * (1 + 2^-20) absorbs it (cf. Ize, "Robust BVH Ray
 // Traversal", JCGT 2013).  A zero direction component is decided exactly.
+// The strict test with a static error bound: every point lies in a box of
+// largest side D, so every difference of two points is at most D per
+// coordinate, every permanent of the triple products at most 6 D^3, and
+// the FP32 error at most 5u * 6 D^3 < 2^-18 D^3 (u = 2^-24); err = 2^-18 D^3
+// (D^3 rounded upward far within the margin) certifies a sign with no
+// per-test permanent.  Otherwise as segtri_filtered: simple exact zeros by
+// comparison, the rest in int64.
+__device__ __forceinline__ int cert_static(float det, float err) {
+  return det > err ? 1 : (det < -err ? -1 : 0);
+}
+__device__ __forceinline__ float dot3(F3 x, F3 m) {
+  return __fadd_rn(__fadd_rn(__fmul_rn(x.x, m.x), __fmul_rn(x.y, m.y)), __fmul_rn(x.z, m.z));
+}
+__device__ __forceinline__ F3 cross3(F3 y, F3 z) {
+  return mkf3(__fsub_rn(__fmul_rn(y.y, z.z), __fmul_rn(y.z, z.y)),
+              __fsub_rn(__fmul_rn(y.z, z.x), __fmul_rn(y.x, z.z)),
+              __fsub_rn(__fmul_rn(y.x, z.y), __fmul_rn(y.y, z.x)));
+}
+__device__ __forceinline__ bool segtri_static(F3 p, F3 q, F3 a, F3 b, F3 c, float err,
+                                             bool *exact) {
+  const F3 A = sub(a, p), B = sub(b, p), C = sub(c, p);
+  const F3 bc = cross3(B, C);
+  int sp = -cert_static(dot3(A, bc), err);
+  if (sp == 0) {
+    if (zero_orient(a, b, c, p)) return false;
+    *exact = true;
+    const I3 pi = toi(p);
+    sp = -sgn64(dot64(isub(toi(a), pi), cross64(isub(toi(b), pi), isub(toi(c), pi))));
+    if (sp == 0) return false;
+  }
+  const F3 Aq = sub(a, q), Bq = sub(b, q), Cq = sub(c, q);
+  int sq = -cert_static(dot3(Aq, cross3(Bq, Cq)), err);
+  if (sq == 0) {
+    if (zero_orient(a, b, c, q)) return false;
+    *exact = true;
+    const I3 qi = toi(q);
+    sq = -sgn64(dot64(isub(toi(a), qi), cross64(isub(toi(b), qi), isub(toi(c), qi))));
+  }
+  if (sq == 0 || sq == sp) return false;
+  const F3 d = sub(q, p);
+  int su = cert_static(dot3(d, cross3(A, B)), err);
+  if (su == 0) {
+    if (zero_orient(p, q, a, b)) return false;
+    *exact = true;
+    const I3 pi = toi(p);
+    su = sgn64(dot64(isub(toi(q), pi), cross64(isub(toi(a), pi), isub(toi(b), pi))));
+    if (su == 0) return false;
+  }
+  int sv = cert_static(dot3(d, bc), err);
+  if (sv == -su) return false;
+  if (sv == 0) {
+    if (zero_orient(p, q, b, c)) return false;
+    *exact = true;
+    const I3 pi = toi(p);
+    sv = sgn64(dot64(isub(toi(q), pi), cross64(isub(toi(b), pi), isub(toi(c), pi))));
+    if (sv != su) return false;
+  }
+  int sw = cert_static(dot3(d, cross3(C, A)), err);
+  if (sw == 0) {
+    if (zero_orient(p, q, c, a)) return false;
+    *exact = true;
+    const I3 pi = toi(p);
+    sw = sgn64(dot64(isub(toi(q), pi), cross64(isub(toi(c), pi), isub(toi(a), pi))));
+  }
+  return sw == su;
+}
+
+// error bound of segtri_static for points in a box of largest side D:
+// 2^-18 D^3, each product rounded upward
+__device__ __forceinline__ float static_err(float D) {
+  return __fmul_ru(__fmul_ru(__fmul_ru(D, D), D), 3.814697265625e-06f /* 2^-18 */);
+}
+
 // ---------------------------------------------------------------------------
 struct Seg {
   F3 p;

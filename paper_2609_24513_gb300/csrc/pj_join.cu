@@ -1673,7 +1673,8 @@ struct StreamCfg {
   // words, test list
   static constexpr int warp_bytes = (SC + LQ) * 16 + kStageF4 * 16 + kStageF4 / 3 * 6 * 4 +
                                     kLeafPairs * 2 * 6 * 4 + kLeafPairs * 3 * 4 +
-                                    kLeafPairs * 16 + kLeafPairs * 4 + kListMax * 2;
+                                    kLeafPairs * 16 + kLeafPairs * 4 + kLeafPairs * 4 +
+                                    kListMax * 2;
 };
 
 // control words of one launch (zeroed before it), each on its own 128-byte
@@ -1757,8 +1758,8 @@ __global__ void __launch_bounds__(128, 4) k_stream(StreamArgs P) {
   float *s_off = s_box + kLeafPairs * 2 * 6;
   uint4 *s_pe = reinterpret_cast<uint4 *>(s_off + kLeafPairs * 3);
   volatile unsigned *s_hit = reinterpret_cast<volatile unsigned *>(s_pe + kLeafPairs);
-  unsigned short *s_list = reinterpret_cast<unsigned short *>(
-      const_cast<unsigned *>(s_hit) + kLeafPairs);
+  float *s_err = reinterpret_cast<float *>(const_cast<unsigned *>(s_hit) + kLeafPairs);
+  unsigned short *s_list = reinterpret_cast<unsigned short *>(s_err + kLeafPairs);
   const WaveArgs &Q = P.w;
   const unsigned lt = (1u << lane) - 1u;
   const int L = 1 << Q.lshift;                    // leaf size
@@ -1874,6 +1875,15 @@ __global__ void __launch_bounds__(128, 4) k_stream(StreamArgs P) {
       }
     }
     __syncwarp();
+    // the pair's static filter bound, from the box around both leaves
+    if (lane < np && !s_hit[lane]) {
+      const float *ba = s_box + 12 * lane, *bb = ba + 6;
+      const float D = fmaxf(fmaxf(fmaxf(ba[3], bb[3]) - fminf(ba[0], bb[0]),
+                                  fmaxf(ba[4], bb[4]) - fminf(ba[1], bb[1])),
+                            fmaxf(ba[5], bb[5]) - fminf(ba[2], bb[2]));
+      s_err[lane] = static_err(D);
+    }
+    __syncwarp();
     // the queued (edge, triangle) tests, one per lane: code = p | dir << 5 |
     // s << 6 | k << 9 | t << 11
     int nlist = 0;
@@ -1898,7 +1908,7 @@ __global__ void __launch_bounds__(128, 4) k_stream(StreamArgs P) {
               r = segtri_exact_staged(pp, qq, a, b, c);
             } else {
               bool ex = false;
-              r = segtri_filtered(pp, qq, a, b, c, &ex);
+              r = segtri_static(pp, qq, a, b, c, s_err[p], &ex);
               lc.fb += ex ? 1 : 0;
             }
             if (r) {
@@ -2371,6 +2381,17 @@ __global__ void k_segtri_batch(const float *pq, const float *abc, int64_t n, int
     bool r;
     if (mode == PJ_LEAF_EXACT) {
       r = segtri_exact_staged(p, q, a, b, c);
+    } else if (mode == PJ_LEAF_STATIC) {
+      bool ex = false;
+      const float D = fmaxf(
+          fmaxf(fmaxf(fmaxf(p.x, q.x), fmaxf(a.x, fmaxf(b.x, c.x))) -
+                    fminf(fminf(p.x, q.x), fminf(a.x, fminf(b.x, c.x))),
+                fmaxf(fmaxf(p.y, q.y), fmaxf(a.y, fmaxf(b.y, c.y))) -
+                    fminf(fminf(p.y, q.y), fminf(a.y, fminf(b.y, c.y)))),
+          fmaxf(fmaxf(p.z, q.z), fmaxf(a.z, fmaxf(b.z, c.z))) -
+              fminf(fminf(p.z, q.z), fminf(a.z, fminf(b.z, c.z))));
+      r = segtri_static(p, q, a, b, c, static_err(D), &ex);
+      fb += ex ? 1 : 0;
     } else {
       bool ex = false;
       r = segtri_filtered(p, q, a, b, c, &ex);

@@ -18,7 +18,7 @@ _lib = None
 
 PJ_OK = 0
 PJ_PENDING = 9
-PJ_LEAF_FILTERED, PJ_LEAF_EXACT = 0, 1
+PJ_LEAF_FILTERED, PJ_LEAF_EXACT, PJ_LEAF_STATIC = 0, 1, 2
 PJ_LAUNCH_PERSISTENT, PJ_LAUNCH_PER_PAIR = 0, 1
 PJ_FRONT_NONE, PJ_FRONT_STREAM = -1, -2   # pj_join_opts.wave_levels
 

@@ -321,11 +321,11 @@ def test_segtri_batch_matches_oracle(ctx):
     exp = np.array([oracle.segtri_strict(*x) for x in P], dtype=np.uint8)
     pq = torch.from_numpy(P[:, :2].reshape(-1, 6).astype(np.float32)).cuda()
     abc = torch.from_numpy(P[:, 2:].reshape(-1, 9).astype(np.float32)).cuda()
-    for mode in (pierce.PJ_LEAF_FILTERED, pierce.PJ_LEAF_EXACT):
+    for mode in (pierce.PJ_LEAF_FILTERED, pierce.PJ_LEAF_STATIC, pierce.PJ_LEAF_EXACT):
         res = torch.zeros(len(P), dtype=torch.uint8, device="cuda")
         nfb = pierce.pj_segtri_batch(ctx.h, pq, abc, res, mode=mode)
         assert np.array_equal(res.cpu().numpy(), exp), mode
-        if mode == pierce.PJ_LEAF_FILTERED:
+        if mode != pierce.PJ_LEAF_EXACT:
             assert 0 < nfb < len(P)
     assert exp.sum() > 100
 
