@@ -55,3 +55,23 @@ def lattice_case_sets():
                 meta.append((na, nb, o))
     return (synth.concat(meshes_a), synth.concat(meshes_b),
             np.array(cand, dtype=np.int32), meta)
+
+
+def sat_overlap(va, ta, vb, tb):
+    """Exact: interiors of two convex polytopes intersect iff no candidate axis
+    (face normals, edge x edge) weakly separates them."""
+    def normals(v, t):
+        a = v[t[:, 0]]
+        return np.cross(v[t[:, 1]] - a, v[t[:, 2]] - a)
+
+    def edges(v, t):
+        e = np.concatenate([v[t[:, 1]] - v[t[:, 0]], v[t[:, 2]] - v[t[:, 1]], v[t[:, 0]] - v[t[:, 2]]])
+        return e
+    axes = [normals(va, ta), normals(vb, tb)]
+    ea, eb = edges(va, ta), edges(vb, tb)
+    axes.append(np.cross(ea[:, None, :], eb[None, :, :]).reshape(-1, 3))
+    ax = np.concatenate(axes)
+    ax = ax[np.any(ax != 0, axis=1)]
+    pa, pb = va @ ax.T, vb @ ax.T
+    sep = (pa.max(axis=0) <= pb.min(axis=0)) | (pb.max(axis=0) <= pa.min(axis=0))
+    return not bool(sep.any())

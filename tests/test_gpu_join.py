@@ -6,6 +6,8 @@ hand-built cases, exhaustive lattice placements, instanced (translated)
 candidates, self joins, and error paths.  The full-size pathology workload is
 in test_gpu_pathology.py.
 """
+import os
+
 import numpy as np
 import pytest
 
@@ -138,6 +140,15 @@ def test_nested_spheres(ctx):
 def test_exhaustive_lattice(ctx):
     A, B, cand, meta = lattice_case_sets()
     exp = oracle.join(A, B, cand, tier=1)
+    # the stored verdicts on the overlapping placements agree with the oracle
+    gold = {}
+    for line in open(os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden",
+                                  "lattice_contacts.txt")):
+        if not line.startswith("#") and line.strip():
+            na, nb, dx, dy, dz, v = line.split()
+            gold[(na, nb, (int(dx), int(dy), int(dz)))] = int(v)
+    keyed = {(na, nb, tuple(int(x) for x in o)): int(exp[k]) for k, (na, nb, o) in enumerate(meta)}
+    assert all(keyed[key] == v for key, v in gold.items()) and len(gold) == 161
     ha, hb = _load(ctx, A, ((4, 4), (2, 1), (8, 8))), _load(ctx, B, ((4, 4), (2, 1), (8, 8)))
     for W, L in ((4, 4), (2, 1), (8, 8)):
         for mode, wave in ((pierce.PJ_LEAF_FILTERED, 0), (pierce.PJ_LEAF_EXACT, -1)):

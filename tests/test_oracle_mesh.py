@@ -9,12 +9,14 @@ separating-axis test over exhaustive lattice placements, and invariants of the
 predicate (swap, translation, axis permutation, reflection, relabelling).
 """
 import itertools
+import os
+import sys
 
 import numpy as np
 import pytest
 
 import oracle
-from cases import HAND, lattice_case_sets
+from cases import HAND, lattice_case_sets, sat_overlap
 from paper_2609_24513_gb300 import synth
 
 QMAX = synth.QMAX
@@ -364,26 +366,6 @@ def test_invariants(tiny, name):
 
 # -- exhaustive lattice placements vs the convex separating-axis test (P4) -------
 
-def _sat_overlap(va, ta, vb, tb):
-    """Exact: interiors of two convex polytopes intersect iff no candidate axis
-    (face normals, edge x edge) weakly separates them."""
-    def normals(v, t):
-        a = v[t[:, 0]]
-        return np.cross(v[t[:, 1]] - a, v[t[:, 2]] - a)
-
-    def edges(v, t):
-        e = np.concatenate([v[t[:, 1]] - v[t[:, 0]], v[t[:, 2]] - v[t[:, 1]], v[t[:, 0]] - v[t[:, 2]]])
-        return e
-    axes = [normals(va, ta), normals(vb, tb)]
-    ea, eb = edges(va, ta), edges(vb, tb)
-    axes.append(np.cross(ea[:, None, :], eb[None, :, :]).reshape(-1, 3))
-    ax = np.concatenate(axes)
-    ax = ax[np.any(ax != 0, axis=1)]
-    pa, pb = va @ ax.T, vb @ ax.T
-    sep = (pa.max(axis=0) <= pb.min(axis=0)) | (pb.max(axis=0) <= pa.min(axis=0))
-    return not bool(sep.any())
-
-
 def test_exhaustive_lattice_vs_sat():
     A, B, cand, meta = lattice_case_sets()
     f1 = oracle.join(A, B, cand, tier=1)
@@ -393,7 +375,7 @@ def test_exhaustive_lattice_vs_sat():
     for k, (i, j) in enumerate(cand):
         va, ta = A.mesh(int(i))
         vb, tb = B.mesh(int(j))
-        sat = _sat_overlap(va.astype(np.int64), ta, vb.astype(np.int64), tb)
+        sat = sat_overlap(va.astype(np.int64), ta, vb.astype(np.int64), tb)
         if f1[k]:
             assert sat, meta[k]                              # soundness, always
         elif sat:
@@ -406,9 +388,32 @@ def test_exhaustive_lattice_vs_sat():
         vb, tb = B.mesh(int(j))
         Ap = synth.concat([(va * 64 - 1000, ta)])
         Bp = synth.concat([(vb * 64 - 1000 + np.array([1, 2, 3], np.float32), tb)])
-        assert _sat_overlap(Ap.xyz.astype(np.int64), ta, Bp.xyz.astype(np.int64), tb)
+        assert sat_overlap(Ap.xyz.astype(np.int64), ta, Bp.xyz.astype(np.int64), tb)
         assert oracle.intersects(Ap, 0, Bp, 0), meta[k]
     # 161 of the 3087 placements overlap; 40 are found and the other 121 are
     # aligned lattice contacts, all of them degenerate by the check above
     n_hit = int(f1.sum())
     assert n_hit == 40 and len(exceptions) == 121
+
+
+def _golden_contacts():
+    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden",
+                        "lattice_contacts.txt")
+    out = []
+    for line in open(path):
+        if line.startswith("#") or not line.strip():
+            continue
+        na, nb, dx, dy, dz, v = line.split()
+        out.append((na, nb, int(dx), int(dy), int(dz), int(v)))
+    return out
+
+
+def test_lattice_contacts_golden():
+    """The stored set of overlapping lattice placements and the strict
+    predicate's verdict on each (written by tests/golden/make_lattice_contacts.py
+    from the oracle and the exact separating-axis test) is reproduced."""
+    sys.path.insert(0, os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden"))
+    import make_lattice_contacts
+    gold = _golden_contacts()
+    assert make_lattice_contacts.rows() == gold
+    assert sum(r[5] for r in gold) == 40 and len(gold) == 161
