@@ -1593,13 +1593,13 @@ __global__ void __launch_bounds__(128, 4) k_refine_tasks(RefineArgs P) {
 // Streaming refinement.  A persistent kernel whose warps each keep a task
 // stack and a leaf-pair queue in shared memory holding the tasks of many
 // candidate pairs at once, so that every traversal round is wide: an expand
-// round copies the nodes of 64 / W (node, node) tasks to shared memory with
-// asynchronous copies issued all at once and tests their child pairs with
-// W / 2 lanes per task; a leaf round does the same with the triangles of up
-// to 16 leaf pairs, filters (edge, triangle) tests by boxes and runs the
-// exact tests that remain one per lane.  A round thus waits for one memory
-// latency however many fetches it makes.  A warp takes 32 new candidates
-// whenever its stack holds less than one round.
+// round copies the nodes of 16 (node, node) tasks (8 at W = 8) to shared
+// memory with asynchronous copies issued all at once and tests their child
+// pairs with 2 lanes per task (4 at W = 8); a leaf round does the same with
+// the triangles of up to 24 leaf pairs (48 / L), filters (edge, triangle)
+// tests by boxes and runs the exact tests that remain one per lane.  A round
+// thus waits for one memory latency however many fetches it makes.  A warp
+// takes 32 new candidates whenever its stack holds less than one round.
 //
 // Load balance.  A few pairs (a nucleus lying along a vessel wall over a
 // large area) cost thousands of times the mean, and a warp that holds one
@@ -1654,7 +1654,7 @@ __device__ __forceinline__ void stage_tri(const float4 *stage, int i, F3 off, F3
 
 // Leaf rounds stage the triangles of up to kLeafPairs leaf pairs (at most
 // 48 / L) in shared memory: kStageF4 float4 = 4.5 KB per warp, which also
-// holds an expand round's nodes (64 / W tasks x 2 nodes x W slots).
+// holds an expand round's nodes (16 or 8 tasks x 2 nodes x W slots, padded).
 constexpr int kLeafPairs = 24;
 constexpr int kStageF4 = 288;
 constexpr int kListMax = 384;  // queued (edge, triangle) tests: 32 units x 3 edges x 4 tests
@@ -1998,7 +1998,7 @@ __global__ void __launch_bounds__(128, 4) k_stream(StreamArgs P) {
   };
 
   for (;;) {
-    if (++iters > (1u << 28)) {  // defensive bound: the work is finite
+    if (++iters > (1u << 24)) {  // defensive bound: a warp needs ~10^3 rounds at most here
       err = DERR_STACK;
       break;
     }
