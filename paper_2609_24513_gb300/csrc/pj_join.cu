@@ -203,6 +203,9 @@ constexpr int MBB_T = 256;
 // One warp per A mesh; lanes sweep the B boxes 32 at a time.  The count pass
 // and the emit pass make the same tests, and the emit pass writes each warp's
 // hits in j order (ballot prefix), so candidates come out sorted by (i, j).
+// B boxes staged in shared memory per tile
+constexpr int MBB_TILE = 1024;
+
 template <bool EMIT>
 __global__ void __launch_bounds__(MBB_T) k_mbb(const float *aabbA, int64_t MA,
                                               const float *aabbB, int64_t MB, int self_join,
@@ -210,29 +213,48 @@ __global__ void __launch_bounds__(MBB_T) k_mbb(const float *aabbA, int64_t MA,
                                               int32_t *cand) {
   pdl_wait();
   pdl_trigger();
-  const int lane = threadIdx.x & 31;
-  const int64_t warps = (int64_t)gridDim.x * (MBB_T / 32);
-  for (int64_t i = blockIdx.x * (int64_t)(MBB_T / 32) + (threadIdx.x >> 5); i < MA; i += warps) {
-    const float *a = aabbA + 6 * i;
-    const float ax0 = a[0], ay0 = a[1], az0 = a[2], ax1 = a[3], ay1 = a[4], az1 = a[5];
-    int64_t cnt = 0, pos = EMIT ? offsets[i] : 0;
-    for (int64_t j0 = self_join ? ((i + 1) & ~31ll) : 0; j0 < MB; j0 += 32) {
-      const int64_t j = j0 + lane;
-      bool ov = false;
-      if (j < MB && (!self_join || j > i)) {
-        const float *b = aabbB + 6 * j;
-        ov = ax0 <= b[3] && b[0] <= ax1 && ay0 <= b[4] && b[1] <= ay1 && az0 <= b[5] && b[2] <= az1;
-      }
-      const unsigned m = __ballot_sync(0xffffffffu, ov);
-      if (EMIT && ov) {
-        const int64_t p = pos + __popc(m & ((1u << lane) - 1u));
-        cand[2 * p] = (int32_t)i;
-        cand[2 * p + 1] = (int32_t)j;
-      }
-      if (EMIT) pos += __popc(m);
-      else cnt += __popc(m);
+  // a tile of B boxes is copied to shared memory once per block (coalesced)
+  // and tested by every warp's A mesh from there
+  __shared__ float sb[MBB_TILE * 6];
+  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+  constexpr int WPB = MBB_T / 32;
+  for (int64_t i0 = blockIdx.x * (int64_t)WPB; i0 < MA; i0 += (int64_t)gridDim.x * WPB) {
+    const int64_t i = i0 + wib;
+    const bool has = i < MA;
+    float ax0 = 0.f, ay0 = 0.f, az0 = 0.f, ax1 = -1.f, ay1 = -1.f, az1 = -1.f;
+    if (has) {
+      const float *a = aabbA + 6 * i;
+      ax0 = a[0], ay0 = a[1], az0 = a[2], ax1 = a[3], ay1 = a[4], az1 = a[5];
     }
-    if (!EMIT && lane == 0) counts[i] = cnt;
+    int64_t cnt = 0, pos = (EMIT && has) ? offsets[i] : 0;
+    // in a self join only j > i counts: tiles below the block's first i are skipped
+    const int64_t jstart = self_join ? ((i0 + 1) / MBB_TILE) * MBB_TILE : 0;
+    for (int64_t t0 = jstart; t0 < MB; t0 += MBB_TILE) {
+      const int n = MB - t0 < MBB_TILE ? (int)(MB - t0) : MBB_TILE;
+      __syncthreads();  // the previous tile is no longer read
+      for (int k = threadIdx.x; k < n * 6; k += MBB_T) sb[k] = aabbB[6 * t0 + k];
+      __syncthreads();
+      if (!has) continue;
+      for (int j0 = 0; j0 < n; j0 += 32) {
+        const int jj = j0 + lane;
+        const int64_t j = t0 + jj;
+        bool ov = false;
+        if (jj < n && (!self_join || j > i)) {
+          const float *bb = sb + 6 * jj;
+          ov = ax0 <= bb[3] && bb[0] <= ax1 && ay0 <= bb[4] && bb[1] <= ay1 && az0 <= bb[5] &&
+               bb[2] <= az1;
+        }
+        const unsigned m = __ballot_sync(0xffffffffu, ov);
+        if (EMIT && ov) {
+          const int64_t p = pos + __popc(m & ((1u << lane) - 1u));
+          cand[2 * p] = (int32_t)i;
+          cand[2 * p + 1] = (int32_t)j;
+        }
+        if (EMIT) pos += __popc(m);
+        else cnt += __popc(m);
+      }
+    }
+    if (!EMIT && has && lane == 0) counts[i] = cnt;
   }
 }
 
