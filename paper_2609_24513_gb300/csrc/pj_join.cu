@@ -1784,7 +1784,8 @@ __global__ void __launch_bounds__(128, 4) k_stream(StreamArgs P) {
   unsigned short *s_list = reinterpret_cast<unsigned short *>(s_err + kLeafPairs);
   const WaveArgs &Q = P.w;
   const unsigned lt = (1u << lane) - 1u;
-  const int L = 1 << Q.lshift;                    // leaf size
+  const int lsh = Q.lshift;
+  const int L = 1 << lsh;                         // leaf size
   const int pmax = min(kLeafPairs, 48 / L);       // leaf pairs per round (<= 32)
   const int upi = L == 8 ? 16 : 32;               // leaf units per filter iteration
   const F3 zero = mkf3(0.f, 0.f, 0.f);
@@ -1832,16 +1833,15 @@ __global__ void __launch_bounds__(128, 4) k_stream(StreamArgs P) {
       pfl = vflags[pe.x];
       po = cand_offset(Q, pe.x);
     }
-    // stage: chunk f = ((p * 2 + side) * L + t) * 3 + k
-    const int nch = np * 2 * L * 3;
-    for (int f = lane; f < nch; f += 32) {
-      const int k = f % 3, r = f / 3;
-      const int t = r % L, ps = r / L, side = ps & 1, p = ps >> 1;
-      const uint4 e = s_pe[p];
-      const int n = (int)((side ? e.w >> 8 : e.w) & 7u) + 1;
-      if (t >= n) continue;
-      const float4 *src = (side ? Q.B.trirec : Q.A.trirec) + 3 * ((int64_t)(side ? e.z : e.y) + t) + k;
-      cp_async16(stage + f, src);
+    // stage: one lane per (pair p, side) copies the leaf's triangle records,
+    // contiguous in the mesh, to float4 ((p * 2 + side) * L + t) * 3 + k
+    for (int ps = lane; ps < 2 * np; ps += 32) {
+      const int side = ps & 1;
+      const uint4 e = s_pe[ps >> 1];
+      const int n3 = 3 * ((int)((side ? e.w >> 8 : e.w) & 7u) + 1);
+      const float4 *src = (side ? Q.B.trirec : Q.A.trirec) + 3 * (int64_t)(side ? e.z : e.y);
+      float4 *dst = stage + 3 * (ps << lsh);
+      for (int c = 0; c < n3; ++c) cp_async16(dst + c, src + c);
     }
     if (lane < np) {
       const bool alive = pfl == 0;
@@ -1856,54 +1856,53 @@ __global__ void __launch_bounds__(128, 4) k_stream(StreamArgs P) {
     }
     cp_async_wait_all();
     __syncwarp();
-    // boxes of the staged triangles, then of the leaves (B's translated by
-    // the pair's offset)
-    for (int i = lane; i < np * 2 * L; i += 32) {
-      const int t = i % L, ps = i / L, side = ps & 1, p = ps >> 1;
-      if (s_hit[p]) continue;
-      const uint4 e = s_pe[p];
-      if (t > (int)((side ? e.w >> 8 : e.w) & 7u)) continue;
-      const F3 o = side ? mkf3(s_off[3 * p], s_off[3 * p + 1], s_off[3 * p + 2]) : zero;
-      F3 a, b, c;
-      int own;
-      stage_tri(stage, i, o, a, b, c, own);
-      float *bp = s_tbox + 6 * i;
-      bp[0] = fminf(a.x, fminf(b.x, c.x));
-      bp[1] = fminf(a.y, fminf(b.y, c.y));
-      bp[2] = fminf(a.z, fminf(b.z, c.z));
-      bp[3] = fmaxf(a.x, fmaxf(b.x, c.x));
-      bp[4] = fmaxf(a.y, fmaxf(b.y, c.y));
-      bp[5] = fmaxf(a.z, fmaxf(b.z, c.z));
-    }
-    __syncwarp();
-    for (int ps = lane; ps < 2 * np; ps += 32) {
-      const int p = ps >> 1, side = ps & 1;
-      if (!s_hit[p]) {
+    // one lane per (pair, side): the boxes of the leaf's staged triangles
+    // (B's translated by the pair's offset) and the leaf's box; the two sides
+    // of a pair sit on adjacent lanes, which combine their leaf boxes into the
+    // pair's static filter bound (from the box around both leaves)
+    for (int ps0 = 0; ps0 < 2 * np; ps0 += 32) {
+      const int ps = ps0 + lane, p = ps >> 1, side = ps & 1;
+      float bx[6] = {3.4e38f, 3.4e38f, 3.4e38f, -3.4e38f, -3.4e38f, -3.4e38f};
+      const bool on = ps < 2 * np && !s_hit[p];  // the same for both sides
+      if (on) {
         const uint4 e = s_pe[p];
         const int n = (int)((side ? e.w >> 8 : e.w) & 7u) + 1;
-        float b[6] = {3.4e38f, 3.4e38f, 3.4e38f, -3.4e38f, -3.4e38f, -3.4e38f};
+        const F3 o = side ? mkf3(s_off[3 * p], s_off[3 * p + 1], s_off[3 * p + 2]) : zero;
         for (int t = 0; t < n; ++t) {
-          const float *tp = s_tbox + 6 * (ps * L + t);
-          b[0] = fminf(b[0], tp[0]);
-          b[1] = fminf(b[1], tp[1]);
-          b[2] = fminf(b[2], tp[2]);
-          b[3] = fmaxf(b[3], tp[3]);
-          b[4] = fmaxf(b[4], tp[4]);
-          b[5] = fmaxf(b[5], tp[5]);
+          const int i = (ps << lsh) + t;
+          F3 a, b, c;
+          int own;
+          stage_tri(stage, i, o, a, b, c, own);
+          const float lx = fminf(a.x, fminf(b.x, c.x)), ly = fminf(a.y, fminf(b.y, c.y));
+          const float lz = fminf(a.z, fminf(b.z, c.z)), hx = fmaxf(a.x, fmaxf(b.x, c.x));
+          const float hy = fmaxf(a.y, fmaxf(b.y, c.y)), hz = fmaxf(a.z, fmaxf(b.z, c.z));
+          float *bp = s_tbox + 6 * i;
+          bp[0] = lx;
+          bp[1] = ly;
+          bp[2] = lz;
+          bp[3] = hx;
+          bp[4] = hy;
+          bp[5] = hz;
+          bx[0] = fminf(bx[0], lx);
+          bx[1] = fminf(bx[1], ly);
+          bx[2] = fminf(bx[2], lz);
+          bx[3] = fmaxf(bx[3], hx);
+          bx[4] = fmaxf(bx[4], hy);
+          bx[5] = fmaxf(bx[5], hz);
         }
         float *bp = s_box + 6 * ps;
 #pragma unroll
-        for (int q = 0; q < 6; ++q) bp[q] = b[q];
+        for (int q = 0; q < 6; ++q) bp[q] = bx[q];
       }
-    }
-    __syncwarp();
-    // the pair's static filter bound, from the box around both leaves
-    if (lane < np && !s_hit[lane]) {
-      const float *ba = s_box + 12 * lane, *bb = ba + 6;
-      const float D = fmaxf(fmaxf(fmaxf(ba[3], bb[3]) - fminf(ba[0], bb[0]),
-                                  fmaxf(ba[4], bb[4]) - fminf(ba[1], bb[1])),
-                            fmaxf(ba[5], bb[5]) - fminf(ba[2], bb[2]));
-      s_err[lane] = static_err(D);
+      float ob[6];
+#pragma unroll
+      for (int q = 0; q < 6; ++q) ob[q] = __shfl_xor_sync(FULL, bx[q], 1);
+      if (on && side == 0) {
+        const float D = fmaxf(fmaxf(fmaxf(bx[3], ob[3]) - fminf(bx[0], ob[0]),
+                                    fmaxf(bx[4], ob[4]) - fminf(bx[1], ob[1])),
+                              fmaxf(bx[5], ob[5]) - fminf(bx[2], ob[2]));
+        s_err[p] = static_err(D);
+      }
     }
     __syncwarp();
     // the queued (edge, triangle) tests, one per lane: code = p | dir << 5 |
@@ -1951,8 +1950,8 @@ __global__ void __launch_bounds__(128, 4) k_stream(StreamArgs P) {
       unsigned mask = 0;  // bit k * L + t: edge k against target triangle t
       int p = 0, dir = 0, si = 0;
       if (u < nu) {
-        si = u % L;
-        const int pd = u / L;
+        si = u & (L - 1);
+        const int pd = u >> lsh;
         dir = pd & 1;
         p = pd >> 1;
         const uint4 e = s_pe[p];
@@ -1968,25 +1967,29 @@ __global__ void __launch_bounds__(128, 4) k_stream(StreamArgs P) {
           const float *tbx = s_tbox + 6 * ((p * 2 + (dir ^ 1)) * L);
           // box filters only (no slab test: its reciprocals cost more here
           // than the exact tests it would save, which run one per lane)
+          // each owned edge's box against the leaf's (bit k of ek), then
+          // against each target triangle's box, read once for all edges
+          F3 elo[3], ehi[3];
+          unsigned ek = 0;
 #pragma unroll
           for (int k = 0; k < 3; ++k) {
+            const F3 pp = v[k], qq = v[k == 2 ? 0 : k + 1];
+            elo[k] = mkf3(fminf(pp.x, qq.x), fminf(pp.y, qq.y), fminf(pp.z, qq.z));
+            ehi[k] = mkf3(fmaxf(pp.x, qq.x), fmaxf(pp.y, qq.y), fmaxf(pp.z, qq.z));
             if (!((own >> k) & 1)) continue;
-            const F3 pp = sel_f3<3>(v, k), qq = sel_f3<3>(v, k == 2 ? 0 : k + 1);
-            const F3 elo = mkf3(fminf(pp.x, qq.x), fminf(pp.y, qq.y), fminf(pp.z, qq.z));
-            const F3 ehi = mkf3(fmaxf(pp.x, qq.x), fmaxf(pp.y, qq.y), fmaxf(pp.z, qq.z));
             lc.slab += 1;
-            // the edge's box against the leaf's, then against each triangle's
-            if (elo.x > thi.x || tlo.x > ehi.x || elo.y > thi.y || tlo.y > ehi.y ||
-                elo.z > thi.z || tlo.z > ehi.z)
-              continue;
+            if (!(elo[k].x > thi.x || tlo.x > ehi[k].x || elo[k].y > thi.y || tlo.y > ehi[k].y ||
+                  elo[k].z > thi.z || tlo.z > ehi[k].z))
+              ek |= 1u << k;
+          }
+          for (int t = 0; ek && t < nt; ++t) {
+            const float *tp = tbx + 6 * t;
+            const float t0 = tp[0], t1 = tp[1], t2 = tp[2], t3 = tp[3], t4 = tp[4], t5 = tp[5];
 #pragma unroll
-            for (int t = 0; t < 8; ++t) {
-              if (t >= nt) break;
-              const float *tp = tbx + 6 * t;
-              if (tp[0] > ehi.x || elo.x > tp[3] || tp[1] > ehi.y || elo.y > tp[4] ||
-                  tp[2] > ehi.z || elo.z > tp[5])
-                continue;
-              mask |= 1u << (k * L + t);
+            for (int k = 0; k < 3; ++k) {
+              if (((ek >> k) & 1) && !(t0 > ehi[k].x || elo[k].x > t3 || t1 > ehi[k].y ||
+                                       elo[k].y > t4 || t2 > ehi[k].z || elo[k].z > t5))
+                mask |= 1u << (k * L + t);
             }
           }
         }
@@ -2001,7 +2004,7 @@ __global__ void __launch_bounds__(128, 4) k_stream(StreamArgs P) {
       while (mask) {
         const int b = __ffs(mask) - 1;
         mask &= mask - 1;
-        const int k = b / L, t = b - k * L;
+        const int k = b >> lsh, t = b & (L - 1);
         s_list[pos++] = (unsigned short)(p | (dir << 5) | (si << 6) | (k << 9) | (t << 11));
       }
       nlist += tot;
@@ -2233,7 +2236,7 @@ __global__ void __launch_bounds__(128, 4) k_stream(StreamArgs P) {
     unsigned tmask = 0, lmask = 0;
     if (live) {
       for (int q = gi, k = 0; q < NA * NB; q += LPT, ++k) {
-        const int a = q / NB, b = q - a * NB;
+        const int a = xb ? (int)((unsigned)q / W) : q, b = xb ? (int)((unsigned)q % W) : 0;
         const float4 a0 = stage[(ti * 2) * Cf::RS + 2 * a], a1 = stage[(ti * 2) * Cf::RS + 2 * a + 1];
         const float4 b0 = stage[(ti * 2 + 1) * Cf::RS + 2 * b];
         const float4 b1 = stage[(ti * 2 + 1) * Cf::RS + 2 * b + 1];
@@ -2269,7 +2272,7 @@ __global__ void __launch_bounds__(128, 4) k_stream(StreamArgs P) {
       const int k = __ffs(bits) - 1;
       bits &= bits - 1;
       const int q = gi + k * LPT;
-      const int a = q / NB, b = q - a * NB;
+      const int a = xb ? (int)((unsigned)q / W) : q, b = xb ? (int)((unsigned)q % W) : 0;
       const float4 a0 = stage[(ti * 2) * Cf::RS + 2 * a], a1 = stage[(ti * 2) * Cf::RS + 2 * a + 1];
       const float4 b0 = stage[(ti * 2 + 1) * Cf::RS + 2 * b];
       const float4 b1 = stage[(ti * 2 + 1) * Cf::RS + 2 * b + 1];
