@@ -2226,33 +2226,53 @@ __global__ void __launch_bounds__(128, 4) k_stream(StreamArgs P) {
     __syncwarp();
     sp -= npop;
     const bool live = act && fl == 0;
-    const int NA = xa ? W : 1, NB = xb ? W : 1;
     if (live && gi == 0) {
       c_np += 1;
       c_bx += node_pair_bytes<W>(xa, xb);
     }
-    // this lane's child pairs q = gi + k LPT, k < W * W / LPT <= 16 (a = q / NB,
-    // b = q % NB); bit k of the masks
+    // this lane's child pairs q = gi + k LPT, k < W * W / LPT <= 16, of the
+    // NA x NB child slots (W for an expanding side, else 1): a = q / NB,
+    // b = q % NB; bit k of the masks.  They are enumerated as (A slot ia,
+    // B slot m) with k = ia * nbl + m, so that each box is read from shared
+    // memory once: the lane's B slots are gi + m LPT (B expands) or the one
+    // slot, its A slots all W (both expand), gi + ia LPT (only A expands) or
+    // the one slot.
+    constexpr int MB = (W + LPT - 1) / LPT;
     unsigned tmask = 0, lmask = 0;
-    if (live) {
-      for (int q = gi, k = 0; q < NA * NB; q += LPT, ++k) {
-        const int a = xb ? (int)((unsigned)q / W) : q, b = xb ? (int)((unsigned)q % W) : 0;
-        const float4 a0 = stage[(ti * 2) * Cf::RS + 2 * a], a1 = stage[(ti * 2) * Cf::RS + 2 * a + 1];
+    if (live && (xa || xb || gi == 0)) {
+      const int nbl = xb ? MB : 1;
+      const int nal = xa ? (xb ? W : MB) : 1;
+      c_bt += (unsigned)(nal * nbl);
+      Box bbx[MB];
+      uint32_t bwd[MB];
+#pragma unroll
+      for (int m = 0; m < MB; ++m) {
+        const int b = xb ? gi + m * LPT : 0;
         const float4 b0 = stage[(ti * 2 + 1) * Cf::RS + 2 * b];
         const float4 b1 = stage[(ti * 2 + 1) * Cf::RS + 2 * b + 1];
-        const uint32_t wa = __float_as_uint(a1.z), wb = __float_as_uint(b1.z);
-        c_bt += 1;
-        if ((xa && wa == kEmpty) || (xb && wb == kEmpty)) continue;
-        Box ba, bb;
+        bwd[m] = __float_as_uint(b1.z);
+        bbx[m].lo = add(mkf3(b0.x, b0.y, b0.z), off);
+        bbx[m].hi = add(mkf3(b0.w, b1.x, b1.y), off);
+      }
+      for (int ia = 0; ia < nal; ++ia) {
+        const int a = xa ? (xb ? ia : gi + ia * LPT) : 0;
+        const float4 a0 = stage[(ti * 2) * Cf::RS + 2 * a], a1 = stage[(ti * 2) * Cf::RS + 2 * a + 1];
+        const uint32_t wa = __float_as_uint(a1.z);
+        if (xa && wa == kEmpty) continue;
+        Box ba;
         ba.lo = mkf3(a0.x, a0.y, a0.z);
         ba.hi = mkf3(a0.w, a1.x, a1.y);
-        bb.lo = add(mkf3(b0.x, b0.y, b0.z), off);
-        bb.hi = add(mkf3(b0.w, b1.x, b1.y), off);
-        if (!overlap(ba, bb)) continue;
         const bool la = xa ? (wa & kLeafBit) != 0 : (t.y & kLeafBit) != 0;
-        const bool lb = xb ? (wb & kLeafBit) != 0 : (t.z & kLeafBit) != 0;
-        if (la && lb) lmask |= 1u << k;
-        else tmask |= 1u << k;
+#pragma unroll
+        for (int m = 0; m < MB; ++m) {
+          if (m >= nbl) break;
+          if (xb && bwd[m] == kEmpty) continue;
+          if (!overlap(ba, bbx[m])) continue;
+          const bool lb = xb ? (bwd[m] & kLeafBit) != 0 : (t.z & kLeafBit) != 0;
+          const int k = ia * nbl + m;
+          if (la && lb) lmask |= 1u << k;
+          else tmask |= 1u << k;
+        }
       }
     }
     // positions of this lane's outputs (task and leaf counts packed)
