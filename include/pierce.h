@@ -158,7 +158,8 @@ typedef struct {
   uint64_t node_pairs;          /* (node, node) traversal steps                 */
   uint64_t box_tests;           /* child-box overlap tests                      */
   uint64_t leaf_pairs;          /* (leaf, leaf) pairs tested                    */
-  uint64_t edge_slab_tests;     /* segment vs leaf-box slab tests               */
+  uint64_t edge_slab_tests;     /* segment vs leaf-box tests (slab tests; in the
+                                   streaming kernel edge-box overlap tests)     */
   uint64_t segtri_tests;        /* strict segment/triangle tests                */
   uint64_t exact_fallbacks;     /* of those, decided by the int64 path          */
   uint64_t parity_rays;         /* +z parity traversals                         */

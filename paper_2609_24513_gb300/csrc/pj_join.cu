@@ -7,12 +7,16 @@
 //     node of the source mesh is a packet of edge segments bounded by the
 //     node's box, so a (source node, target node) step prunes every edge of
 //     the packet against the target subtree at once.  At a (leaf, leaf) step
-//     each owned edge of one leaf is slab-tested against the other leaf's
-//     box and then tested exactly against its triangles, in both
-//     directions.  The first crossing ends the pair (warp vote).
-//   - Alg. 2's parity test (Sec. 3.3) runs for pairs without a crossing, in
-//     both directions (Sec. 3.4: not filtered by crossings, but a crossing
-//     already decides the intersection predicate).
+//     each owned edge of one leaf is tested against the other leaf's box (a
+//     slab test, or in the streaming kernel an overlap test of the edge's
+//     box) and then exactly against its triangles, in both directions.  The
+//     first crossing ends the pair.
+//   - Alg. 2's parity test (Sec. 3.3) runs in both directions (Sec. 3.4: not
+//     filtered by crossings, but a crossing already decides the
+//     intersection predicate).  The streaming (default) and breadth-first
+//     front ends run it first, so that a contained pair skips the traversal;
+//     the per-warp passes run it for the pairs their traversal left without a
+//     crossing.
 //   - Result materialisation (Sec. 3.5) is one flag per candidate followed
 //     by a prefix-sum compaction, so nothing needs deduplication.
 #include <algorithm>
@@ -1813,9 +1817,9 @@ __global__ void __launch_bounds__(128, 4) k_stream(StreamArgs P) {
 
   // one leaf round: the triangles of up to np leaf pairs from the top of the
   // queue are copied to shared memory (cp.async, all at once), each leaf's
-  // box is taken from its triangles, every owned edge is slab-tested against
-  // the other leaf's box and box-tested against its triangles, and the
-  // surviving (edge, triangle) tests run one per lane.
+  // box is taken from its triangles, every owned edge's box is tested against
+  // the other leaf's box and its triangles' boxes, and the surviving (edge,
+  // triangle) tests run one per lane.
   auto leaf_round = [&]() {
     const int np = min(nlq, pmax);
     uint4 pe = make_uint4(0u, 0u, 0u, 0u);
@@ -2360,6 +2364,11 @@ __global__ void k_flag_count(const uint8_t *flags, const int64_t *n_dev, int64_t
   pdl_trigger();
   const int64_t n = *n_dev;
   int64_t base = blockIdx.x * (int64_t)CMP_CHUNK;
+  // the grid covers the candidate capacity; chunks past the count are empty
+  if (base >= n) {
+    if (threadIdx.x == 0) bcount[blockIdx.x] = 0;
+    return;
+  }
   int c = 0;
   for (int k = threadIdx.x; k < CMP_CHUNK; k += CMP_T) {
     int64_t i = base + k;
@@ -2382,6 +2391,7 @@ __global__ void k_flag_emit(const uint8_t *flags, const int64_t *n_dev, const in
   pdl_wait();
   pdl_trigger();
   const int64_t n = *n_dev;
+  if (blockIdx.x * (int64_t)CMP_CHUNK >= n) return;  // an empty chunk (see k_flag_count)
   int64_t base = blockIdx.x * (int64_t)CMP_CHUNK + (int64_t)threadIdx.x * CMP_PER;
   int c = 0;
   uint8_t f[CMP_PER];
