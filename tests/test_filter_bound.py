@@ -1,0 +1,124 @@
+"""The static FP32 filter bound of the streaming kernel's leaf tests, checked
+on the CPU.
+
+The segment/triangle test is exact on the 2^18 grid (the strict reading of
+Sec. 3.2 and the robustness discussion of Sec. 3.6): five orientation signs,
+each the sign of det[a - p; b - p; c - p] for four grid points.  The kernel
+first evaluates each determinant in FP32 and trusts the sign when
+|det_f32| > 2^-18 D^3, where D is the largest side of a box holding all four
+points; otherwise it decides the sign exactly.  The claim behind that bound:
+every difference is at most D per coordinate, each permanent of the triple
+products is at most 6 D^3, and the FP32 evaluation (two rounded products and
+a rounded difference per cross-product component, three rounded products and
+two rounded sums for the dot product, no fused multiply-add) errs by less
+than 30 u D^3 < 2^-18 D^3 with u = 2^-24.
+
+numpy float32 arithmetic rounds every product, sum and difference to nearest
+exactly like the kernel's explicit round-to-nearest intrinsics, so these
+tests reproduce the kernel's FP32 values bit for bit and compare them with the
+exact integer determinant: the error stays below the bound on random,
+near-coplanar and extreme-magnitude inputs, so a certified sign is always the
+exact sign.
+"""
+import numpy as np
+import pytest
+
+QMAX = (1 << 18) - 1
+
+
+def det_f32(p, a, b, c):
+    """FP32 dot3(a - p, cross3(b - p, c - p)), in the kernel's operation order."""
+    f = np.float32
+    A, B, C = (np.asarray(v, f) - np.asarray(p, f) for v in (a, b, c))
+    cx = B[:, 1] * C[:, 2] - B[:, 2] * C[:, 1]
+    cy = B[:, 2] * C[:, 0] - B[:, 0] * C[:, 2]
+    cz = B[:, 0] * C[:, 1] - B[:, 1] * C[:, 0]
+    return (A[:, 0] * cx + A[:, 1] * cy) + A[:, 2] * cz
+
+
+def det_exact(p, a, b, c):
+    """The same determinant in int64 (differences < 2^19, |det| < 2^57)."""
+    A, B, C = (np.asarray(v, np.int64) - np.asarray(p, np.int64) for v in (a, b, c))
+    cx = B[:, 1] * C[:, 2] - B[:, 2] * C[:, 1]
+    cy = B[:, 2] * C[:, 0] - B[:, 0] * C[:, 2]
+    cz = B[:, 0] * C[:, 1] - B[:, 1] * C[:, 0]
+    return A[:, 0] * cx + A[:, 1] * cy + A[:, 2] * cz
+
+
+def check(p, a, b, c, D):
+    """Error below the bound; a certified sign equals the exact sign."""
+    f = det_f32(p, a, b, c).astype(np.float64)
+    e = det_exact(p, a, b, c)
+    bound = (np.asarray(D, np.float64) ** 3) * 2.0 ** -18
+    err = np.abs(f - e.astype(np.float64))
+    # e as float64 is exact to 2^-52 relative; the margin below covers it
+    assert (err <= bound).all(), float((err / bound).max())
+    cert = np.abs(f) > bound
+    assert (np.sign(f[cert]) == np.sign(e[cert])).all()
+    return err / bound, cert
+
+
+def boxed_points(rng, n, D):
+    """n quadruples of grid points inside a box of side D placed on the grid."""
+    D = np.asarray(D, np.int64)
+    x0 = rng.integers(0, QMAX - D + 1, size=(n, 3)) if D.ndim == 0 else \
+        (rng.random((n, 3)) * (QMAX - D + 1)[:, None]).astype(np.int64)
+    Dv = D if D.ndim else np.full(n, int(D))
+    pts = [x0 + (rng.random((n, 3)) * (Dv[:, None] + 1)).astype(np.int64) for _ in range(4)]
+    return pts, Dv
+
+
+@pytest.mark.parametrize("D", [1, 7, 100, 4096, 1 << 15, QMAX])
+def test_static_bound_random(D):
+    rng = np.random.default_rng(7000 + D % 997)
+    (p, a, b, c), Dv = boxed_points(rng, 400_000, D)
+    ratio, _ = check(p, a, b, c, Dv)
+    # the analysis leaves a factor of about 2 (30 u against 64 u)
+    assert ratio.max() < 0.6
+
+
+def test_static_bound_mixed_sizes():
+    rng = np.random.default_rng(7100)
+    n = 1_000_000
+    D = np.exp(rng.uniform(0, np.log(QMAX), size=n)).astype(np.int64).clip(1, QMAX)
+    (p, a, b, c), Dv = boxed_points(rng, n, D)
+    check(p, a, b, c, Dv)
+
+
+def test_static_bound_near_coplanar():
+    """p on the plane of a, b, c (an integer barycentric point) or one grid
+    step off it: exact determinants zero or near zero, where a wrong
+    certified sign would show."""
+    rng = np.random.default_rng(7200)
+    n = 600_000
+    D = np.exp(rng.uniform(np.log(16), np.log(QMAX), size=n)).astype(np.int64)
+    (a, _, _, _), Dv = boxed_points(rng, n, D)
+    a = np.minimum(a, QMAX - D[:, None])                # room for the triangle
+    q = D[:, None] // 4
+    b = a + 4 * (rng.random((n, 3)) * (q + 1)).astype(np.int64)
+    c = a + 4 * (rng.random((n, 3)) * (q + 1)).astype(np.int64)
+    i = rng.integers(0, 5, size=n)
+    j = (rng.random(n) * (5 - i)).astype(np.int64)      # i + j <= 4
+    p = (a * (4 - i - j)[:, None] + b * i[:, None] + c * j[:, None]) // 4
+    off = rng.random(n) < 0.5
+    p[off] += rng.integers(-1, 2, size=(int(off.sum()), 3))
+    lo, hi = np.minimum(np.minimum(a, b), c), np.maximum(np.maximum(a, b), c)
+    p = np.clip(p, lo, hi)                              # inside the box of a, b, c
+    _, cert = check(p, a, b, c, Dv)
+    e = det_exact(p, a, b, c)
+    assert (e == 0).sum() > n // 4   # exact zeros occur and are never certified
+    assert not cert[e == 0].any()
+    assert ((e != 0) & (np.abs(e) < 1000)).sum() > 1000
+
+
+def test_static_bound_extremes():
+    """Box corners: the permanents reach their maximum 6 D^3 order."""
+    rng = np.random.default_rng(7300)
+    n = 200_000
+    D = QMAX
+    corner = lambda: rng.integers(0, 2, size=(n, 3)) * D
+    p, a, b, c = corner(), corner(), corner(), corner()
+    check(p, a, b, c, np.full(n, D))
+    # near-corners, one unit inside
+    jig = lambda v: np.clip(v + rng.integers(-1, 2, size=(n, 3)), 0, QMAX)
+    check(jig(p), jig(a), jig(b), jig(c), np.full(n, D))
