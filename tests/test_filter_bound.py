@@ -45,6 +45,34 @@ def det_exact(p, a, b, c):
     return A[:, 0] * cx + A[:, 1] * cy + A[:, 2] * cz
 
 
+def det_perm_f32(p, a, b, c):
+    """The per-test filter of the other front ends: the FP32 determinant and
+    its error bound 2^-21 x (the permanent, evaluated in FP32), each value
+    rounded to nearest in the kernel's order."""
+    f = np.float32
+    A, B, C = (np.asarray(v, f) - np.asarray(p, f) for v in (a, b, c))
+    p1, p2 = B[:, 1] * C[:, 2], B[:, 2] * C[:, 1]
+    p3, p4 = B[:, 2] * C[:, 0], B[:, 0] * C[:, 2]
+    p5, p6 = B[:, 0] * C[:, 1], B[:, 1] * C[:, 0]
+    m = (p1 - p2, p3 - p4, p5 - p6)
+    pm = (np.abs(p1) + np.abs(p2), np.abs(p3) + np.abs(p4), np.abs(p5) + np.abs(p6))
+    det = (A[:, 0] * m[0] + A[:, 1] * m[1]) + A[:, 2] * m[2]
+    perm = (np.abs(A[:, 0]) * pm[0] + np.abs(A[:, 1]) * pm[1]) + np.abs(A[:, 2]) * pm[2]
+    return det, perm * f(2.0 ** -21)
+
+
+def check_perm(p, a, b, c):
+    """Error below the per-test bound; a certified sign equals the exact sign."""
+    det, err = det_perm_f32(p, a, b, c)
+    e = det_exact(p, a, b, c)
+    assert (det == det_f32(p, a, b, c)).all()   # the same determinant as the static filter
+    gap = np.abs(det.astype(np.float64) - e.astype(np.float64))
+    assert (gap <= err.astype(np.float64)).all()
+    cert = np.abs(det) > err
+    assert (np.sign(det[cert]) == np.sign(e[cert])).all()
+    return cert
+
+
 def check(p, a, b, c, D):
     """Error below the bound; a certified sign equals the exact sign."""
     f = det_f32(p, a, b, c).astype(np.float64)
@@ -122,3 +150,22 @@ def test_static_bound_extremes():
     # near-corners, one unit inside
     jig = lambda v: np.clip(v + rng.integers(-1, 2, size=(n, 3)), 0, QMAX)
     check(jig(p), jig(a), jig(b), jig(c), np.full(n, D))
+
+
+def test_per_test_bound_random_and_near_coplanar():
+    rng = np.random.default_rng(7400)
+    n = 600_000
+    D = np.exp(rng.uniform(0, np.log(QMAX), size=n)).astype(np.int64).clip(1, QMAX)
+    (p, a, b, c), _ = boxed_points(rng, n, D)
+    cert = check_perm(p, a, b, c)
+    assert cert.mean() > 0.9               # random orientations are nearly all certified
+    # near the plane: midpoints and small offsets from it
+    q = D[:, None] // 4
+    a = np.minimum(a, QMAX - D[:, None])
+    b = a + 4 * (rng.random((n, 3)) * (q + 1)).astype(np.int64)
+    c = a + 4 * (rng.random((n, 3)) * (q + 1)).astype(np.int64)
+    p = (2 * a + b + c) // 4 + rng.integers(-1, 2, size=(n, 3))
+    p = np.clip(p, np.minimum(np.minimum(a, b), c), np.maximum(np.maximum(a, b), c))
+    cert = check_perm(p, a, b, c)
+    e = det_exact(p, a, b, c)
+    assert not cert[e == 0].any() and (e == 0).sum() > 1000
