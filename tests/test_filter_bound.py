@@ -1,5 +1,5 @@
-"""The static FP32 filter bound of the streaming kernel's leaf tests, checked
-on the CPU.
+"""The FP32 filter bounds of the leaf tests and the conservative slab test,
+checked on the CPU.
 
 The segment/triangle test is exact on the 2^18 grid (the strict reading of
 Sec. 3.2 and the robustness discussion of Sec. 3.6): five orientation signs,
@@ -169,3 +169,85 @@ def test_per_test_bound_random_and_near_coplanar():
     cert = check_perm(p, a, b, c)
     e = det_exact(p, a, b, c)
     assert not cert[e == 0].any() and (e == 0).sum() > 1000
+
+
+# -- the conservative slab test of the breadth-first and per-warp fronts --------
+
+def slab_hit_f32(p, q, lo, hi):
+    """The kernels' segment/box slab test in FP32, in their operation order:
+    t = (bound - p) * rcp(d) with a correctly rounded reciprocal (numpy's
+    float32 1/d), t_enter <= t_exit * (1 + 2^-20)."""
+    f = np.float32
+    p, q, lo, hi = (np.asarray(v, f) for v in (p, q, lo, hi))
+    d = q - p
+    tmin = np.zeros(len(p), f)
+    tmax = np.ones(len(p), f)
+    big = f(1e30)
+    for k in range(3):
+        z = d[:, k] == 0
+        inv = np.where(z, f(0), f(1) / np.where(z, f(1), d[:, k]))
+        t0 = np.where(z, np.where(p[:, k] >= lo[:, k], -big, big), (lo[:, k] - p[:, k]) * inv)
+        t1 = np.where(z, np.where(p[:, k] <= hi[:, k], big, -big), (hi[:, k] - p[:, k]) * inv)
+        tmin = np.maximum(tmin, np.minimum(t0, t1))
+        tmax = np.minimum(tmax, np.maximum(t0, t1))
+    return tmin <= tmax * f(1.00000095367431640625)
+
+
+def seg_box_exact(p, q, lo, hi):
+    """Whether the closed segment meets the closed box, in exact rationals:
+    t ranges (num / den, den > 0) intersected over the axes and [0, 1]."""
+    p, q, lo, hi = (np.asarray(v, np.int64) for v in (p, q, lo, hi))
+    n = len(p)
+    d = q - p
+    a_num, a_den = np.zeros(n, np.int64), np.ones(n, np.int64)     # t_enter
+    b_num, b_den = np.ones(n, np.int64), np.ones(n, np.int64)      # t_exit
+    ok = np.ones(n, bool)
+    for k in range(3):
+        z = d[:, k] == 0
+        ok &= ~z | ((p[:, k] >= lo[:, k]) & (p[:, k] <= hi[:, k]))
+        s = np.where(d[:, k] < 0, -1, 1)
+        den = np.where(z, 1, np.abs(d[:, k]))
+        n0, n1 = s * (lo[:, k] - p[:, k]), s * (hi[:, k] - p[:, k])
+        e_num, x_num = np.minimum(n0, n1), np.maximum(n0, n1)
+        # t_enter = max(t_enter, e_num / den); t_exit = min(t_exit, x_num / den)
+        later = ~z & (e_num * a_den > a_num * den)
+        a_num, a_den = np.where(later, e_num, a_num), np.where(later, den, a_den)
+        sooner = ~z & (x_num * b_den < b_num * den)
+        b_num, b_den = np.where(sooner, x_num, b_num), np.where(sooner, den, b_den)
+    return ok & (a_num * b_den <= b_num * a_den)
+
+
+def test_slab_never_rejects_a_met_box_random():
+    rng = np.random.default_rng(7500)
+    n = 1_000_000
+    S = np.exp(rng.uniform(0, np.log(QMAX), size=n)).astype(np.int64)[:, None]
+    base = (rng.random((n, 3)) * (QMAX - S)).astype(np.int64)
+    pt = lambda: base + (rng.random((n, 3)) * (S + 1)).astype(np.int64)
+    p, q, u, v = pt(), pt(), pt(), pt()
+    lo, hi = np.minimum(u, v), np.maximum(u, v)
+    met = seg_box_exact(p, q, lo, hi)
+    hit = slab_hit_f32(p, q, lo, hi)
+    assert not (met & ~hit).any()
+    assert 0.05 < met.mean() < 0.95
+
+
+def test_slab_never_rejects_a_touched_box():
+    """Boxes that the segment only touches: a corner, an edge or a face of
+    the box lies on a grid point of the segment."""
+    rng = np.random.default_rng(7600)
+    n = 600_000
+    step = rng.integers(-64, 65, size=(n, 3))
+    step[np.abs(step).sum(axis=1) == 0, 0] = 1
+    m = rng.integers(1, 2000, size=n)
+    span = np.abs(step) * m[:, None]
+    p = (rng.random((n, 3)) * (QMAX - span)).astype(np.int64) + np.where(step < 0, span, 0)
+    q = p + step * m[:, None]
+    j = (rng.random(n) * (m + 1)).astype(np.int64)
+    x = p + step * j[:, None]                          # a grid point on the segment
+    ext = rng.integers(0, 500, size=(n, 3))
+    side = rng.integers(0, 3, size=(n, 3))              # box below, above or around x per axis
+    lo = np.where(side == 0, x - ext, np.where(side == 1, x, x - ext))
+    hi = np.where(side == 0, x, np.where(side == 1, x + ext, x + ext))
+    lo, hi = np.clip(lo, 0, QMAX), np.clip(hi, 0, QMAX)
+    assert seg_box_exact(p, q, lo, hi).all()           # x is in the closed box
+    assert slab_hit_f32(p, q, lo, hi).all()
