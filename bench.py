@@ -175,13 +175,16 @@ def run_reference(args, rank, world):
     A, B = make_workload(args.seed, args.nuclei, args.vessels)
     cand = oracle.mbb_candidates(A, B)
     rng = np.random.default_rng(args.seed)
-    per_step = max(1.0, args.ref_step_s)
+    # each timed step gets an equal share of the run's time budget (at most
+    # --ref-step-s, at least 0.5 s); warm-up steps are short
+    per_step = min(args.ref_step_s, max(0.5, args.ref_total_s / max(1, args.steps)))
     times, counts = [], []
     for step in range(args.warmup + args.steps):
         sel = cand[rng.permutation(len(cand))]
+        limit = per_step if step >= args.warmup else min(per_step, 0.5)
         t0 = time.perf_counter()
         n = 0
-        while n < len(sel) and time.perf_counter() - t0 < per_step:
+        while n < len(sel) and time.perf_counter() - t0 < limit:
             oracle.join(A, B, sel[n:n + 8], tier=2)
             n += len(sel[n:n + 8])
         el = time.perf_counter() - t0
@@ -194,7 +197,7 @@ def run_reference(args, rank, world):
             "ms_per_step": 1000 * sum(times) / len(times), "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "int64", "data": "synthetic",
             "config": {"workload": WORKLOAD, "candidates": int(len(cand)),
-                       "step": "bounded sample of the candidates, %.0f s of oracle work" % per_step},
+                       "step": "bounded sample of the candidates, %.1f s of oracle work" % per_step},
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
                              "sample": "%d candidate pairs per step, uniform random" % int(np.mean(counts))},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -637,6 +640,8 @@ def main():
                          "levels, or none (per-warp passes only)")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--ref-step-s", type=float, default=10.0)
+    ap.add_argument("--ref-total-s", type=float, default=120.0,
+                    help="reference arm: seconds of oracle work over all timed steps")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--nuclei", type=int, default=10000)
