@@ -112,3 +112,23 @@ def test_axis_parity_on_spheres(seed):
     A, _ = synth.tiny_spheres(seed)
     total = sum(_check_mesh(A, k, rng, 25) for k in range(3))
     assert total > 100
+
+
+def test_outside_the_box_parity_is_even():
+    """The containment prefilter: a point outside a closed mesh's closed box
+    has even parity (the ray leaves the box without meeting the surface an
+    odd number of times), so the kernels skip its traversal."""
+    rng = np.random.default_rng(8400)
+    A, _ = synth.tiny_spheres(1002)
+    for k in range(4):
+        tris = _mesh_tris(A, k)
+        V = tris.reshape(-1, 3)
+        lo, hi = V.min(axis=0), V.max(axis=0)
+        pts = rng.integers(lo - 50, hi + 51, size=(400, 3))
+        out = ((pts < lo) | (pts > hi)).any(axis=1)
+        for v in pts[out]:
+            ref, on = oracle.point_query([int(x) for x in v], A, k)
+            assert not on and not ref
+            for ax in range(3):
+                for d in (1, -1):
+                    assert axis_parity(v, tris, ax, d) == 0
