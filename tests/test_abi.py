@@ -86,3 +86,15 @@ def test_no_cpu_fallback_when_library_missing(monkeypatch, tmp_path):
     monkeypatch.setattr(pierce._build, "LIB", str(tmp_path / "missing.so"))
     with pytest.raises(RuntimeError):
         pierce.load()
+
+
+def test_no_cpu_fallback_without_a_gpu():
+    """With the library present but no CUDA device, creating a context fails
+    with PJ_ERR_CUDA: nothing runs on the host instead."""
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    with pytest.raises(pierce.PierceError) as e:
+        pierce.pj_create(0)
+    assert "PJ_ERR_CUDA" in str(e.value)
+    assert pierce.pj_last_error(None) == "null context"
