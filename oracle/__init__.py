@@ -79,6 +79,9 @@ def _load():
     lib.orc_join.restype = ctypes.c_int64
     lib.orc_join.argtypes = [D, D, _i32p, _i32p, ctypes.c_int64, ctypes.c_int32,
                              _u8p, _i64p]
+    lib.orc_join_pred.restype = ctypes.c_int64
+    lib.orc_join_pred.argtypes = [D, D, _i32p, _i32p, ctypes.c_int64, ctypes.c_int32,
+                                  ctypes.c_int32, _u8p, _i64p]
     lib.orc_mbb_candidates.restype = ctypes.c_int64
     lib.orc_mbb_candidates.argtypes = [D, D, ctypes.c_int32, _i32p, ctypes.c_int64]
     lib.orc_is_closed_manifold.restype = ctypes.c_int32
@@ -186,9 +189,18 @@ def inside(dsB, j: int, dsA, i: int) -> bool:
     return bool(_check(_load().orc_inside_pair(b.ref, j, a.ref, i)))
 
 
-def join(dsA, dsB, cand: np.ndarray, tier: int = 2, offsets=None, stats: bool = False):
-    """Refine candidate pairs (n x 2 int32).  Returns uint8 flags[n]
-    (and the counters [segment/triangle tests, parity rays] if stats)."""
+# The paper's join predicates (Sec. 3.2-3.4): intersects = overlap OR
+# containment either way; overlap = a surface crossing; contains = A_i holds
+# B_j with no crossing (Alg. 2); within = the role swap (B_j holds A_i).
+PREDICATES = {"intersects": 0, "overlap": 1, "contains": 2, "within": 3}
+
+
+def join(dsA, dsB, cand: np.ndarray, tier: int = 2, offsets=None, stats: bool = False,
+         predicate: str = "intersects"):
+    """Refine candidate pairs (n x 2 int32) under `predicate` (a key of
+    PREDICATES).  Returns uint8 flags[n] (and the counters [segment/triangle
+    tests, parity rays] if stats)."""
+    pred = PREDICATES[predicate]
     a, b = _DS(dsA), _DS(dsB)
     cand = np.ascontiguousarray(cand, dtype=np.int32).reshape(-1, 2)
     n = cand.shape[0]
@@ -198,8 +210,12 @@ def join(dsA, dsB, cand: np.ndarray, tier: int = 2, offsets=None, stats: bool = 
     if offsets is not None:
         offsets = np.ascontiguousarray(offsets, dtype=np.int32).reshape(-1, 3)
         op = _ptr(offsets, ctypes.c_int32)
-    _check(_load().orc_join(a.ref, b.ref, _ptr(cand, ctypes.c_int32), op, n, tier,
-                            _ptr(flags, ctypes.c_uint8), _ptr(st, ctypes.c_int64)))
+    if pred == 0:
+        _check(_load().orc_join(a.ref, b.ref, _ptr(cand, ctypes.c_int32), op, n, tier,
+                                _ptr(flags, ctypes.c_uint8), _ptr(st, ctypes.c_int64)))
+    else:
+        _check(_load().orc_join_pred(a.ref, b.ref, _ptr(cand, ctypes.c_int32), op, n, tier,
+                                     pred, _ptr(flags, ctypes.c_uint8), _ptr(st, ctypes.c_int64)))
     flags = flags[:n]
     return (flags, st) if stats else flags
 

@@ -22,6 +22,11 @@
  *                 (Alg. 2, Sec. 3.3).  The parity test is not filtered by
  *                 the crossing result (Sec. 3.4).
  *
+ * orc_join_pred also evaluates the paper's other two join predicates:
+ * overlap = cross(A,B) (Sec. 3.2), and containment (Sec. 3.3, Alg. 2):
+ * A contains B iff there is no crossing and inside(B,A); "within" is the
+ * role swap.
+ *
  * Coordinates are integers in [0, 2^18) (stored as float32 by callers), so
  * every orientation determinant is evaluated exactly in 64-bit integers:
  * differences are below 2^18 in magnitude, 2x2 minors below 2^37, a 3x3
@@ -441,6 +446,57 @@ int32_t orc_inside_pair(const orc_dataset *DB, int64_t j,
                         const orc_dataset *DA, int64_t i) {
   /* inside(B_j, A_i): note the argument order (B first) */
   return pair_eval(DA, i, DB, j, NULL, 1, 2, NULL);
+}
+
+/* The paper's three join predicates for one pair (A_i, B_j [+ off]):
+ *   ORC_PRED_INTERSECTS  cross OR inside(B,A) OR inside(A,B)          (Sec. 3.4)
+ *   ORC_PRED_OVERLAP     cross: a surface crossing, bidirectional     (Sec. 3.2)
+ *   ORC_PRED_CONTAINS    A_i contains B_j: no crossing, and B_j's
+ *                        representative vertex inside A_i    (Sec. 3.3, Alg. 2)
+ *   ORC_PRED_WITHIN      A_i within B_j, i.e. B_j contains A_i: the role swap
+ *                        of the containment test                     (Sec. 3.3)
+ * As in Alg. 2 the crossing test runs first and only a pair without a
+ * crossing gets the parity test.  Returns 1/0 or a negative error code. */
+enum { ORC_PRED_INTERSECTS = 0, ORC_PRED_OVERLAP = 1, ORC_PRED_CONTAINS = 2,
+       ORC_PRED_WITHIN = 3 };
+
+static int pair_pred(const orc_dataset *DA, int64_t i, const orc_dataset *DB,
+                     int64_t j, const int32_t *off, int tier, int pred,
+                     int64_t *stats) {
+  if (pred == ORC_PRED_INTERSECTS) return pair_eval(DA, i, DB, j, off, tier, 7, stats);
+  if (pred != ORC_PRED_OVERLAP && pred != ORC_PRED_CONTAINS && pred != ORC_PRED_WITHIN)
+    return ORC_ERR_ARG;
+  mesh_t A, B;
+  int rc = mesh_load(DA, i, NULL, &A);
+  if (rc) return rc;
+  rc = mesh_load(DB, j, off, &B);
+  if (rc) { mesh_free(&A); return rc; }
+  int64_t dummy[2] = {0, 0};
+  if (!stats) stats = dummy;
+  int res = cross_meshes(&A, &B, tier, &stats[0]);
+  if (res >= 0 && pred != ORC_PRED_OVERLAP) {
+    if (res) res = 0;                                   /* a crossing pair */
+    else if (pred == ORC_PRED_CONTAINS) res = inside_meshes(&B, &A, &stats[1]);
+    else res = inside_meshes(&A, &B, &stats[1]);
+  }
+  mesh_free(&A);
+  mesh_free(&B);
+  return res;
+}
+
+/* orc_join with a predicate (ORC_PRED_*): flags[c] for candidate c. */
+int64_t orc_join_pred(const orc_dataset *DA, const orc_dataset *DB,
+                      const int32_t *cand, const int32_t *off, int64_t n,
+                      int32_t tier, int32_t pred, uint8_t *flags, int64_t *stats) {
+  int64_t k = 0;
+  for (int64_t c = 0; c < n; ++c) {
+    int r = pair_pred(DA, cand[2 * c], DB, cand[2 * c + 1], off ? off + 3 * c : NULL,
+                      tier, pred, stats);
+    if (r < 0) return r;
+    flags[c] = (uint8_t)r;
+    k += r;
+  }
+  return k;
 }
 
 /* Representative vertex of B_j with respect to A_i (mesh-local index, or -1). */

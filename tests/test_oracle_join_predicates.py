@@ -1,0 +1,165 @@
+"""Pins of the oracle's overlap, containment and within predicates.
+
+The paper defines three joins on closed meshes (Sec. 3.2-3.4):
+  overlap(A, B)    the surfaces cross (edge piercing, both directions);
+  contains(A, B)   A fully encloses B: no crossing and B inside A (Alg. 2);
+  within(A, B)     the role swap: B encloses A;
+  intersects(A, B) overlap or containment either way.
+These tests fix the values on hand-built solids by reasoning, check the
+identities that follow from the definitions on many generated pairs, a
+closed form for nested spheres, and the paper's argument that one
+representative vertex decides containment of a non-crossing pair (every
+other off-surface vertex of the inner mesh agrees).
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2609_24513_gb300 import synth
+
+from cases import HAND, lattice_case_sets
+
+QMAX = (1 << 18) - 1
+
+# (overlap, contains(A, B), within(A, B)) for A, B = the case's two meshes
+EXPECTED = {
+    "disjoint boxes": (False, False, False),
+    "face to face": (False, False, False),
+    "shared edge": (False, False, False),
+    "shared vertex": (False, False, False),
+    "interpenetrating boxes": (True, False, False),
+    "nested boxes": (False, True, False),
+    "nested boxes sharing a face": (False, True, False),
+    "vertex on a face, outside": (False, False, False),
+    "identical meshes": (False, False, False),
+}
+
+PREDS = ("intersects", "overlap", "contains", "within")
+
+
+def _flags(A, B, cand, tier=2):
+    return {p: oracle.join(A, B, cand, tier=tier, predicate=p).astype(bool) for p in PREDS}
+
+
+@pytest.mark.parametrize("name", sorted(EXPECTED))
+def test_hand_built_predicates(name):
+    ma, mb, inter = HAND[name]
+    A, B = synth.concat([ma]), synth.concat([mb])
+    ov, co, wi = EXPECTED[name]
+    one = np.zeros((1, 2), np.int32)
+    for tier in (1, 2):
+        f = _flags(A, B, one, tier)
+        assert (f["intersects"][0], f["overlap"][0], f["contains"][0], f["within"][0]) == \
+            (inter, ov, co, wi)
+        g = _flags(B, A, one, tier)                     # swapped roles
+        assert (g["overlap"][0], g["contains"][0], g["within"][0]) == (ov, wi, co)
+
+
+def _identities(A, B, cand):
+    f = _flags(A, B, cand)
+    g = _flags(B, A, cand[:, ::-1])
+    assert (f["intersects"] == (f["overlap"] | f["contains"] | f["within"])).all()
+    assert not (f["overlap"] & f["contains"]).any()
+    assert not (f["overlap"] & f["within"]).any()
+    assert not (f["contains"] & f["within"]).any()
+    assert (f["overlap"] == g["overlap"]).all()
+    assert (f["contains"] == g["within"]).all() and (f["within"] == g["contains"]).all()
+    return f
+
+
+def test_identities_on_sphere_pairs():
+    A, B = synth.tiny_spheres(1003)
+    cand = oracle.mbb_candidates(A, B)
+    f = _identities(A, B, cand)
+    assert f["overlap"].sum() > 0
+
+
+def test_identities_and_tiers_on_lattice_placements():
+    A, B, cand, _ = lattice_case_sets()
+    f = _identities(A, B, cand)
+    for p in PREDS[1:]:
+        assert (oracle.join(A, B, cand, tier=1, predicate=p).astype(bool) == f[p]).all()
+
+
+def test_nested_spheres_closed_form():
+    """A small sphere whose circumscribed ball lies inside a big sphere's
+    inscribed ball is contained without crossing; one partly outside the big
+    sphere's circumscribed ball while its centre is inside the inscribed one
+    crosses."""
+    rng = np.random.default_rng(41)
+    n_in = n_cross = 0
+    for _ in range(40):
+        rb, rs = rng.uniform(0.06, 0.1), rng.uniform(0.01, 0.03)
+        u = rng.normal(size=3)
+        u /= np.linalg.norm(u)
+        cb = np.full(3, 0.5)
+        cs = cb + u * rng.uniform(0, rb + rs)
+        meshes, rho, R = [], [], []
+        for c, r, lvl in ((cb, rb, 3), (cs, rs, 2)):
+            v, t = synth._placed_sphere(lvl, c, r, synth.random_rotations(rng, 1)[0])
+            vd, cc = v.astype(np.float64), c * QMAX
+            a = vd[t[:, 0]]
+            nrm = np.cross(vd[t[:, 1]] - a, vd[t[:, 2]] - a)
+            nrm /= np.linalg.norm(nrm, axis=1, keepdims=True)
+            rho.append(np.abs(np.einsum("ij,ij->i", nrm, a - cc)).min())
+            R.append(np.linalg.norm(vd - cc, axis=1).max())
+            meshes.append((v, t))
+        d = np.linalg.norm((cb - cs) * QMAX)
+        A, B = synth.concat([meshes[0]]), synth.concat([meshes[1]])
+        f = _flags(A, B, np.zeros((1, 2), np.int32))
+        if d + R[1] + 2 < rho[0]:
+            assert f["contains"][0] and not f["overlap"][0] and not f["within"][0]
+            n_in += 1
+        elif d + 2 < rho[0] and d + rho[1] > R[0] + 2:
+            assert f["overlap"][0] and not f["contains"][0]
+            n_cross += 1
+    assert n_in > 5 and n_cross > 3
+
+
+def _nested_sphere_set(rng, n):
+    """n (big, small) sphere pairs, the small one at a random offset: nested,
+    crossing or apart; random rotations keep them in general position."""
+    big, small = [], []
+    for _ in range(n):
+        rb, rs = rng.uniform(0.06, 0.1), rng.uniform(0.01, 0.03)
+        u = rng.normal(size=3)
+        cb = np.full(3, 0.5)
+        cs = cb + u / np.linalg.norm(u) * rng.uniform(0, rb + 1.5 * rs)
+        big.append(synth._placed_sphere(2, cb, rb, synth.random_rotations(rng, 1)[0]))
+        small.append(synth._placed_sphere(1, cs, rs, synth.random_rotations(rng, 1)[0]))
+    return synth.concat(big), synth.concat(small)
+
+
+def test_one_representative_vertex_decides_containment():
+    """For a pair whose surfaces do not cross, every vertex of B off A's
+    surface has the same parity with respect to A as the representative vertex
+    (Sec. 3.3).  Placements in general position only: the aligned lattice
+    contacts whose surfaces cross through edges and vertices alone (the strict
+    rule's known blind spot) are crossings, to which the argument does not
+    apply."""
+    rng = np.random.default_rng(43)
+    SA, SB = _nested_sphere_set(rng, 40)
+    TA, TB = synth.tiny_spheres(1001)
+    nested = [(HAND[k][0], HAND[k][1]) for k in ("nested boxes", "nested boxes sharing a face")]
+    HA, HB = synth.concat([m for m, _ in nested]), synth.concat([m for _, m in nested])
+    sets = ((SA, SB, np.stack([np.arange(40), np.arange(40)], 1).astype(np.int32)),
+            (TA, TB, oracle.mbb_candidates(TA, TB)),
+            (HA, HB, np.array([[0, 0], [1, 1]], np.int32)))
+    checked = contained = 0
+    for dA, dB, cc in sets:
+        ov = oracle.join(dA, dB, cc, predicate="overlap").astype(bool)
+        co = oracle.join(dA, dB, cc, predicate="contains").astype(bool)
+        for k in np.nonzero(~ov)[0]:
+            i, j = (int(x) for x in cc[k])
+            vb, _ = dB.mesh(j)
+            par = set()
+            for v in vb.astype(np.int64):
+                p, on = oracle.point_query([int(x) for x in v], dA, i)
+                if not on:
+                    par.add(p)
+            assert len(par) <= 1, (i, j)
+            if par:
+                assert co[k] == par.pop()
+                checked += 1
+                contained += int(co[k])
+    assert checked > 50 and contained > 5
