@@ -10,6 +10,10 @@ A dataset is any object with the attributes ``xyz`` (V x 3 float32, integer
 valued in [0, 2^18)), ``tris`` (F x 3 int32, mesh-local vertex ids), ``voff``
 and ``toff`` (M + 1 int64 offsets).
 
+``oracle.estimate`` (plain numpy) states the paper's selectivity estimate
+(Sec. 3.5); ``join(..., predicate=)`` also evaluates the overlap, containment
+and within joins (Sec. 3.2, 3.3).
+
 Parity status: every function here is pinned by the ``-m "not gpu"`` tests
 (hand-built cases, exact rational re-derivations, closed forms, invariants,
 winding numbers and a convex separating-axis cross-check).
