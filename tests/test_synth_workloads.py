@@ -49,3 +49,27 @@ def test_urban_workload():
         if t[i] == t[j] and t[i] in ("shared_wall", "shared_edge") and abs(int(i) - int(j)) == 1:
             assert not f
     assert 0 < flags.sum() < len(cand)
+
+
+def test_tiers_agree_on_workload_samples():
+    """Oracle self-consistency (pure brute force against the box-pruned tier)
+    on seeded samples of the batching pairs (with their translations) and of
+    the urban self join's candidates, including its exactly touching walls.
+    The pathology meshes (5k-50k triangles) make a brute-force pair cost
+    seconds, so that workload is checked through tier 2 only."""
+    rng = np.random.default_rng(3)
+    A, B, cand, off, cls = synth.batching(3002, n_pairs=400, n_templates=60)
+    fa, fb = np.diff(A.toff), np.diff(B.toff)
+    small = np.nonzero((fa[cand[:, 0]] < 1500) & (fb[cand[:, 1]] < 1500))[0]
+    pick = rng.choice(small, size=min(60, len(small)), replace=False)
+    f1 = oracle.join(A, B, cand[pick], tier=1, offsets=off[pick])
+    f2 = oracle.join(A, B, cand[pick], tier=2, offsets=off[pick])
+    assert (f1 == f2).all() and 0 < f1.sum() < len(pick)
+    U = synth.urban(5002, n_buildings=120, n_parts=12)
+    uc = oracle.mbb_candidates(U, U, self_join=True)
+    fu = np.diff(U.toff)
+    light = np.nonzero((fu[uc[:, 0]] < 800) & (fu[uc[:, 1]] < 800))[0]
+    pick = rng.choice(light, size=min(80, len(light)), replace=False)
+    g1 = oracle.join(U, U, uc[pick], tier=1)
+    g2 = oracle.join(U, U, uc[pick], tier=2)
+    assert (g1 == g2).all()
