@@ -196,7 +196,9 @@ def inside(dsB, j: int, dsA, i: int) -> bool:
 # The paper's join predicates (Sec. 3.2-3.4): intersects = overlap OR
 # containment either way; overlap = a surface crossing; contains = A_i holds
 # B_j with no crossing (Alg. 2); within = the role swap (B_j holds A_i).
-PREDICATES = {"intersects": 0, "overlap": 1, "contains": 2, "within": 3}
+# "any_vertex" adds to intersects any vertex of either mesh strictly inside
+# the other (a completeness mode for crossings through edges and vertices only).
+PREDICATES = {"intersects": 0, "overlap": 1, "contains": 2, "within": 3, "any_vertex": 4}
 
 
 def join(dsA, dsB, cand: np.ndarray, tier: int = 2, offsets=None, stats: bool = False,

@@ -455,17 +455,39 @@ int32_t orc_inside_pair(const orc_dataset *DB, int64_t j,
  *                        representative vertex inside A_i    (Sec. 3.3, Alg. 2)
  *   ORC_PRED_WITHIN      A_i within B_j, i.e. B_j contains A_i: the role swap
  *                        of the containment test                     (Sec. 3.3)
+ *   ORC_PRED_ANY_VERTEX  intersects, or some vertex of either mesh strictly
+ *                        inside the other: a completeness mode for the
+ *                        strict rule's blind spot (surfaces that cross only
+ *                        through edge and vertex coincidences); still sound,
+ *                        since such a vertex is an interior point of the other
+ *                        solid on the boundary of its own
  * As in Alg. 2 the crossing test runs first and only a pair without a
  * crossing gets the parity test.  Returns 1/0 or a negative error code. */
 enum { ORC_PRED_INTERSECTS = 0, ORC_PRED_OVERLAP = 1, ORC_PRED_CONTAINS = 2,
-       ORC_PRED_WITHIN = 3 };
+       ORC_PRED_WITHIN = 3, ORC_PRED_ANY_VERTEX = 4 };
+
+/* Some vertex of B lies strictly inside A (off A's surface, odd parity). */
+static int any_vertex_inside(const mesh_t *B, const mesh_t *A, int64_t *nparity) {
+  for (int64_t k = 0; k < B->nv; ++k) {
+    const int64_t *v = VTX(B, k);
+    if (on_surface(v, A)) continue;
+    ++*nparity;
+    if (parity_up(v, A)) return 1;
+  }
+  return 0;
+}
 
 static int pair_pred(const orc_dataset *DA, int64_t i, const orc_dataset *DB,
                      int64_t j, const int32_t *off, int tier, int pred,
                      int64_t *stats) {
   if (pred == ORC_PRED_INTERSECTS) return pair_eval(DA, i, DB, j, off, tier, 7, stats);
-  if (pred != ORC_PRED_OVERLAP && pred != ORC_PRED_CONTAINS && pred != ORC_PRED_WITHIN)
+  if (pred == ORC_PRED_ANY_VERTEX) {
+    int r = pair_eval(DA, i, DB, j, off, tier, 7, stats);
+    if (r != 0) return r;
+  } else if (pred != ORC_PRED_OVERLAP && pred != ORC_PRED_CONTAINS &&
+             pred != ORC_PRED_WITHIN) {
     return ORC_ERR_ARG;
+  }
   mesh_t A, B;
   int rc = mesh_load(DA, i, NULL, &A);
   if (rc) return rc;
@@ -473,7 +495,15 @@ static int pair_pred(const orc_dataset *DA, int64_t i, const orc_dataset *DB,
   if (rc) { mesh_free(&A); return rc; }
   int64_t dummy[2] = {0, 0};
   if (!stats) stats = dummy;
-  int res = cross_meshes(&A, &B, tier, &stats[0]);
+  int res;
+  if (pred == ORC_PRED_ANY_VERTEX) {
+    res = any_vertex_inside(&B, &A, &stats[1]);
+    if (!res) res = any_vertex_inside(&A, &B, &stats[1]);
+    mesh_free(&A);
+    mesh_free(&B);
+    return res;
+  }
+  res = cross_meshes(&A, &B, tier, &stats[0]);
   if (res >= 0 && pred != ORC_PRED_OVERLAP) {
     if (res) res = 0;                                   /* a crossing pair */
     else if (pred == ORC_PRED_CONTAINS) res = inside_meshes(&B, &A, &stats[1]);

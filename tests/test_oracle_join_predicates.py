@@ -163,3 +163,30 @@ def test_one_representative_vertex_decides_containment():
                 checked += 1
                 contained += int(co[k])
     assert checked > 50 and contained > 5
+
+
+def test_any_vertex_mode_is_sound_and_adds_degenerate_contacts():
+    """The completeness mode (intersects, or a vertex of either mesh strictly
+    inside the other) stays sound against the exact convex separating-axis
+    test, contains every intersecting pair, and recovers some of the aligned
+    lattice contacts that the strict rule misses; on pairs in general position
+    it equals the intersection predicate."""
+    from cases import sat_overlap
+    A, B, cand, _ = lattice_case_sets()
+    fi = oracle.join(A, B, cand, predicate="intersects").astype(bool)
+    fa = oracle.join(A, B, cand, predicate="any_vertex").astype(bool)
+    sat = np.array([sat_overlap(A.mesh(int(i))[0].astype(np.int64), A.mesh(int(i))[1],
+                                B.mesh(int(j))[0].astype(np.int64), B.mesh(int(j))[1])
+                    for i, j in cand])
+    assert not (fa & ~sat).any()                 # sound
+    assert not (fi & ~fa).any()                  # a superset
+    assert (fa & ~fi).sum() > 10                 # recovers degenerate contacts
+    for name in EXPECTED:
+        ma, mb, inter = HAND[name]
+        f = oracle.join(synth.concat([ma]), synth.concat([mb]), np.zeros((1, 2), np.int32),
+                        predicate="any_vertex")
+        assert bool(f[0]) == inter, name
+    TA, TB = synth.tiny_spheres(1002)
+    tc = oracle.mbb_candidates(TA, TB)
+    assert (oracle.join(TA, TB, tc, predicate="any_vertex") ==
+            oracle.join(TA, TB, tc, predicate="intersects")).all()
