@@ -201,27 +201,62 @@ def inside(dsB, j: int, dsA, i: int) -> bool:
 PREDICATES = {"intersects": 0, "overlap": 1, "contains": 2, "within": 3, "any_vertex": 4}
 
 
+def host_cores() -> int:
+    """Host cores this process may run on."""
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:  # not Linux
+        return os.cpu_count() or 1
+
+
 def join(dsA, dsB, cand: np.ndarray, tier: int = 2, offsets=None, stats: bool = False,
-         predicate: str = "intersects"):
+         predicate: str = "intersects", threads: int = 1):
     """Refine candidate pairs (n x 2 int32) under `predicate` (a key of
     PREDICATES).  Returns uint8 flags[n] (and the counters [segment/triangle
-    tests, parity rays] if stats)."""
+    tests, parity rays] if stats).
+
+    threads > 1 (None: every host core) splits the list into contiguous
+    shards that that many threads refine at once; each shard is one plain
+    single-threaded call of the C code on its own slice of the list and of
+    the flags, so the result does not depend on the sharding."""
     pred = PREDICATES[predicate]
     a, b = _DS(dsA), _DS(dsB)
     cand = np.ascontiguousarray(cand, dtype=np.int32).reshape(-1, 2)
     n = cand.shape[0]
     flags = np.zeros(max(n, 1), dtype=np.uint8)
-    st = np.zeros(2, dtype=np.int64)
-    op = None
     if offsets is not None:
         offsets = np.ascontiguousarray(offsets, dtype=np.int32).reshape(-1, 3)
-        op = _ptr(offsets, ctypes.c_int32)
-    if pred == 0:
-        _check(_load().orc_join(a.ref, b.ref, _ptr(cand, ctypes.c_int32), op, n, tier,
-                                _ptr(flags, ctypes.c_uint8), _ptr(st, ctypes.c_int64)))
+        if offsets.shape[0] != n:
+            raise OracleError("one offset per candidate is required")
+    lib = _load()
+
+    def run(lo: int, hi: int) -> np.ndarray:
+        st = np.zeros(2, dtype=np.int64)
+        if hi <= lo:
+            return st
+        cp = _ptr(cand[lo:hi], ctypes.c_int32)
+        op = None if offsets is None else _ptr(offsets[lo:hi], ctypes.c_int32)
+        fp = _ptr(flags[lo:hi], ctypes.c_uint8)
+        sp = _ptr(st, ctypes.c_int64)
+        if pred == 0:
+            _check(lib.orc_join(a.ref, b.ref, cp, op, hi - lo, tier, fp, sp))
+        else:
+            _check(lib.orc_join_pred(a.ref, b.ref, cp, op, hi - lo, tier, pred, fp, sp))
+        return st
+
+    if threads is None:
+        threads = host_cores()
+    threads = max(1, min(int(threads), n))
+    if threads == 1:
+        st = run(0, n)
     else:
-        _check(_load().orc_join_pred(a.ref, b.ref, _ptr(cand, ctypes.c_int32), op, n, tier,
-                                     pred, _ptr(flags, ctypes.c_uint8), _ptr(st, ctypes.c_int64)))
+        # many more shards than threads: pair costs differ by orders of
+        # magnitude, so small shards keep every thread busy to the end
+        import concurrent.futures as cf
+        bounds = np.linspace(0, n, min(n, 32 * threads) + 1).astype(np.int64)
+        with cf.ThreadPoolExecutor(threads) as ex:
+            parts = list(ex.map(run, bounds[:-1].tolist(), bounds[1:].tolist()))
+        st = np.sum(parts, axis=0)
     flags = flags[:n]
     return (flags, st) if stats else flags
 

@@ -52,6 +52,10 @@
  *           the segment, the triangle and both meshes, hence in all of those
  *           boxes, so the restriction cannot drop a crossing.
  * inside() is evaluated the same way in both tiers (all triangles).
+ *
+ * Every exported function is reentrant: a call reads its inputs, allocates its
+ * own meshes and writes only its own outputs, so disjoint candidate lists may
+ * be refined by several threads at once (the Python driver shards that way).
  */
 #include <stdint.h>
 #include <stdlib.h>
@@ -363,7 +367,9 @@ static int parity_up(const int64_t *v, const mesh_t *A) {
   return par;
 }
 
-static const mesh_t *g_sort_mesh; /* qsort has no context argument */
+/* qsort has no context argument; one per thread, so that several threads may
+ * refine disjoint candidate lists at once (every other object is per call) */
+static _Thread_local const mesh_t *g_sort_mesh;
 static int lex_cmp(const void *x, const void *y) {
   const int64_t *p = VTX(g_sort_mesh, *(const int64_t *)x);
   const int64_t *q = VTX(g_sort_mesh, *(const int64_t *)y);
