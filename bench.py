@@ -147,7 +147,9 @@ def profile_traffic(kernel: str, kernel_src: str):
 
 
 def cpu_baseline(A, B, cand, seconds: float, seed: int):
-    """The oracle (tier 2, single-threaded) on a bounded random sample."""
+    """The oracle (tier 2) on bounded random samples: one thread, then the
+    same per-pair code sharded over every host core.  The all-core figure is
+    the line's value; `cores` is the number of threads it used."""
     import oracle
     rng = np.random.default_rng(seed)
     order = rng.permutation(len(cand))
@@ -158,11 +160,21 @@ def cpu_baseline(A, B, cand, seconds: float, seed: int):
         tests += int(st[0])
         done += len(blk)
     el = time.perf_counter() - t0
-    return {"value": done / el, "unit": UNIT, "cores": 1, "kind": "oracle",
+    single = {"value": done / el, "cores": 1, "segtri_tests_per_s": tests / el,
+              "sample": "%d candidate pairs, %.1f s" % (done, el)}
+    # all cores: a disjoint sample of (about) the same wall time
+    cores = oracle.host_cores()
+    n = min(len(order) - done, max(cores, int(single["value"] * cores * seconds)))
+    sel = cand[order[done:done + n]]
+    t0 = time.perf_counter()
+    _, st = oracle.join(A, B, sel, tier=2, stats=True, threads=cores)
+    el_all = time.perf_counter() - t0
+    return {"value": len(sel) / el_all, "unit": UNIT, "cores": cores, "kind": "oracle",
             "sample": "%d of %d candidate pairs drawn uniformly (seed %d), oracle tier 2 "
-                      "(bounding-box-pruned brute force, exact int64), %.1f s"
-                      % (done, len(cand), seed, el),
-            "segtri_tests_per_s": tests / el}
+                      "(bounding-box-pruned brute force, exact int64) sharded over %d threads, "
+                      "%.1f s" % (len(sel), len(cand), seed, cores, el_all),
+            "segtri_tests_per_s": int(st[0]) / el_all,
+            "single_core": single}
 
 
 def run_reference(args, rank, world):
@@ -175,22 +187,29 @@ def run_reference(args, rank, world):
     A, B = make_workload(args.seed, args.nuclei, args.vessels)
     cand = oracle.mbb_candidates(A, B)
     rng = np.random.default_rng(args.seed)
+    cores = oracle.host_cores()
     # each timed step gets an equal share of the run's time budget (at most
-    # --ref-step-s, at least 0.5 s); warm-up steps are short
+    # --ref-step-s, at least 0.5 s): a sample of the candidates sized from
+    # the per-core rate of a short single-threaded calibration, refined by
+    # the same per-pair code sharded over every host core
     per_step = min(args.ref_step_s, max(0.5, args.ref_total_s / max(1, args.steps)))
+    sel = cand[rng.permutation(len(cand))]
+    t0, n = time.perf_counter(), 0
+    while n < len(sel) and time.perf_counter() - t0 < 1.0:
+        oracle.join(A, B, sel[n:n + 8], tier=2)
+        n += len(sel[n:n + 8])
+    rate1 = n / (time.perf_counter() - t0)
     times, counts = [], []
     for step in range(args.warmup + args.steps):
         sel = cand[rng.permutation(len(cand))]
         limit = per_step if step >= args.warmup else min(per_step, 0.5)
+        m = int(min(len(sel), max(cores, rate1 * cores * limit)))
         t0 = time.perf_counter()
-        n = 0
-        while n < len(sel) and time.perf_counter() - t0 < limit:
-            oracle.join(A, B, sel[n:n + 8], tier=2)
-            n += len(sel[n:n + 8])
+        oracle.join(A, B, sel[:m], tier=2, threads=cores)
         el = time.perf_counter() - t0
         if step >= args.warmup:
             times.append(el)
-            counts.append(n)
+            counts.append(m)
     value = sum(counts) / sum(times)
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
             "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
@@ -198,8 +217,9 @@ def run_reference(args, rank, world):
             "scaling": "weak", "vs_baseline": None, "dtype": "int64", "data": "synthetic",
             "config": {"workload": WORKLOAD, "candidates": int(len(cand)),
                        "step": "bounded sample of the candidates, %.1f s of oracle work" % per_step},
-            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
-                             "sample": "%d candidate pairs per step, uniform random" % int(np.mean(counts))},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": "%d candidate pairs per step, uniform random, sharded "
+                                       "over %d threads" % (int(np.mean(counts)), cores)},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 

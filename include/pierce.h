@@ -279,10 +279,10 @@ pj_status pj_free_pairs(pj_ctx *ctx, pj_pairs *res);
 
 /* The join's device part with no allocation at all (the paper has no
  * counterpart: this entry point exists for callers that cannot call
- * cudaMalloc -- code running while a stream is captured into a CUDA graph,
- * loops that must not stall on the allocator's implicit device
+ * cudaMalloc -- loops that must not stall on the allocator's implicit device
  * synchronisation, or programs whose device memory belongs to another
- * allocator or budget).  It calls no cudaMalloc, cudaFree or allocating
+ * allocator or budget, such as a framework's caching allocator or a pool
+ * sized at start-up).  It calls no cudaMalloc, cudaFree or allocating
  * library routine; every buffer is the caller's:
  *   d_cand   device, n_cand x 2 int32 candidates (idA in a, idB in b)
  *   d_flags  device, n_cand bytes: 1 where the candidate intersects
@@ -290,9 +290,11 @@ pj_status pj_free_pairs(pj_ctx *ctx, pj_pairs *res);
  *            in candidate order
  *   d_count  device, one int64: the number of pairs, or -1 if a device-side
  *            check failed (a candidate id out of range)
- * Uses both datasets' last-built BVH (same width and leaf size), the FP32
- * filter with int64 fallback, one warp per pair and plain depth-first
- * traversal.  Asynchronous: the work is enqueued on cuda_stream (NULL: the
+ * Uses each dataset's last-built BVH; the two must have the same width and
+ * leaf size (else PJ_ERR_INVALID_ARG, nothing queued).  Runs the FP32 filter
+ * with int64 fallback, one warp per pair and plain depth-first traversal.
+ * A candidate id out of range is skipped (its flag stays 0) and makes
+ * *d_count -1; the next call clears that state.  Asynchronous: the work is enqueued on cuda_stream (NULL: the
  * context's stream) and the outputs are valid once it has completed.
  * n_cand above 16,777,216 is rejected with PJ_ERR_INVALID_ARG.
  * Scratch: a 65,600-byte array in device global memory, defined at file
@@ -301,7 +303,11 @@ pj_status pj_free_pairs(pj_ctx *ctx, pj_pairs *res);
  * address (make that first call before any stream capture).  All calls on a
  * device share the array, which keeps the last call's contents (each call
  * clears the parts that must start at zero): calls whose work overlaps on
- * the GPU race, so order them on one stream or synchronise between them. */
+ * the GPU race, so order them on one stream or synchronise between them.
+ * Lifetime: the queued work reads both datasets' BVHs, triangles and vertices
+ * until it completes.  pj_free_dataset and pj_destroy wait for the whole
+ * device before they free anything, but the caller must not queue such work
+ * after freeing a dataset it reads. */
 pj_status pj_join_intersects_noalloc(pj_ctx *ctx, pj_dataset a, pj_dataset b,
                                      const int32_t *d_cand, int64_t n_cand,
                                      uint8_t *d_flags, int32_t *d_pairs,

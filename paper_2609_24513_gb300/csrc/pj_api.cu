@@ -495,7 +495,9 @@ pj_status pj_destroy(pj_ctx *h) {
   if (!ctx) return PJ_ERR_INVALID_ARG;
   cudaSetDevice(ctx->device);
   serve_stop(ctx);
-  cudaStreamSynchronize(ctx->stream);
+  // work that reads the datasets may sit on any stream of the device (the
+  // allocation-free join runs on the caller's), so wait for all of it
+  cudaDeviceSynchronize();
   for (auto &kv : ctx->datasets) free_dataset(kv.second.get());
   for (auto &g : ctx->graphs) cudaGraphExecDestroy(g.second);
   exec_free(&ctx->main);
@@ -551,7 +553,10 @@ pj_status pj_free_dataset(pj_ctx *h, pj_dataset id) {
   if (serve_uses(ctx, d))
     return fail(ctx, PJ_ERR_BUSY, "serving queries on this dataset have not been polled yet");
   cudaSetDevice(ctx->device);
-  cudaStreamSynchronize(ctx->stream);
+  // joins that read this dataset may still run on a caller's stream (the
+  // allocation-free join returns once its work is queued): wait for the
+  // whole device, not only the context's stream
+  cudaDeviceSynchronize();
   free_dataset(d);
   ctx->datasets.erase(id);
   for (auto &g : ctx->graphs) cudaGraphExecDestroy(g.second);

@@ -3164,10 +3164,10 @@ pj_status run_join(Ctx *ctx, Dataset *A, Dataset *B, const int32_t *cand,
 // ---------------------------------------------------------------------------
 // Join without allocation (pj_join_intersects_noalloc)
 //
-// For callers that cannot call cudaMalloc: code that runs while a stream is
-// being captured into a CUDA graph, real-time loops that must not block on
-// the allocator's implicit device synchronisation, and hosts whose device
-// memory is owned by another allocator or budget.  The caller passes device
+// For callers that cannot call cudaMalloc: real-time loops that must not
+// block on the allocator's implicit device synchronisation, and hosts whose
+// device memory is owned by another allocator or budget (a framework's
+// caching allocator, a pool sized at start-up).  The caller passes device
 // buffers for the candidates, the per-candidate flags, the pairs and the
 // count; the little scratch the kernels need (candidate count, work counter,
 // error words, per-chunk counts and offsets of the compaction) lives in one
@@ -3234,9 +3234,13 @@ pj_status run_join_noalloc(Ctx *ctx, Dataset *A, Dataset *B, const int32_t *d_ca
                 "n_cand must be in [0, 16777216] for the allocation-free join");
   if (!d_count || (n > 0 && (!d_cand || !d_flags || !d_pairs)))
     return fail(ctx, PJ_ERR_INVALID_ARG, "null device buffer");
-  auto ia = A->bvhs.find(A->last_bvh), ib = B->bvhs.find(A->last_bvh);
+  // each dataset's own last-built BVH; the two must have one shape
+  if (A->last_bvh != B->last_bvh)
+    return fail(ctx, PJ_ERR_INVALID_ARG,
+                "the two datasets' last-built BVHs differ in width or leaf size (pj_build_bvh)");
+  auto ia = A->bvhs.find(A->last_bvh), ib = B->bvhs.find(B->last_bvh);
   if (ia == A->bvhs.end() || ib == B->bvhs.end())
-    return fail(ctx, PJ_ERR_INVALID_ARG, "both datasets need a BVH of the same shape (pj_build_bvh)");
+    return fail(ctx, PJ_ERR_INVALID_ARG, "both datasets need a BVH (pj_build_bvh)");
   Bvh &bA = ia->second, &bB = ib->second;
   const int W = A->last_bvh.first;
   int64_t *scr = nullptr;

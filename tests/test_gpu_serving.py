@@ -3,9 +3,10 @@
 A window query's answer is the set of intersecting pairs among the meshes
 whose closed boxes meet the window.  It must not depend on how the query was
 scheduled: alone, batched with many others, split into several batches by a
-small admission budget, or submitted from several threads at once.  The small
-case is checked against the oracle; the larger one against the regular join
-restricted to the window.
+small admission budget, or submitted from several threads at once.  Every
+answer is checked against the oracle: on the full pathology workload the
+oracle's verdict on all of its bounding-box candidates, restricted to the
+window, is the expected answer.
 """
 import threading
 
@@ -66,20 +67,22 @@ def test_small_case_matches_oracle_alone_and_mixed():
 
 
 @pytest.fixture(scope="module")
-def pathology_small():
-    A, B = synth.pathology(4201, n_nuclei=3000, n_vessels=120)
+def pathology_served(pathology_truth):
+    """The full pathology datasets resident with cached BVHs, and the
+    oracle's pair set over all of their candidates."""
+    A, B, cand, flags = pathology_truth
     ctx = pierce.Context(0, serve_streams=4)
     ha, hb = ctx.load(A), ctx.load(B)
     ctx.build(ha, 4, 4)
     ctx.build(hb, 4, 4)
-    full, _ = ctx.join(ha, hb)
+    full = cand[flags.astype(bool)]
     bA, bB = synth.mesh_boxes(A), synth.mesh_boxes(B)
     yield A, B, ctx, ha, hb, full, bA, bB
     ctx.close()
 
 
-def test_alone_equals_mixed_on_pathology(pathology_small):
-    A, B, ctx, ha, hb, full, bA, bB = pathology_small
+def test_alone_equals_mixed_on_pathology(pathology_served):
+    A, B, ctx, ha, hb, full, bA, bB = pathology_served
     lo, hi = synth.serving_windows(4202, 96)
     alone = _alone(ctx, ha, hb, lo, hi)
     mixed = _mixed(ctx, ha, hb, lo, hi)
@@ -94,8 +97,8 @@ def test_alone_equals_mixed_on_pathology(pathology_small):
     assert sum(len(a[0]) for a in alone) > 50
 
 
-def test_small_budget_splits_batches_and_keeps_answers(pathology_small):
-    A, B, _, _, _, full, bA, bB = pathology_small
+def test_small_budget_splits_batches_and_keeps_answers(pathology_served):
+    A, B, _, _, _, full, bA, bB = pathology_served
     lo, hi = synth.serving_windows(4203, 40, frac_range=(1e-3, 0.05))
     with pierce.Context(0, serve_streams=2) as probe:
         pa, pb = probe.load(A), probe.load(B)
@@ -122,8 +125,8 @@ def test_small_budget_splits_batches_and_keeps_answers(pathology_small):
     assert len(per_batch) > 1
 
 
-def test_threads_submit_and_poll_concurrently(pathology_small):
-    A, B, ctx, ha, hb, full, bA, bB = pathology_small
+def test_threads_submit_and_poll_concurrently(pathology_served):
+    A, B, ctx, ha, hb, full, bA, bB = pathology_served
     lo, hi = synth.serving_windows(4204, 64)
     results = {}
     errors = []
