@@ -113,11 +113,14 @@ typedef struct {
   int32_t kernel_times;     /* 1: also time the front end's launches with CUDA
                                events (pj_pairs.expand_ms / leaf_ms; events
                                between launches cost a little overlap)       */
-  int32_t wait_polls;       /* streaming kernel: bound on the polls of each of
-                               its waits (0: 2^19, about half a second); a
-                               wait that runs out sets an error word and the
-                               join is redone by plain depth-first traversal
-                               (same result, slower)                        */
+  int32_t wait_polls;       /* bound on the polls of each wait of the
+                               streaming kernel (0: 2^19, about half a
+                               second) and of the single-pass box join and
+                               compaction (0: 2^20); a wait that runs out
+                               sets an error word and the join is redone by
+                               plain depth-first traversal with the
+                               multi-pass box join and compaction (same
+                               result, slower)                              */
 } pj_join_opts;
 
 /* Result of a join.  Owned by the library until pj_free_pairs. */
@@ -168,8 +171,8 @@ typedef struct {
   uint64_t bytes_fetched;       /* algorithmic bytes: nodes, triangles, vertices */
   uint64_t pairs_hit;           /* pairs found intersecting                     */
   uint64_t kernel_launches;     /* kernels launched by joins (host count)       */
-  uint64_t tasks_spilled;       /* traversal tasks handed to a later pass        */
-  uint64_t tasks_resumed;       /* spilled tasks taken up by a later pass        */
+  uint64_t tasks_spilled;       /* traversal tasks (streaming: and leaf pairs) handed to another warp or pass */
+  uint64_t tasks_resumed;       /* of those, taken up by another warp or pass    */
   uint64_t bytes_tasks;         /* of bytes_fetched: the per-warp passes        */
   uint64_t bytes_parity;        /* of bytes_fetched: the parity rays            */
   uint64_t bytes_expand;        /* of bytes_fetched: breadth-first node pairs   */

@@ -248,8 +248,8 @@ __device__ __forceinline__ F3 cross3(F3 y, F3 z) {
               __fsub_rn(__fmul_rn(y.z, z.x), __fmul_rn(y.x, z.z)),
               __fsub_rn(__fmul_rn(y.x, z.y), __fmul_rn(y.y, z.x)));
 }
-__device__ __forceinline__ bool segtri_static(F3 p, F3 q, F3 a, F3 b, F3 c, float err,
-                                             bool *exact) {
+__device__ __forceinline__ bool segtri_static_staged(F3 p, F3 q, F3 a, F3 b, F3 c, float err,
+                                                    bool *exact) {
   const F3 A = sub(a, p), B = sub(b, p), C = sub(c, p);
   const F3 bc = cross3(B, C);
   int sp = -cert_static(dot3(A, bc), err);
@@ -295,6 +295,30 @@ __device__ __forceinline__ bool segtri_static(F3 p, F3 q, F3 a, F3 b, F3 c, floa
     sw = sgn64(dot64(isub(toi(q), pi), cross64(isub(toi(c), pi), isub(toi(a), pi))));
   }
   return sw == su;
+}
+
+// The same test with the five FP32 orientations evaluated together as
+// independent chains (no early exit between them, so their latencies
+// overlap).  Their certified signs settle the answer when the plane does not
+// separate p and q, when two of u, v, w have opposite signs, or when all five
+// are certified; any other pattern (some sign uncertain) goes through the
+// staged test above, which decides the uncertain signs exactly.
+__device__ __forceinline__ bool segtri_static(F3 p, F3 q, F3 a, F3 b, F3 c, float err,
+                                             bool *exact) {
+  const F3 A = sub(a, p), B = sub(b, p), C = sub(c, p);
+  const F3 Aq = sub(a, q), Bq = sub(b, q), Cq = sub(c, q);
+  const F3 d = sub(q, p);
+  const F3 bc = cross3(B, C);
+  const int sp = -cert_static(dot3(A, bc), err);
+  const int sq = -cert_static(dot3(Aq, cross3(Bq, Cq)), err);
+  const int su = cert_static(dot3(d, cross3(A, B)), err);
+  const int sv = cert_static(dot3(d, bc), err);
+  const int sw = cert_static(dot3(d, cross3(C, A)), err);
+  if (sp != 0 && sp == sq) return false;                   // p, q on one side
+  if (su * sv < 0 || sv * sw < 0 || su * sw < 0) return false;  // u, v, w disagree
+  if (sp != 0 && sq != 0 && su != 0 && sv != 0 && sw != 0)
+    return true;                                           // sp != sq, u = v = w
+  return segtri_static_staged(p, q, a, b, c, err, exact);
 }
 
 // error bound of segtri_static for points in a box of largest side D:

@@ -162,10 +162,13 @@ pj_status run_autotune(Ctx *ctx, Dataset *A, Dataset *B, const int32_t *cand, in
                        int self_join, const pj_tune_space *space, pj_join_opts *best,
                        pj_tune_entry *table, int table_cap, int *table_n);
 // join.cu
+// safe: plain depth-first refinement and the multi-pass box join and
+// compaction (no kernel waits on another block); the join redoes itself this
+// way when a bounded wait of the default kernels ran out
 pj_status run_join(Ctx *ctx, Dataset *A, Dataset *B, const int32_t *cand,
                    const int32_t *cand_off, int64_t n_cand, int cand_on_device,
                    int self_join, const pj_join_opts *opts, cudaStream_t s,
-                   pj_pairs *out);
+                   pj_pairs *out, bool safe = false);
 pj_status run_join_noalloc(Ctx *ctx, Dataset *A, Dataset *B, const int32_t *d_cand,
                            int64_t n, uint8_t *d_flags, int32_t *d_pairs, int64_t *d_count,
                            cudaStream_t s);

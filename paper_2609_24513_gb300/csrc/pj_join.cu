@@ -1732,15 +1732,21 @@ __device__ __forceinline__ unsigned ld_vol(const unsigned *p) {
   return *reinterpret_cast<volatile const unsigned *>(p);
 }
 
-// give stk[0, n) to the queue (all lanes; n > 0); false if it is full
-__device__ __forceinline__ bool queue_push(const StreamArgs &P, const uint4 *stk, int n,
-                                           int lane) {
+// A queue entry's ready word: 1 for a traversal task (candidate, item A,
+// item B); kLeafEntry | the leaf-queue counts word for a leaf pair
+// (candidate, first triangle of A's leaf, first triangle of B's leaf).
+constexpr unsigned kLeafEntry = 0x80000000u;
+
+// give src[0, n) to the queue (all lanes; n > 0), tasks or (leaves) leaf
+// pairs; false if it is full
+__device__ __forceinline__ bool queue_push(const StreamArgs &P, const uint4 *src, int n,
+                                           int lane, bool leaves) {
   unsigned base = 0;
   if (lane == 0) base = atomicAdd(sq(P, SQ_TAIL), (unsigned)n);
   base = __shfl_sync(FULL, base, 0);
   if ((uint64_t)base + (uint64_t)n > (uint64_t)P.dq_cap) return false;
   for (int k = lane; k < n; k += 32) {
-    const uint4 v = stk[k];
+    const uint4 v = src[k];
     uint4 *d = P.dq + base + k;
     d->x = v.x;
     d->y = v.y;
@@ -1748,7 +1754,8 @@ __device__ __forceinline__ bool queue_push(const StreamArgs &P, const uint4 *stk
   }
   __threadfence();
   for (int k = lane; k < n; k += 32)
-    *reinterpret_cast<volatile unsigned *>(&P.dq[base + k].w) = 1u;
+    *reinterpret_cast<volatile unsigned *>(&P.dq[base + k].w) =
+        leaves ? (kLeafEntry | src[k].w) : 1u;
   // no fence needed before publishing: a consumer waits for each slot's
   // ready flag, which may become visible after the count
   __syncwarp();
@@ -1837,15 +1844,22 @@ __global__ void __launch_bounds__(128, 4) k_stream(StreamArgs P) {
       pfl = vflags[pe.x];
       po = cand_offset(Q, pe.x);
     }
-    // stage: one lane per (pair p, side) copies the leaf's triangle records,
-    // contiguous in the mesh, to float4 ((p * 2 + side) * L + t) * 3 + k
-    for (int ps = lane; ps < 2 * np; ps += 32) {
-      const int side = ps & 1;
-      const uint4 e = s_pe[ps >> 1];
-      const int n3 = 3 * ((int)((side ? e.w >> 8 : e.w) & 7u) + 1);
-      const float4 *src = (side ? Q.B.trirec : Q.A.trirec) + 3 * (int64_t)(side ? e.z : e.y);
-      float4 *dst = stage + 3 * (ps << lsh);
-      for (int c = 0; c < n3; ++c) cp_async16(dst + c, src + c);
+    // stage: the triangle records of each (pair p, side), contiguous in the
+    // mesh, go to float4 ((p * 2 + side) * L + t) * 3 + k.  A (pair, side)
+    // owns 4 L lanes of an iteration (at least its 3 L float4): lane h of
+    // them copies float4 h, so that the lanes of one run read consecutive
+    // addresses (one coalesced request per run instead of a lane copying it
+    // piece by piece).
+    {
+      const int chs = lsh + 2, h = lane & ((1 << chs) - 1);
+      for (int ps = lane >> chs; ps < 2 * np; ps += 32 >> chs) {
+        const int side = ps & 1;
+        const uint4 e = s_pe[ps >> 1];
+        const int n3 = 3 * ((int)((side ? e.w >> 8 : e.w) & 7u) + 1);
+        if (h < n3)
+          cp_async16(stage + 3 * (ps << lsh) + h,
+                     (side ? Q.B.trirec : Q.A.trirec) + 3 * (int64_t)(side ? e.z : e.y) + h);
+      }
     }
     if (lane < np) {
       const bool alive = pfl == 0;
@@ -1919,12 +1933,15 @@ __global__ void __launch_bounds__(128, 4) k_stream(StreamArgs P) {
           const unsigned code = s_list[i];
           const int p = code & 31, dir = (code >> 5) & 1, si = (code >> 6) & 7;
           const int k = (code >> 9) & 3, t = (code >> 11) & 7;
+          // every shared-memory read of the test is issued at once, before
+          // the pair's hit word decides whether to run it
+          const F3 o = mkf3(s_off[3 * p], s_off[3 * p + 1], s_off[3 * p + 2]);
+          F3 v0, v1, v2, a, b, c;
+          int own, town;
+          stage_tri(stage, (p * 2 + dir) * L + si, dir ? o : zero, v0, v1, v2, own);
+          stage_tri(stage, (p * 2 + (dir ^ 1)) * L + t, dir ? zero : o, a, b, c, town);
+          const float err_p = s_err[p];
           if (!s_hit[p]) {
-            const F3 o = mkf3(s_off[3 * p], s_off[3 * p + 1], s_off[3 * p + 2]);
-            F3 v0, v1, v2, a, b, c;
-            int own, town;
-            stage_tri(stage, (p * 2 + dir) * L + si, dir ? o : zero, v0, v1, v2, own);
-            stage_tri(stage, (p * 2 + (dir ^ 1)) * L + t, dir ? zero : o, a, b, c, town);
             const F3 pp = k == 0 ? v0 : (k == 1 ? v1 : v2);
             const F3 qq = k == 0 ? v1 : (k == 1 ? v2 : v0);
             lc.st += 1;
@@ -1933,7 +1950,7 @@ __global__ void __launch_bounds__(128, 4) k_stream(StreamArgs P) {
               r = segtri_exact_staged(pp, qq, a, b, c);
             } else {
               bool ex = false;
-              r = segtri_static(pp, qq, a, b, c, s_err[p], &ex);
+              r = segtri_static(pp, qq, a, b, c, err_p, &ex);
               lc.fb += ex ? 1 : 0;
             }
             if (r) {
@@ -2017,12 +2034,60 @@ __global__ void __launch_bounds__(128, 4) k_stream(StreamArgs P) {
     flush();
   };
 
+  // take the k claimed queue entries at position h (their producers may
+  // still be writing them): tasks onto the stack, leaf pairs onto the leaf
+  // queue, those of candidates found intersecting dropped; false if a
+  // bounded wait ran out (k <= 32; the caller checked the room)
+  auto take = [&](int64_t h, int k) -> bool {
+    bool tpush = false, lpush = false, late = false;
+    uint4 ent = make_uint4(0u, 0u, 0u, 0u);
+    if (lane < k) {
+      volatile unsigned *rdy = reinterpret_cast<volatile unsigned *>(&P.dq[h + lane].w);
+      unsigned it = 0;
+      unsigned w = 0;
+      while ((w = *rdy) == 0u) {
+        if (++it >= P.spin_limit) {
+          late = true;
+          break;
+        }
+        __nanosleep(64);
+      }
+      if (!late) {
+        __threadfence();
+        ent = __ldcg(P.dq + h + lane);
+        *rdy = 0u;
+        const bool alive = vflags[ent.x] == 0;
+        lpush = alive && (w & kLeafEntry);
+        tpush = alive && !(w & kLeafEntry);
+        ent.w = lpush ? (w & ~kLeafEntry) : 0u;
+      }
+    }
+    if (__any_sync(FULL, late)) return false;
+    c_res += lane == 0 ? (unsigned)k : 0u;
+    const unsigned mt = __ballot_sync(FULL, tpush), ml = __ballot_sync(FULL, lpush);
+    if (tpush) stk[sp + __popc(mt & lt)] = ent;
+    if (lpush) lq[nlq + __popc(ml & lt)] = ent;
+    sp += __popc(mt);
+    nlq += __popc(ml);
+    __syncwarp();
+    return true;
+  };
+
   // give the older half of the stack to the queue
   auto give_half = [&](int n) -> bool {
-    if (!queue_push(P, stk, n, lane)) return false;
+    if (!queue_push(P, stk, n, lane, false)) return false;
     c_sp += lane == 0 ? (unsigned)n : 0u;
     stack_drop_bottom(stk, n, sp, lane);
     sp -= n;
+    return true;
+  };
+  // give the older leaf pairs of the leaf queue: leaf rounds are the costly
+  // part of a heavy candidate, so its leaf pairs spread like its tasks
+  auto give_leaves = [&](int n) -> bool {
+    if (!queue_push(P, lq, n, lane, true)) return false;
+    c_sp += lane == 0 ? (unsigned)n : 0u;
+    stack_drop_bottom(lq, n, nlq, lane);
+    nlq -= n;
     return true;
   };
 
@@ -2139,42 +2204,24 @@ __global__ void __launch_bounds__(128, 4) k_stream(StreamArgs P) {
       registered = h >= 0;
       if (h < 0) break;
       t_new = clock64();
-      // take the claimed entries (their producers may still be writing them)
-      bool tpush = false;
-      uint4 ent = make_uint4(0u, 0u, 0u, 0u);
-      bool late = false;
-      if (lane < k) {
-        volatile unsigned *rdy = reinterpret_cast<volatile unsigned *>(&P.dq[h + lane].w);
-        unsigned it = 0;
-        while (*rdy == 0u) {
-          if (++it >= P.spin_limit) {
-            late = true;
-            break;
-          }
-          __nanosleep(64);
-        }
-        if (!late) {
-          __threadfence();
-          ent = __ldcg(P.dq + h + lane);
-          *rdy = 0u;
-          tpush = vflags[ent.x] == 0;  // (a leaf pair goes to the leaf queue when popped)
-        }
-      }
-      if (__any_sync(FULL, late)) {
+      sp = 0;
+      nlq = 0;
+      if (!take(h, k)) {
         err = DERR_TIMEOUT;
         break;
       }
-      c_res += lane == 0 ? (unsigned)k : 0u;
-      const unsigned mt = __ballot_sync(FULL, tpush);
-      if (tpush) stk[__popc(mt & lt)] = ent;
-      sp = __popc(mt);
-      nlq = 0;
-      __syncwarp();
       continue;
     }
-    // 3. a straggler and hungry warps: give the older half of the stack
+    // 3. a straggler and hungry warps: give the older half of the stack and
+    // of the leaf queue
     if (give && sp >= Cf::NT) {
       if (!give_half(sp / 2)) {
+        err = DERR_QUEUE;
+        break;
+      }
+    }
+    if (give && nlq >= pmax) {
+      if (!give_leaves(nlq / 2)) {
         err = DERR_QUEUE;
         break;
       }
@@ -2205,9 +2252,17 @@ __global__ void __launch_bounds__(128, 4) k_stream(StreamArgs P) {
     const bool act = ti < npop;
     const uint4 t = act ? stk[sp - 1 - ti] : make_uint4(0u, 0u, 0u, 0u);
     const bool xa = t.y & kExpand, xb = t.z & kExpand;
+    // the candidate's flag, offset and first triangles are requested before
+    // the node copies, so that they do not queue behind them
+    const uint8_t fl = act ? vflags[t.x] : (uint8_t)1;
+    const F3 off = act ? cand_offset(Q, t.x) : zero;
+    const int2 cbv = act ? P.cbase[t.x] : make_int2(0, 0);  // for leaf pairs
     // stage: task i, side s, slot j (of W) at float4 index (i * 2 + s) * RS + 2 j;
     // one lane per (task, side) copies the W child slots of an expanding
-    // node, or the one slot of the item's own box
+    // node, or the one slot of the item's own box.  (Spreading a node's
+    // pieces over consecutive lanes, so that each copy request is one
+    // coalesced run, measured slower here: 0.281 against 0.265 ms on the
+    // pathology step; the leaf triangles below do gain from it.)
     for (int is = lane; is < npop * 2; is += 32) {
       const int side = is & 1, i = is >> 1;
       const uint4 e = stk[sp - 1 - i];
@@ -2223,9 +2278,6 @@ __global__ void __launch_bounds__(128, 4) k_stream(StreamArgs P) {
       const int n = x ? 2 * W : 2;
       for (int h = 0; h < n; ++h) cp_async16(dst + h, src + h);
     }
-    const uint8_t fl = act ? vflags[t.x] : (uint8_t)1;
-    const F3 off = act ? cand_offset(Q, t.x) : zero;
-    const int2 cbv = act ? P.cbase[t.x] : make_int2(0, 0);  // for leaf pairs
     cp_async_wait_all();
     __syncwarp();
     sp -= npop;
@@ -2424,6 +2476,230 @@ __global__ void k_flag_emit(const uint8_t *flags, const int64_t *n_dev, const in
 }
 
 // ---------------------------------------------------------------------------
+// Single-pass compaction and box join: output offsets by decoupled
+// look-back (Merrill and Garland, "Single-pass Parallel Prefix Scan with
+// Decoupled Look-back", 2016).  Tiles take ids from a ticket counter in the
+// order blocks start them; a tile publishes its own count as soon as it has
+// it (AGG) and its inclusive prefix once known (INC); it finds its exclusive
+// prefix by summing its predecessors' words backwards, 32 at a time, down to
+// the nearest inclusive prefix.  It only waits for tiles whose ids were
+// taken before its own, by blocks that are running, so every wait ends; each
+// is bounded all the same (on expiry the kernel records DERR_TIMEOUT and the
+// host redoes the join with the multi-pass kernels).  The words and the
+// ticket are zeroed before each launch.
+// ---------------------------------------------------------------------------
+constexpr unsigned long long LB_AGG = 1ull << 62, LB_INC = 2ull << 62,
+                             LB_VAL = (1ull << 62) - 1;
+
+__device__ __forceinline__ void lb_publish(unsigned long long *state, unsigned tile,
+                                           unsigned long long word) {
+  *reinterpret_cast<volatile unsigned long long *>(state + tile) = word;
+}
+
+// one warp (all lanes): the exclusive prefix of `tile`, or -1 if a bounded
+// wait ran out
+__device__ long long lb_exclusive(const unsigned long long *state, unsigned tile,
+                                  unsigned spin_limit, int lane) {
+  long long excl = 0;
+  for (int64_t j0 = (int64_t)tile - 32;; j0 -= 32) {
+    const int64_t j = j0 + lane;
+    unsigned long long st = LB_INC;  // before tile 0: an inclusive prefix of 0
+    bool late = false;
+    if (j >= 0) {
+      unsigned it = 0;
+      while (((st = *reinterpret_cast<const volatile unsigned long long *>(state + j)) >> 62) ==
+             0ull) {
+        if (++it > spin_limit) {
+          late = true;
+          break;
+        }
+        __nanosleep(32);
+      }
+    }
+    if (__any_sync(FULL, late)) return -1;
+    const unsigned pm = __ballot_sync(FULL, (st >> 62) == 2ull);
+    const int hp = pm ? 31 - __clz(pm) : 0;  // the nearest inclusive prefix
+    long long v = lane >= hp ? (long long)(st & LB_VAL) : 0;
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(FULL, v, o);
+    excl += v;
+    if (pm) return excl;
+  }
+}
+
+// flags -> (idA, idB) of the flagged candidates in candidate order, the pair
+// count to *count and to the hit counter; one tile = CMP_CHUNK candidates
+__global__ void __launch_bounds__(CMP_T) k_compact(const uint8_t *flags, const int64_t *n_dev,
+                                                   const int32_t *cand, unsigned *ticket,
+                                                   unsigned long long *state, int32_t *out,
+                                                   int64_t *count, unsigned long long *hits,
+                                                   int *err, unsigned spin_limit) {
+  pdl_wait();
+  pdl_trigger();
+  __shared__ unsigned s_tile;
+  __shared__ int ws[CMP_T / 32];
+  __shared__ long long s_excl;
+  if (threadIdx.x == 0) s_tile = atomicAdd(ticket, 1u);
+  __syncthreads();
+  const unsigned tile = s_tile;
+  const int64_t n = *n_dev;
+  const int64_t ntiles = (n + CMP_CHUNK - 1) / CMP_CHUNK;
+  if ((int64_t)tile >= ntiles) {
+    if (tile == 0 && threadIdx.x == 0) *count = 0;  // no candidates at all
+    return;
+  }
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int64_t base = (int64_t)tile * CMP_CHUNK + (int64_t)threadIdx.x * CMP_PER;
+  // CMP_PER = 16 flags: one 16-byte load when the run is in range
+  uint8_t f[CMP_PER];
+  if (base + CMP_PER <= n) {
+    const uint4 v = *reinterpret_cast<const uint4 *>(flags + base);
+    const unsigned u[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+    for (int k = 0; k < CMP_PER; ++k) f[k] = (uint8_t)(u[k >> 2] >> (8 * (k & 3)));
+  } else {
+#pragma unroll
+    for (int k = 0; k < CMP_PER; ++k) f[k] = base + k < n ? flags[base + k] : 0;
+  }
+  int c = 0;
+#pragma unroll
+  for (int k = 0; k < CMP_PER; ++k) c += f[k] != 0;
+  int inc = c;
+  for (int o = 1; o < 32; o <<= 1) {
+    const int t = __shfl_up_sync(FULL, inc, o);
+    if (lane >= o) inc += t;
+  }
+  if (lane == 31) ws[w] = inc;
+  __syncthreads();
+  int wbase = 0, agg = 0;
+  for (int k = 0; k < CMP_T / 32; ++k) {
+    wbase += k < w ? ws[k] : 0;
+    agg += ws[k];
+  }
+  if (threadIdx.x == 0) lb_publish(state, tile, (tile == 0 ? LB_INC : LB_AGG) | (unsigned long long)agg);
+  if (w == 0) {
+    const long long e = tile == 0 ? 0 : lb_exclusive(state, tile, spin_limit, lane);
+    if (lane == 0) {
+      if (e < 0) {
+        atomicCAS(err, 0, DERR_TIMEOUT);
+      } else {
+        if (tile > 0) lb_publish(state, tile, LB_INC | (unsigned long long)(e + agg));
+        if ((int64_t)tile == ntiles - 1) *count = e + agg;
+        if (hits && agg) atomicAdd(hits, (unsigned long long)agg);
+      }
+      s_excl = e;
+    }
+  }
+  __syncthreads();
+  if (s_excl < 0) return;
+  int64_t pos = s_excl + wbase + inc - c;
+#pragma unroll
+  for (int k = 0; k < CMP_PER; ++k) {
+    if (f[k]) {
+      const int64_t i = base + k;
+      out[2 * pos] = cand[2 * i];
+      out[2 * pos + 1] = cand[2 * i + 1];
+      ++pos;
+    }
+  }
+}
+
+// The bounding-box filter join in one launch: a tile is MBB_T / 32 A meshes
+// (one warp each); its blocks count their candidates (the tests of k_mbb),
+// take the tile's output offset by look-back, then test again and write.
+// Persistent blocks take tiles from the ticket counter until none is left;
+// the last tile writes the candidate count.
+__global__ void __launch_bounds__(MBB_T) k_mbb1(const float *aabbA, int64_t MA,
+                                               const float *aabbB, int64_t MB, int self_join,
+                                               unsigned *ticket, unsigned long long *state,
+                                               int32_t *cand, int64_t *count, int *err,
+                                               unsigned spin_limit) {
+  pdl_wait();
+  pdl_trigger();
+  __shared__ float sb[MBB_TILE * 6];
+  __shared__ unsigned s_tile;
+  __shared__ long long s_wcnt[MBB_T / 32];
+  __shared__ long long s_excl;
+  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+  constexpr int WPB = MBB_T / 32;
+  const int64_t ntiles = (MA + WPB - 1) / WPB;
+  if (ntiles == 0) {
+    if (blockIdx.x == 0 && threadIdx.x == 0) *count = 0;
+    return;
+  }
+  for (;;) {
+    __syncthreads();  // s_tile and s_excl of the previous tile are no longer read
+    if (threadIdx.x == 0) s_tile = atomicAdd(ticket, 1u);
+    __syncthreads();
+    const unsigned tile = s_tile;
+    if ((int64_t)tile >= ntiles) return;
+    const int64_t i0 = (int64_t)tile * WPB, i = i0 + wib;
+    const bool has = i < MA;
+    float ax0 = 0.f, ay0 = 0.f, az0 = 0.f, ax1 = -1.f, ay1 = -1.f, az1 = -1.f;
+    if (has) {
+      const float *a = aabbA + 6 * i;
+      ax0 = a[0], ay0 = a[1], az0 = a[2], ax1 = a[3], ay1 = a[4], az1 = a[5];
+    }
+    // in a self join only j > i counts: tiles below the block's first i are skipped
+    const int64_t jstart = self_join ? ((i0 + 1) / MBB_TILE) * MBB_TILE : 0;
+    int64_t pos = 0;
+    for (int pass = 0; pass < 2; ++pass) {
+      int64_t cnt = 0;
+      for (int64_t t0 = jstart; t0 < MB; t0 += MBB_TILE) {
+        const int n = MB - t0 < MBB_TILE ? (int)(MB - t0) : MBB_TILE;
+        __syncthreads();  // the previous tile is no longer read
+        for (int k = threadIdx.x; k < n * 6; k += MBB_T) sb[k] = aabbB[6 * t0 + k];
+        __syncthreads();
+        if (!has) continue;
+        for (int j0 = 0; j0 < n; j0 += 32) {
+          const int jj = j0 + lane;
+          const int64_t j = t0 + jj;
+          bool ov = false;
+          if (jj < n && (!self_join || j > i)) {
+            const float *bb = sb + 6 * jj;
+            ov = ax0 <= bb[3] && bb[0] <= ax1 && ay0 <= bb[4] && bb[1] <= ay1 && az0 <= bb[5] &&
+                 bb[2] <= az1;
+          }
+          const unsigned m = __ballot_sync(FULL, ov);
+          if (pass == 1 && ov) {
+            const int64_t p = pos + __popc(m & ((1u << lane) - 1u));
+            cand[2 * p] = (int32_t)i;
+            cand[2 * p + 1] = (int32_t)j;
+          }
+          if (pass == 1) pos += __popc(m);
+          else cnt += __popc(m);
+        }
+      }
+      if (pass == 1) break;
+      // the tile's count, its offset by look-back, each warp's start
+      if (lane == 0) s_wcnt[wib] = cnt;
+      __syncthreads();
+      long long agg = 0, before = 0;
+      for (int k = 0; k < WPB; ++k) {
+        before += k < wib ? s_wcnt[k] : 0;
+        agg += s_wcnt[k];
+      }
+      if (threadIdx.x == 0)
+        lb_publish(state, tile, (tile == 0 ? LB_INC : LB_AGG) | (unsigned long long)agg);
+      if (wib == 0) {
+        const long long e = tile == 0 ? 0 : lb_exclusive(state, tile, spin_limit, lane);
+        if (lane == 0) {
+          if (e < 0) {
+            atomicCAS(err, 0, DERR_TIMEOUT);
+          } else {
+            if (tile > 0) lb_publish(state, tile, LB_INC | (unsigned long long)(e + agg));
+            if ((int64_t)tile == ntiles - 1) *count = e + agg;
+          }
+          s_excl = e;
+        }
+      }
+      __syncthreads();
+      if (s_excl < 0) return;  // (the whole block: s_excl is shared)
+      pos = s_excl + before;
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
 // Leaf predicate on explicit inputs (tests of the filter and exact path)
 // ---------------------------------------------------------------------------
 __global__ void k_segtri_batch(const float *pq, const float *abc, int64_t n, int mode,
@@ -2580,7 +2856,8 @@ static cudaError_t occupancy(int device, const void *kern, int block, size_t sme
 
 pj_status run_join(Ctx *ctx, Dataset *A, Dataset *B, const int32_t *cand,
                    const int32_t *cand_off, int64_t n_cand, int cand_on_device,
-                   int self_join, const pj_join_opts *o, cudaStream_t s, pj_pairs *out) {
+                   int self_join, const pj_join_opts *o, cudaStream_t s, pj_pairs *out,
+                   bool safe) {
   // pick the BVH
   std::pair<int, int> key = o->width ? std::make_pair((int)o->width, (int)o->leaf_size)
                                      : A->last_bvh;
@@ -2633,24 +2910,48 @@ pj_status run_join(Ctx *ctx, Dataset *A, Dataset *B, const int32_t *cand,
     int64_t *offs = (int64_t *)ws_get(ctx, "mbb_offs", sizeof(int64_t) * (MA + 1), &st);
     if (!offs) return st;
     int nb = (int)std::min<int64_t>((MA + (MBB_T / 32) - 1) / (MBB_T / 32), (int64_t)ctx->num_sms * 64);
-    k_mbb<false><<<nb, MBB_T, 0, s>>>(A->d_aabb, MA, B->d_aabb, MB, self_join, counts, nullptr, nullptr);
-    ++ctx->launches;
-    PJ_CK(cudaGetLastError());
-    if ((st = scan_i64(ctx, counts, offs, MA, d_misc, s)) != PJ_OK) return st;
     const int64_t all = self_join ? MA * (MA - 1) / 2 : MA * MB;
     if (all <= (int64_t(1) << 24) && o->launch_mode != PJ_LAUNCH_PER_PAIR) {
+      // every pair fits the buffers: the count stays on the device
       Ccap = std::max<int64_t>(all, 1);
       count_on_host = false;
-    } else {
-      PJ_CK(cudaMemcpyAsync(h_misc, d_misc, 8, cudaMemcpyDeviceToHost, s));
-      PJ_CK(cudaStreamSynchronize(s));
-      C = Ccap = h_misc[0];
     }
-    d_cand = (int32_t *)ws_get(ctx, "cand", sizeof(int32_t) * 2 * (size_t)std::max<int64_t>(Ccap, 1), &st);
-    if (!d_cand) return st;
-    k_mbb<true><<<nb, MBB_T, 0, s>>>(A->d_aabb, MA, B->d_aabb, MB, self_join, nullptr, offs, d_cand);
-    ++ctx->launches;
-    PJ_CK(cudaGetLastError());
+    if (!count_on_host && !safe) {
+      // one launch: count, offset by look-back, emit (tiles of 8 A meshes)
+      d_cand = (int32_t *)ws_get(ctx, "cand", sizeof(int32_t) * 2 * (size_t)Ccap, &st);
+      if (!d_cand) return st;
+      const int64_t tiles = (MA + (MBB_T / 32) - 1) / (MBB_T / 32);
+      unsigned long long *lb =
+          (unsigned long long *)ws_get(ctx, "mbb_lookback", 8 * (size_t)(tiles + 1), &st);
+      if (!lb) return st;
+      PJ_CK(cudaMemsetAsync(lb, 0, 8 * (size_t)(tiles + 1), s));
+      // the count is written by the last tile; zero until then, so that a
+      // join whose look-back gave up refines nothing before it is redone
+      PJ_CK(cudaMemsetAsync(d_misc, 0, 8, s));
+      int occ = 0;
+      PJ_CK(occupancy(ctx->device, (const void *)k_mbb1, MBB_T, 0, &occ));
+      const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(tiles, (int64_t)std::max(occ, 1) * ctx->num_sms));
+      k_mbb1<<<grid, MBB_T, 0, s>>>(A->d_aabb, MA, B->d_aabb, MB, self_join,
+                                    reinterpret_cast<unsigned *>(lb + tiles), lb, d_cand, d_misc,
+                                    d_err, o->wait_polls > 0 ? (unsigned)o->wait_polls : (1u << 20));
+      ++ctx->launches;
+      PJ_CK(cudaGetLastError());
+    } else {
+      k_mbb<false><<<nb, MBB_T, 0, s>>>(A->d_aabb, MA, B->d_aabb, MB, self_join, counts, nullptr, nullptr);
+      ++ctx->launches;
+      PJ_CK(cudaGetLastError());
+      if ((st = scan_i64(ctx, counts, offs, MA, d_misc, s)) != PJ_OK) return st;
+      if (count_on_host) {
+        PJ_CK(cudaMemcpyAsync(h_misc, d_misc, 8, cudaMemcpyDeviceToHost, s));
+        PJ_CK(cudaStreamSynchronize(s));
+        C = Ccap = h_misc[0];
+      }
+      d_cand = (int32_t *)ws_get(ctx, "cand", sizeof(int32_t) * 2 * (size_t)std::max<int64_t>(Ccap, 1), &st);
+      if (!d_cand) return st;
+      k_mbb<true><<<nb, MBB_T, 0, s>>>(A->d_aabb, MA, B->d_aabb, MB, self_join, nullptr, offs, d_cand);
+      ++ctx->launches;
+      PJ_CK(cudaGetLastError());
+    }
   } else {
     C = Ccap = n_cand;
     if (cand_on_device) {
@@ -2684,6 +2985,10 @@ pj_status run_join(Ctx *ctx, Dataset *A, Dataset *B, const int32_t *cand,
   if (!bcount) return st;
   int64_t *boff = (int64_t *)ws_get(ctx, "cmp_offs", sizeof(int64_t) * nchunks, &st);
   if (!boff) return st;
+  // single-pass compaction: look-back words of the tiles, then the ticket
+  unsigned long long *cmp_lb =
+      (unsigned long long *)ws_get(ctx, "cmp_lookback", 8 * (size_t)(nchunks + 1), &st);
+  if (!cmp_lb) return st;
 
   PJ_CK(cudaEventRecord(ev[1], s));
   // 2. refinement
@@ -2716,7 +3021,7 @@ pj_status run_join(Ctx *ctx, Dataset *A, Dataset *B, const int32_t *cand,
   int wave_levels = o->wave_levels > 0 ? o->wave_levels : 0;
   bool stream = (o->wave_levels == 0 || o->wave_levels == PJ_FRONT_STREAM) &&
                 o->launch_mode != PJ_LAUNCH_PER_PAIR;
-  if (std::max(bA.max_depth, bB.max_depth) > 64) {
+  if (std::max(bA.max_depth, bB.max_depth) > 64 || safe) {
     wave_levels = 0;
     stream = false;
   }
@@ -2785,7 +3090,7 @@ pj_status run_join(Ctx *ctx, Dataset *A, Dataset *B, const int32_t *cand,
   args.counters = ctx->d_counters;
   args.err = d_err;
   args.stack_cap = stack_cap;
-  args.max_pop = 32;
+  args.max_pop = safe ? 1 : 32;
   args.warps_per_pair = k;
   args.MA = A->M;
   args.MB = B->M;
@@ -2794,6 +3099,7 @@ pj_status run_join(Ctx *ctx, Dataset *A, Dataset *B, const int32_t *cand,
   // pass 1 spills a pair after this many traversal steps; pass 2 after more;
   // pass 3 finishes everything
   long long budget1 = o->spill_budget > 0 ? o->spill_budget : (o->spill_budget < 0 ? 0 : 40000);
+  if (safe) budget1 = 0;
   if (per_pair) budget1 = 0;
   const long long budget2 = budget1 > 0 ? 8 * budget1 : 0;
   args.q_cap = q_cap;
@@ -2897,7 +3203,7 @@ pj_status run_join(Ctx *ctx, Dataset *A, Dataset *B, const int32_t *cand,
         sa.dq_cap = dq_cap;
         sa.spin_limit = o->wait_polls > 0 ? (unsigned)o->wait_polls : (1u << 19);
         sa.hungry_max = 2u * (unsigned)ctx->num_sms;
-        sa.give_after = 20000;
+        sa.give_after = 5000;
         const bool kt = timed && !kev.empty();
         if (kt) PJ_CK(cudaEventRecord(kev[0], s));
         PJ_CK(launch_pdl(ks, stream_grid, 128, stream_smem, s, sa));
@@ -3015,7 +3321,19 @@ pj_status run_join(Ctx *ctx, Dataset *A, Dataset *B, const int32_t *cand,
       PJ_CK(cudaGetLastError());
     }
     if (timed) PJ_CK(cudaEventRecord(ev[2], s));
-    // 3. compaction
+    // 3. compaction: one launch (offsets by look-back), or count, scan and
+    // emit in the safe mode
+    if (!safe) {
+      PJ_CK(cudaMemsetAsync(cmp_lb, 0, 8 * (size_t)(nchunks + 1), s));
+      PJ_CK(launch_pdl(k_compact, nchunks, CMP_T, 0, s, (const uint8_t *)d_flags,
+                       (const int64_t *)d_misc, (const int32_t *)d_cand,
+                       reinterpret_cast<unsigned *>(cmp_lb + nchunks), cmp_lb, d_pairs,
+                       d_misc + 1, ctx->d_counters + C_HITS, d_err,
+                       o->wait_polls > 0 ? (unsigned)o->wait_polls : (1u << 20)));
+      ++ctx->launches;
+      PJ_CK(cudaGetLastError());
+      return PJ_OK;
+    }
     PJ_CK(launch_pdl(k_flag_count, nchunks, CMP_T, 0, s, (const uint8_t *)d_flags,
                      (const int64_t *)d_misc, bcount, ctx->d_counters + C_HITS));
     ++ctx->launches;
@@ -3073,23 +3391,16 @@ pj_status run_join(Ctx *ctx, Dataset *A, Dataset *B, const int32_t *cand,
   PJ_CK(cudaStreamSynchronize(s));
   if (herr[1]) return fail(ctx, PJ_ERR_INVALID_ARG, "a candidate mesh id is out of range");
   if (herr[2]) return fail(ctx, PJ_ERR_INVALID_ARG, "a translated candidate mesh leaves the 2^18 grid");
-  if (herr[0] == DERR_STACK || herr[0] == DERR_QUEUE || herr[0] == DERR_TIMEOUT) {
+  if (!safe && (herr[0] == DERR_STACK || herr[0] == DERR_QUEUE || herr[0] == DERR_TIMEOUT)) {
     // batched pops outgrew the stack, a spill queue filled up or a bounded
-    // wait gave up: redo every pair in plain depth-first order (whose stack
-    // bound holds by construction) and in one pass
+    // wait gave up: redo the whole join in the safe mode -- every pair in
+    // plain depth-first order (whose stack bound holds by construction), in
+    // one pass, and the multi-pass box join and compaction
     if (dq) ws_mark_dirty(ctx, "stream_queue");
-    args.max_pop = 1;
-    budget1 = 0;
-    wave_levels = 0;
-    stream = false;
-    front = false;
-    PJ_CK(cudaMemsetAsync(d_err, 0, sizeof(int) * 4, s));
-    if ((st = device_part(true)) != PJ_OK) return st;
-    PJ_CK(cudaEventRecord(e1, s));
-    PJ_CK(cudaMemcpyAsync(h_misc, d_misc, 16, cudaMemcpyDeviceToHost, s));
-    PJ_CK(cudaMemcpyAsync(herr, d_err, sizeof(herr), cudaMemcpyDeviceToHost, s));
-    PJ_CK(cudaStreamSynchronize(s));
-    replayed = false;
+    pj_join_opts o2 = *o;
+    o2.use_graph = 0;
+    return run_join(ctx, A, B, cand, cand_off, n_cand, cand_on_device, self_join, &o2, s, out,
+                    true);
   }
   if (herr[0]) return fail(ctx, PJ_ERR_INTERNAL, "traversal stack capacity exceeded");
   const int64_t K = h_misc[1];
