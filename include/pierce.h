@@ -277,7 +277,10 @@ pj_status pj_join_intersects_ex(pj_ctx *ctx, pj_dataset a, pj_dataset b,
                                 const pj_join_opts *opts, void *cuda_stream,
                                 pj_pairs *out);
 
-/* Free a join result. */
+/* Free a join result.  Device buffers (pairs with out_host = 0, flags,
+ * cycles) go back to a pool of the context that later joins reuse instead of
+ * calling cudaMalloc / cudaFree: any work of the caller that reads them must
+ * have completed (pj_destroy frees the pool). */
 pj_status pj_free_pairs(pj_ctx *ctx, pj_pairs *res);
 
 /* The join's device part with no allocation at all (the paper has no

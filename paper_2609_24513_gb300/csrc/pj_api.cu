@@ -108,6 +108,52 @@ void *ws_get_zeroed(Ctx *ctx, const char *name, size_t bytes, cudaStream_t s, pj
 
 void ws_mark_dirty(Ctx *ctx, const char *name) { cur_exec(ctx)->ws[name].zeroed = false; }
 
+void *pool_get(Ctx *ctx, size_t bytes, cudaError_t *e) {
+  *e = cudaSuccess;
+  auto it = ctx->pool.lower_bound(bytes);
+  if (it != ctx->pool.end() && it->first <= 4 * std::max<size_t>(bytes, 4096)) {
+    void *p = it->second;
+    ctx->pool_bytes -= it->first;
+    ctx->pool.erase(it);
+    return p;
+  }
+  size_t cap = 4096;
+  while (cap < bytes) cap *= 2;
+  void *p = nullptr;
+  *e = cudaMalloc(&p, cap);
+  if (*e != cudaSuccess) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  ctx->pool_cap[p] = cap;
+  return p;
+}
+
+void pool_put(Ctx *ctx, void *p) {
+  if (!p) return;
+  auto it = ctx->pool_cap.find(p);
+  if (it == ctx->pool_cap.end()) {
+    cudaFree(p);
+    return;
+  }
+  if (ctx->pool_bytes + it->second > (size_t(1) << 30)) {
+    cudaFree(p);
+    ctx->pool_cap.erase(it);
+    return;
+  }
+  ctx->pool.emplace(it->second, p);
+  ctx->pool_bytes += it->second;
+}
+
+void pool_release(Ctx *ctx) {
+  for (auto &kv : ctx->pool) {
+    cudaFree(kv.second);
+    ctx->pool_cap.erase(kv.second);
+  }
+  ctx->pool.clear();
+  ctx->pool_bytes = 0;
+}
+
 // ---------------------------------------------------------------------------
 // Load kernels
 // ---------------------------------------------------------------------------
@@ -501,6 +547,7 @@ pj_status pj_destroy(pj_ctx *h) {
   for (auto &kv : ctx->datasets) free_dataset(kv.second.get());
   for (auto &g : ctx->graphs) cudaGraphExecDestroy(g.second);
   exec_free(&ctx->main);
+  pool_release(ctx);
   cudaFree(ctx->d_counters);
   cudaStreamDestroy(ctx->stream);
   delete ctx;
@@ -674,12 +721,12 @@ pj_status pj_free_pairs(pj_ctx *h, pj_pairs *res) {
   std::lock_guard<std::mutex> lk(ctx->mu);
   cudaSetDevice(ctx->device);
   if (res->pairs) {
-    if (res->on_device) cudaFree(res->pairs);
+    if (res->on_device) pool_put(ctx, res->pairs);
     else if (res->pairs_malloc) free(res->pairs);
     else cudaFreeHost(res->pairs);
   }
-  if (res->flags) cudaFree(res->flags);
-  if (res->cycles) cudaFree(res->cycles);
+  pool_put(ctx, res->flags);
+  pool_put(ctx, res->cycles);
   memset(res, 0, sizeof(*res));
   return PJ_OK;
 }

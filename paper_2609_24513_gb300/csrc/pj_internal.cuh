@@ -122,7 +122,23 @@ struct Ctx {
   // API calls that add or remove one take it exclusively (after `mu`)
   std::shared_mutex ds_rw;
   Serve *serve = nullptr;
+  // device buffers of join results (pairs, flags, cycles): pj_free_pairs
+  // hands them back here and later joins reuse them, so that neither side
+  // pays for cudaMalloc / cudaFree (the latter synchronises the device).
+  // pool: free buffers by capacity; cap: capacity of every buffer the pool
+  // made, free or lent out.  Guarded by `mu`.
+  std::multimap<size_t, void *> pool;
+  std::map<void *, size_t> pool_cap;
+  size_t pool_bytes = 0;  // capacity of the free buffers
 };
+
+// A device buffer of at least `bytes` from the context's result pool (or a
+// new one, its size rounded up to a power of two of at least 4 KiB).
+void *pool_get(Ctx *c, size_t bytes, cudaError_t *e);
+// Give a buffer back: pooled if the pool made it (and the free buffers stay
+// under 1 GiB), else cudaFree.  The caller's work on it must be complete.
+void pool_put(Ctx *c, void *p);
+void pool_release(Ctx *c);  // cudaFree every free pooled buffer
 
 // The scratch the calling thread works with: a serving thread's own, else
 // the context's.
