@@ -331,6 +331,7 @@ def run_ours(args, rank, world, local_rank):
     cand_host = _candidates_host(ctx, ha, hb, C)
     if not args.no_e2e:
         line_e2e = _end_to_end(ctx, ha, hb, cand_host, args, flush, stream, dist, pierce)
+    serving = None if args.no_serving else _serving_summary(ctx, pierce, ha, hb, args.seed)
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
@@ -359,6 +360,12 @@ def run_ours(args, rank, world, local_rank):
                              "tasks_ms": phase_ms["tasks_ms"]}},
             "e2e": line_e2e,
             "clocks": clk}
+    if serving:
+        # the metric's latency part: window queries on the same resident
+        # datasets at 2,000 queries/s (Poisson), submit to results on the host
+        line["p50_ms"] = serving["poisson_2000qps"]["p50_ms"]
+        line["p99_ms"] = serving["poisson_2000qps"]["p99_ms"]
+        line["serving"] = serving
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(A, B, cand_host, args.cpu_seconds, args.seed)
     ctx.close()
@@ -394,6 +401,35 @@ def _end_to_end(ctx, ha, hb, cand_host, args, flush, stream, dist, pierce):
     e2e_ms, e2e_units = aggregate_ranks(1000.0 * e2e_t / args.steps, len(cand_np), dist, "cuda")
     return {"value": e2e_units / (e2e_ms / 1000.0), "unit": UNIT,
             "h2d_bytes_per_step": int(cand_np.nbytes), "d2h_bytes_per_step": int(8 * e2e_k + 8)}
+
+
+def _serving_summary(ctx, pierce, ha, hb, seed, n_alone=200, n_poisson=400, n_burst=800):
+    """Window join queries through pj_submit / pj_poll on the resident
+    datasets: one at a time, as a Poisson stream at 2,000 queries/s and as a
+    burst submitted at once (a saturating load, so that continuous batching
+    forms batches); p50/p99 latency, throughput and mean batch size of each,
+    and whether every answer equals the same query served alone."""
+    from paper_2609_24513_gb300 import synth
+    lo, hi = synth.serving_windows(seed + 77, max(n_alone, n_poisson, n_burst))
+    _serve_stream(ctx, pierce, ha, hb, lo[:64], hi[:64], np.zeros(64))   # warm-up
+    alone_ans, alone_st = [], []
+    t0 = time.perf_counter()
+    for k in range(n_alone):
+        a, st = ctx.poll(ctx.submit(ha, hb, lo[k], hi[k]), wait=True)
+        alone_ans.append(a)
+        alone_st.append(st)
+    out = {"alone": _latency_summary(alone_st, time.perf_counter() - t0)}
+    identical = True
+    for name, n, arr in (("poisson_2000qps", n_poisson, synth.poisson_arrivals(seed + 101, 2000.0, n_poisson)),
+                         ("burst", n_burst, np.zeros(n_burst))):
+        ans, st, span = _serve_stream(ctx, pierce, ha, hb, lo[:n], hi[:n], arr)
+        for k in range(min(n, n_alone)):
+            identical &= bool(np.array_equal(ans[k], alone_ans[k]))
+        out[name] = _latency_summary(st, span)
+    out["answers_identical_to_alone"] = identical
+    out["burst_speedup_over_alone_qps"] = (out["burst"]["queries_per_s"] /
+                                           out["alone"]["queries_per_s"])
+    return out
 
 
 def _candidates_host(ctx, ha, hb, n):
@@ -664,6 +700,8 @@ def main():
                     help="reference arm: seconds of oracle work over all timed steps")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-serving", action="store_true",
+                    help="skip the short serving run (p50/p99 latency) of the default line")
     ap.add_argument("--nuclei", type=int, default=10000)
     ap.add_argument("--vessels", type=int, default=500)
     ap.add_argument("--workload", default="pathology",

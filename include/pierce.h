@@ -81,6 +81,23 @@ enum { PJ_LEAF_FILTERED = 0, PJ_LEAF_EXACT = 1 };
 enum { PJ_LEAF_STATIC = 2 };
 enum { PJ_LAUNCH_PERSISTENT = 0, PJ_LAUNCH_PER_PAIR = 1 };
 enum { PJ_FRONT_NONE = -1, PJ_FRONT_STREAM = -2 };  /* pj_join_opts.wave_levels */
+/* pj_join_opts.predicate: the paper's join predicates (Sec. 3.2-3.4).  With
+ * cross(A_i, B_j) = an edge of one mesh strictly pierces a triangle of the
+ * other (Sec. 3.2, both directions) and inside(X, Y) = X's representative
+ * vertex (its lexicographically smallest vertex off Y's surface) has odd
+ * ray parity against Y (Sec. 3.3):
+ *   PJ_PRED_INTERSECTS  cross OR inside(B_j, A_i) OR inside(A_i, B_j)  (Sec. 3.4)
+ *   PJ_PRED_OVERLAP     cross                                           (Sec. 3.2)
+ *   PJ_PRED_CONTAINS    A_i contains B_j: no cross AND inside(B_j, A_i) (Alg. 2)
+ *   PJ_PRED_WITHIN      A_i within B_j:  no cross AND inside(A_i, B_j)
+ *   PJ_PRED_ANY_VERTEX  intersects, or some vertex of either mesh strictly
+ *                       inside the other (off its surface, odd parity): a
+ *                       completeness mode for meshes whose surfaces cross
+ *                       only through edges and vertices, which the strict
+ *                       crossing test does not see.  It tests every vertex in
+ *                       the other mesh's box, so it costs far more. */
+enum { PJ_PRED_INTERSECTS = 0, PJ_PRED_OVERLAP = 1, PJ_PRED_CONTAINS = 2, PJ_PRED_WITHIN = 3,
+       PJ_PRED_ANY_VERTEX = 4 };
 
 /* Options of one join.  Zero-initialised = defaults. */
 typedef struct {
@@ -121,6 +138,7 @@ typedef struct {
                                plain depth-first traversal with the
                                multi-pass box join and compaction (same
                                result, slower)                              */
+  int32_t predicate;        /* PJ_PRED_* (0: intersects)                     */
 } pj_join_opts;
 
 /* Result of a join.  Owned by the library until pj_free_pairs. */

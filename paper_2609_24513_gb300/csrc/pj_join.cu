@@ -332,6 +332,10 @@ struct RefineArgs {
   const unsigned int *q_par_n;
   unsigned int *q_par_pos;
   unsigned int q_par_cap;
+  // join predicate (PJ_PRED_*); with contains / within the containment
+  // result goes to pflags and flags keeps the crossing result
+  int predicate;
+  uint8_t *pflags;
 };
 
 struct Cnt {
@@ -906,6 +910,29 @@ __device__ int pair_inside(const Side &Q, int iq, F3 qoff, const Side &T, int it
   return 0;
 }
 
+// Some vertex of Q_iq strictly inside T_it: off T's surface with odd ray
+// parity (the any-vertex completeness mode).  Vertices outside T's closed box
+// are outside T.  Returns 1/0, or -1 on a capacity error.
+template <int W>
+__device__ int pair_any_inside(const Side &Q, int iq, F3 qoff, const Side &T, int it, F3 toff,
+                               WarpMem &sm, int lane, int stack_cap, int max_pop, Cnt &cnt) {
+  const int64_t v0 = Q.voff[iq], nv = Q.voff[iq + 1] - v0;
+  const float *tb = T.aabb + 6 * (int64_t)it;
+  F3 lo = add(ld3(tb), toff), hi = add(ld3(tb + 3), toff);
+  for (int64_t k = 0; k < nv; ++k) {
+    F3 v = add(ld3(Q.xyz + 3 * (v0 + k)), qoff);
+    if (lane == 0) cnt.v[C_BYTES] += 12;
+    if (v.x < lo.x || v.x > hi.x || v.y < lo.y || v.y > hi.y || v.z < lo.z || v.z > hi.z)
+      continue;
+    int ax, dir;
+    ray_axis_choice(v, lo, hi, ax, dir);
+    int r = parity_query<W>(T, it, toff, v, ax, dir, sm, lane, stack_cap, max_pop, cnt);
+    if (r < 0) return -1;
+    if (r == 1) return 1;
+  }
+  return 0;
+}
+
 __device__ __forceinline__ void bar_group(int id, int nthreads) {
   asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(nthreads) : "memory");
 }
@@ -982,26 +1009,35 @@ __global__ void __launch_bounds__(128, 4) k_refine(RefineArgs P) {
       res = group_flag[grp];
       bar_group(1 + grp, 32 * k);
     }
-    if (!res) {
-      // containment both ways; with several warps per pair, ranks 0 and 1
-      // take one direction each
+    // containment (Sec. 3.3): both directions for intersects, one for
+    // contains (B_j inside A_i) or within (A_i inside B_j), none for overlap;
+    // with several warps per pair, ranks 0 and 1 take one direction each
+    const bool dBA = P.predicate != PJ_PRED_OVERLAP && P.predicate != PJ_PRED_WITHIN;
+    const bool dAB = P.predicate != PJ_PRED_OVERLAP && P.predicate != PJ_PRED_CONTAINS;
+    int ins = 0;
+    if (!res && (dBA || dAB)) {
       int r1 = 0, r2 = 0;
       F3 zero = mkf3(0.f, 0.f, 0.f);
-      if (rank == 0)
+      if (rank == 0 && dBA)
         r1 = pair_inside<W>(P.B, ib, off, P.A, ia, zero, sm, lane, P.stack_cap, P.max_pop, cnt);
-      if ((k == 1 && r1 == 0) || (k > 1 && rank == 1))
+      if (dAB && ((k == 1 && r1 == 0) || (k > 1 && rank == 1)))
         r2 = pair_inside<W>(P.A, ia, zero, P.B, ib, off, sm, lane, P.stack_cap, P.max_pop, cnt);
       if (r1 < 0 || r2 < 0) {
         if (lane == 0) atomicCAS(P.err, 0, DERR_STACK);
         r1 = r2 = 0;
       }
-      res = (r1 > 0 || r2 > 0) ? 1 : 0;
+      ins = (r1 > 0 || r2 > 0) ? 1 : 0;
       if (k > 1) {
-        if (res && lane == 0) group_flag[grp] = 1;
+        if (ins && lane == 0) group_flag[grp] = 1;
         bar_group(1 + grp, 32 * k);
-        res = group_flag[grp];
+        ins = group_flag[grp];
         bar_group(1 + grp, 32 * k);
       }
+    }
+    if (P.pflags) {
+      if (rank == 0 && lane == 0) P.pflags[c] = (uint8_t)ins;  // flags[c] = the crossing
+    } else {
+      res = res || ins;
     }
     if (rank == 0 && lane == 0) {
       if (P.cycles) {
@@ -1045,6 +1081,9 @@ struct WaveArgs {
   uint4 *q_par;              // parity rays over the per-thread node budget
   unsigned int *q_par_n;
   unsigned int q_par_cap;
+  int par_dirs;              // parity rays cast: bit 0 inside(B, A), bit 1 inside(A, B)
+  uint8_t *pflags;           // where parity results go (null: flags)
+  const uint8_t *need;       // non-null: only candidates with need[c] != 0 are traversed
 };
 
 __device__ __forceinline__ F3 cand_offset(const WaveArgs &P, int64_t c) {
@@ -1144,7 +1183,7 @@ __global__ void k_wave_init(WaveArgs P, uint4 *q, unsigned *q_n) {
     const int64_t g = g0 + threadIdx.x;
     bool push = false;
     uint2 t = make_uint2(0u, 0u);
-    if (g < n) {
+    if (g < n && (!P.need || P.need[g])) {
       const int ia = P.cand[2 * g], ib = P.cand[2 * g + 1];
       if (ia >= 0 && ia < P.MA && ib >= 0 && ib < P.MB) {
         const F3 off = cand_offset(P, g);
@@ -1470,6 +1509,7 @@ __global__ void __launch_bounds__(128) k_wave_parity(WaveArgs P) {
   for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < n; g += stride) {
     const int64_t c = g >> 1;
     const bool bInA = (g & 1) == 0;
+    if (!((P.par_dirs >> (bInA ? 0 : 1)) & 1)) continue;  // direction not asked for
     const int ia = P.cand[2 * c], ib = P.cand[2 * c + 1];
     if (ia < 0 || ia >= P.MA || ib < 0 || ib >= P.MB) continue;
     const F3 off = cand_offset(P, c);
@@ -1521,7 +1561,7 @@ __global__ void __launch_bounds__(128) k_wave_parity(WaveArgs P) {
         break;
       }
     }
-    if (res) P.flags[c] = 1;
+    if (res) (P.pflags ? P.pflags : P.flags)[c] = 1;
   }
   const int slots[6] = {C_PARITY_RAYS, C_PARITY_NODES, C_PARITY_TRIS, C_BYTES, C_BYTES_PARITY,
                         C_PAR_HANDOVER};
@@ -1551,7 +1591,7 @@ __global__ void __launch_bounds__(128, 4) k_refine_tasks(RefineArgs P) {
     if (t >= np) break;
     const uint4 e = P.q_par[t];
     const uint32_t c = e.x;
-    volatile uint8_t *flag = P.flags + c;
+    volatile uint8_t *flag = (P.pflags ? P.pflags : P.flags) + c;
     int done = lane == 0 ? (int)*flag : 0;
     if (__shfl_sync(FULL, done, 0)) continue;
     const int ia = P.cand[2 * (int64_t)c], ib = P.cand[2 * (int64_t)c + 1];
@@ -1614,6 +1654,56 @@ __global__ void __launch_bounds__(128, 4) k_refine_tasks(RefineArgs P) {
     for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(FULL, v, o);
     if (lane == 0 && v) atomicAdd(P.counters + i, v);
   }
+}
+
+// The any-vertex completeness mode: after the intersection join, each
+// candidate not found intersecting is tested vertex by vertex, both ways
+// (one warp per candidate, warp-cooperative parity rays).
+template <int W>
+__global__ void __launch_bounds__(128, 4) k_any_vertex(RefineArgs P) {
+  pdl_wait();
+  pdl_trigger();
+  extern __shared__ __align__(16) unsigned char smem[];
+  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+  WarpMem sm = carve<W>(smem + (size_t)wib * warp_smem_bytes<W>(P.stack_cap), P.stack_cap);
+  Cnt cnt;
+  for (int i = 0; i < C_WARP_NUM; ++i) cnt.v[i] = 0;
+  const int64_t n = *P.n_cand;
+  const F3 zero = mkf3(0.f, 0.f, 0.f);
+  for (;;) {
+    unsigned long long w = 0;
+    if (lane == 0) w = atomicAdd(P.work, 1ull);
+    const long long c = (long long)__shfl_sync(FULL, w, 0);
+    if (c >= n) break;
+    int done = lane == 0 ? (int)P.flags[c] : 0;
+    if (__shfl_sync(FULL, done, 0)) continue;
+    const int ia = P.cand[2 * c], ib = P.cand[2 * c + 1];
+    if (ia < 0 || ia >= P.MA || ib < 0 || ib >= P.MB) continue;
+    F3 off = zero;
+    if (P.cand_off)
+      off = mkf3((float)P.cand_off[3 * c], (float)P.cand_off[3 * c + 1], (float)P.cand_off[3 * c + 2]);
+    int r = pair_any_inside<W>(P.B, ib, off, P.A, ia, zero, sm, lane, P.stack_cap, P.max_pop, cnt);
+    if (r == 0)
+      r = pair_any_inside<W>(P.A, ia, zero, P.B, ib, off, sm, lane, P.stack_cap, P.max_pop, cnt);
+    if (r < 0 && lane == 0) atomicCAS(P.err, 0, DERR_STACK);
+    if (r > 0 && lane == 0) P.flags[c] = 1;
+  }
+  for (int i = 0; i < C_WARP_NUM; ++i) {
+    unsigned long long v = cnt.v[i];
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(FULL, v, o);
+    if (lane == 0 && v) atomicAdd(P.counters + i, v);
+  }
+}
+
+// contains / within: a candidate is reported when its parity test holds and
+// no crossing was found (Alg. 2): flags = pflags AND NOT flags
+__global__ void k_pred_combine(uint8_t *flags, const uint8_t *pflags, const int64_t *n_dev) {
+  pdl_wait();
+  pdl_trigger();
+  const int64_t n = *n_dev;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    flags[i] = (uint8_t)(pflags[i] != 0 && flags[i] == 0);
 }
 
 // ---------------------------------------------------------------------------
@@ -2125,7 +2215,7 @@ __global__ void __launch_bounds__(128, 4) k_stream(StreamArgs P) {
       const int64_t idx = (int64_t)base + lane;
       bool push = false;
       uint4 ent = make_uint4(0u, 0u, 0u, 0u);
-      if (idx < n_in && vflags[idx] == 0) {
+      if (idx < n_in && vflags[idx] == 0 && (!Q.need || Q.need[idx])) {
         const int ia = Q.cand[2 * idx], ib = Q.cand[2 * idx + 1];
         if (ia >= 0 && ia < Q.MA && ib >= 0 && ib < Q.MB) {
           const F3 off = cand_offset(Q, idx);
@@ -2792,6 +2882,13 @@ static WaveParityKernel pick_wave_parity(int W) {
 }
 
 typedef void (*StreamKernel)(StreamArgs);
+typedef void (*AnyVertexKernel)(RefineArgs);
+static AnyVertexKernel pick_any_vertex(int W) {
+  if (W == 2) return k_any_vertex<2>;
+  if (W == 4) return k_any_vertex<4>;
+  return k_any_vertex<8>;
+}
+
 static StreamKernel pick_stream(int W, bool exact) {
   if (W == 2) return exact ? k_stream<2, true> : k_stream<2, false>;
   if (W == 4) return exact ? k_stream<4, true> : k_stream<4, false>;
@@ -2871,6 +2968,12 @@ pj_status run_join(Ctx *ctx, Dataset *A, Dataset *B, const int32_t *cand,
   const int k = o->warps_per_pair ? o->warps_per_pair : 1;
   if (!(k == 1 || k == 2 || k == 4)) return fail(ctx, PJ_ERR_INVALID_ARG, "warps_per_pair must be 1, 2 or 4");
   const bool exact = o->leaf_mode == PJ_LEAF_EXACT;
+  const int pred = o->predicate;
+  if (pred < PJ_PRED_INTERSECTS || pred > PJ_PRED_ANY_VERTEX)
+    return fail(ctx, PJ_ERR_INVALID_ARG, "unknown join predicate");
+  // contains / within keep the parity result apart from the crossing result
+  const bool split = pred == PJ_PRED_CONTAINS || pred == PJ_PRED_WITHIN;
+  const bool parity_rays = pred != PJ_PRED_OVERLAP;
 
   pj_status st;
   // [0] n_cand, [1] K, [2] work counter, [3..4] spill queue counters, [5..7] wave counters
@@ -2988,6 +3091,16 @@ pj_status run_join(Ctx *ctx, Dataset *A, Dataset *B, const int32_t *cand,
   }
   uint8_t *d_flags = (uint8_t *)ws_get(ctx, "flags", (size_t)std::max<int64_t>(Ccap, 1), &st);
   if (!d_flags) return st;
+  uint8_t *d_pflags = nullptr;
+  if (split) {
+    d_pflags = (uint8_t *)ws_get(ctx, "pflags", (size_t)std::max<int64_t>(Ccap, 1), &st);
+    if (!d_pflags) return st;
+  }
+  unsigned long long *d_anyv = nullptr;  // work counter of the any-vertex pass
+  if (pred == PJ_PRED_ANY_VERTEX) {
+    d_anyv = (unsigned long long *)ws_get(ctx, "anyv_work", 8, &st);
+    if (!d_anyv) return st;
+  }
   int32_t *d_pairs = (int32_t *)ws_get(ctx, "pairs", sizeof(int32_t) * 2 * (size_t)std::max<int64_t>(Ccap, 1), &st);
   if (!d_pairs) return st;
   int nchunks = (int)std::max<int64_t>(1, (Ccap + CMP_CHUNK - 1) / CMP_CHUNK);
@@ -3016,6 +3129,8 @@ pj_status run_join(Ctx *ctx, Dataset *A, Dataset *B, const int32_t *cand,
     int occ_k = 0;
     PJ_CK(occupancy(ctx->device, (const void *)kern, threads, smem, &occ_k));
     PJ_CK(occupancy(ctx->device, (const void *)kern_tasks, threads, smem, &occ_k));
+    if (pred == PJ_PRED_ANY_VERTEX)
+      PJ_CK(occupancy(ctx->device, (const void *)pick_any_vertex(W), threads, smem, &occ_k));
   }
   // spill queues between the refinement passes
   const unsigned int q_cap = 1u << 22;
@@ -3105,6 +3220,8 @@ pj_status run_join(Ctx *ctx, Dataset *A, Dataset *B, const int32_t *cand,
   args.MA = A->M;
   args.MB = B->M;
   args.single = -1;
+  args.predicate = pred;
+  args.pflags = d_pflags;
   const bool per_pair = o->launch_mode == PJ_LAUNCH_PER_PAIR;
   // pass 1 spills a pair after this many traversal steps; pass 2 after more;
   // pass 3 finishes everything
@@ -3162,6 +3279,9 @@ pj_status run_join(Ctx *ctx, Dataset *A, Dataset *B, const int32_t *cand,
     wa.q_par = wpar;
     wa.q_par_n = nullptr;
     wa.q_par_cap = wpar_cap;
+    wa.par_dirs = pred == PJ_PRED_OVERLAP ? 0 : (pred == PJ_PRED_CONTAINS ? 1 : (pred == PJ_PRED_WITHIN ? 2 : 3));
+    wa.pflags = d_pflags;
+    wa.need = d_pflags;  // contains / within: traverse where the parity test holds
     return wa;
   };
   // everything from here to the compacted pairs is a fixed sequence of
@@ -3172,6 +3292,7 @@ pj_status run_join(Ctx *ctx, Dataset *A, Dataset *B, const int32_t *cand,
       ++ctx->launches;
       if (timed) PJ_CK(cudaEventRecord(ev[1], s));
     }
+    if (d_pflags) PJ_CK(cudaMemsetAsync(d_pflags, 0, (size_t)Ccap, s));
     if (Ccap > 0) {
       if (o->launch_mode == PJ_LAUNCH_PER_PAIR) {
         args.q_out = nullptr;
@@ -3210,8 +3331,10 @@ pj_status run_join(Ctx *ctx, Dataset *A, Dataset *B, const int32_t *cand,
         // (Running the parity launches on a second stream beside the
         // streaming one measured slower: its persistent grid holds the SMs,
         // so the parity flags came late -- 0.445 against 0.437 ms a step.)
-        PJ_CK(launch_pdl(pick_wave_parity(W), wave_grid[2], 128, 0, s, wa));
-        PJ_CK(launch_pdl(kern_tasks, (int)blocks, threads, smem, s, ap));
+        if (parity_rays) {
+          PJ_CK(launch_pdl(pick_wave_parity(W), wave_grid[2], 128, 0, s, wa));
+          PJ_CK(launch_pdl(kern_tasks, (int)blocks, threads, smem, s, ap));
+        }
         if (timed) PJ_CK(cudaEventRecord(ev[4], s));
         StreamArgs sa{};
         sa.w = wa;
@@ -3247,8 +3370,7 @@ pj_status run_join(Ctx *ctx, Dataset *A, Dataset *B, const int32_t *cand,
         WaveLeafKernel kl = pick_wave_leaf(W, exact);
         WaveParityKernel kp = pick_wave_parity(W);
         const int wblocks = wave_grid[0], lblocks = wave_grid[1], pblocks = wave_grid[2];
-        k_wave_init<<<wblocks, 256, 0, s>>>(wa, wqa, qn);
-        PJ_CK(launch_pdl(kp, pblocks, 128, 0, s, wa));
+        if (parity_rays) PJ_CK(launch_pdl(kp, pblocks, 128, 0, s, wa));
         // the rays over the per-thread node budget, one warp each, before
         // the front end: a containment-only pair (no crossing to stop at)
         // is the costliest kind to traverse, so its flag should be set early
@@ -3263,8 +3385,11 @@ pj_status run_join(Ctx *ctx, Dataset *A, Dataset *B, const int32_t *cand,
         ap.q_par_n = misc + 1;
         ap.q_par_pos = misc + 2;
         ap.q_par_cap = wpar_cap;
-        PJ_CK(launch_pdl(kern_tasks, (int)blocks, threads, smem, s, ap));
+        if (parity_rays) PJ_CK(launch_pdl(kern_tasks, (int)blocks, threads, smem, s, ap));
         if (timed) PJ_CK(cudaEventRecord(ev[4], s));
+        // the roots after the parity rays: contains / within traverse only
+        // the candidates whose parity test held
+        k_wave_init<<<wblocks, 256, 0, s>>>(wa, wqa, qn);
         uint4 *qin = wqa, *qout = wqb;
         const bool kt = timed && !kev.empty();
         for (int lvl = 0; lvl < wave_levels; ++lvl) {
@@ -3338,6 +3463,21 @@ pj_status run_join(Ctx *ctx, Dataset *A, Dataset *B, const int32_t *cand,
       }
       PJ_CK(cudaGetLastError());
     }
+    // the other predicates' last steps: the any-vertex pass over what did
+    // not intersect; contains / within combine parity and crossing
+    if (pred == PJ_PRED_ANY_VERTEX && Ccap > 0) {
+      PJ_CK(cudaMemsetAsync(d_anyv, 0, 8, s));
+      RefineArgs av = args;
+      av.work = d_anyv;
+      av.max_pop = 32;
+      PJ_CK(launch_pdl(pick_any_vertex(W), (int)blocks, threads, smem, s, av));
+      ++ctx->launches;
+    }
+    if (split && Ccap > 0) {
+      PJ_CK(launch_pdl(k_pred_combine, std::min(blocks_for(Ccap, 256), ctx->num_sms * 8), 256, 0,
+                       s, d_flags, (const uint8_t *)d_pflags, (const int64_t *)d_misc));
+      ++ctx->launches;
+    }
     if (timed) PJ_CK(cudaEventRecord(ev[2], s));
     // 3. compaction: one launch (offsets by look-back), or count, scan and
     // emit in the safe mode
@@ -3369,7 +3509,7 @@ pj_status run_join(Ctx *ctx, Dataset *A, Dataset *B, const int32_t *cand,
            (void *)d_cand, (void *)d_off, (void *)d_cycles, W, key.second, (int)exact, k,
            (int)o->launch_mode, (long long)Ccap, (int)budget1,
            args.max_pop * 1000 + wave_levels * 2 + (stream ? 1 : 0),
-           mbb_in_graph ? 1 + self_join : 0);
+           (mbb_in_graph ? 1 + self_join : 0) + 4 * pred);
   snprintf(gk + strlen(gk), sizeof(gk) - strlen(gk), "|%d", (int)o->wait_polls);
   bool replayed = false;
   if (graph) {
@@ -3628,6 +3768,8 @@ pj_status run_join_noalloc(Ctx *ctx, Dataset *A, Dataset *B, const int32_t *d_ca
   args.MA = A->M;
   args.MB = B->M;
   args.single = -1;
+  args.predicate = PJ_PRED_INTERSECTS;
+  args.pflags = nullptr;
 
   k_noalloc_begin<<<1, 1, 0, s>>>(scr, n);
   if (n > 0) {

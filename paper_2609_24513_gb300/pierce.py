@@ -21,6 +21,9 @@ PJ_PENDING = 9
 PJ_LEAF_FILTERED, PJ_LEAF_EXACT, PJ_LEAF_STATIC = 0, 1, 2
 PJ_LAUNCH_PERSISTENT, PJ_LAUNCH_PER_PAIR = 0, 1
 PJ_FRONT_NONE, PJ_FRONT_STREAM = -1, -2   # pj_join_opts.wave_levels
+# pj_join_opts.predicate (the paper's join predicates, Sec. 3.2-3.4)
+PJ_PRED_INTERSECTS, PJ_PRED_OVERLAP, PJ_PRED_CONTAINS, PJ_PRED_WITHIN, PJ_PRED_ANY_VERTEX = range(5)
+PREDICATES = {"intersects": 0, "overlap": 1, "contains": 2, "within": 3, "any_vertex": 4}
 
 _STATUS = {1: "PJ_ERR_INVALID_ARG", 2: "PJ_ERR_NOT_QUANTIZED", 3: "PJ_ERR_NOT_MANIFOLD",
            4: "PJ_ERR_NO_MEMORY", 5: "PJ_ERR_BUSY", 6: "PJ_ERR_TIMEOUT", 7: "PJ_ERR_CUDA",
@@ -50,7 +53,7 @@ class pj_join_opts(ctypes.Structure):
                 ("out_host", ctypes.c_int32), ("keep_flags", ctypes.c_int32),
                 ("record_cycles", ctypes.c_int32), ("spill_budget", ctypes.c_int32),
                 ("wave_levels", ctypes.c_int32), ("kernel_times", ctypes.c_int32),
-                ("wait_polls", ctypes.c_int32)]
+                ("wait_polls", ctypes.c_int32), ("predicate", ctypes.c_int32)]
 
 
 class pj_pairs(ctypes.Structure):
@@ -265,7 +268,8 @@ def pj_join_intersects_ex(ctx, a: int, b: int, cand=None, cand_offsets=None, sel
                           width=0, leaf_size=0, warps_per_pair=0, leaf_mode=PJ_LEAF_FILTERED,
                           launch_mode=PJ_LAUNCH_PERSISTENT, use_graph=False, out_host=True,
                           keep_flags=False, record_cycles=False, spill_budget=0, wave_levels=0,
-                          kernel_times=False, wait_polls=0, stream=None):
+                          kernel_times=False, wait_polls=0, predicate=PJ_PRED_INTERSECTS,
+                          stream=None):
     """Run the join.  Returns the filled pj_pairs (free it with pj_free_pairs).
 
     cand / cand_offsets: None (device bounding-box filter join), numpy int32
@@ -280,7 +284,8 @@ def pj_join_intersects_ex(ctx, a: int, b: int, cand=None, cand_offsets=None, sel
         n = int(cand.shape[0])
     opts = pj_join_opts(width, leaf_size, warps_per_pair, leaf_mode, launch_mode,
                         int(use_graph), int(out_host), int(keep_flags), int(record_cycles),
-                        int(spill_budget), int(wave_levels), int(kernel_times), int(wait_polls))
+                        int(spill_budget), int(wave_levels), int(kernel_times), int(wait_polls),
+                        int(PREDICATES.get(predicate, predicate)))
     res = pj_pairs()
     rc = load().pj_join_intersects_ex(ctx, a, b, _ptr(cand), _ptr(cand_offsets), n,
                                       1 if dev else 0, int(self_join), ctypes.byref(opts),

@@ -41,7 +41,7 @@ def test_binding_covers_the_header():
 
 def test_struct_sizes_match_header_layout():
     assert ctypes.sizeof(pierce.pj_config) == 32
-    assert ctypes.sizeof(pierce.pj_join_opts) == 52
+    assert ctypes.sizeof(pierce.pj_join_opts) == 56
     assert ctypes.sizeof(pierce.pj_pairs) == 96
     assert ctypes.sizeof(pierce.pj_counters) == 20 * 8
     assert ctypes.sizeof(pierce.pj_query) == 40
