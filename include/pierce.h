@@ -338,6 +338,32 @@ pj_status pj_join_intersects_noalloc(pj_ctx *ctx, pj_dataset a, pj_dataset b,
                                      int64_t *d_count, void *cuda_stream);
 
 /* --------------------------------------------------------------------------
+ * Selectivity estimate (paper Sec. 3.5, "Result Materialization")
+ * ------------------------------------------------------------------------ */
+
+typedef struct {
+  double e_final;           /* expected intersecting pairs: sum over the grid
+                               cells of N_1 N_2 min(P_base F_shape, 1)       */
+  double slots;             /* hashmap slots: e_final / 0.5 (load factor)    */
+  int64_t cells_occupied;   /* cells touched by objects of both datasets     */
+  int32_t grid;             /* G: cells per axis                             */
+  float ms;                 /* device time (CUDA events)                     */
+} pj_estimate;
+
+/* The paper's estimate of a join's result size, from per-cell statistics of
+ * a G x G x G grid over the box of both datasets (Sec. 3.5): per cell and
+ * dataset k the number N_k of objects whose closed box touches the cell,
+ * their mean box side S_k and mean mesh-to-box volume ratio; P_base =
+ * (S_1 + S_2 + 1e-3)^3 / V_cell (the Minkowski sum of two cubes), F_shape =
+ * sqrt(VolRatio_1 VolRatio_2)^0.8, E_i = N_1 N_2 min(P_base F_shape, 1).
+ * Lengths are in units of the grid extent (coordinates / (2^18 - 1)).
+ * grid: G in [1, 256] (0: 16).  cells_out: NULL, or a host array of G^3
+ * doubles that receives each cell's E_i (index (x G + y) G + z).  Reads only
+ * the datasets' meshes and boxes (no BVH needed).  Synchronous. */
+pj_status pj_estimate_join(pj_ctx *ctx, pj_dataset a, pj_dataset b, int32_t grid,
+                           double *cells_out, pj_estimate *out);
+
+/* --------------------------------------------------------------------------
  * Autotuning (the paper has no counterpart: its parameters are fixed by
  * OptiX; here BVH width, leaf size, warps per pair and the depth of the
  * breadth-first front end are chosen per dataset pair by measurement)

@@ -698,6 +698,19 @@ pj_status pj_join_intersects_noalloc(pj_ctx *h, pj_dataset a, pj_dataset b,
                           stream ? (cudaStream_t)stream : ctx->stream);
 }
 
+pj_status pj_estimate_join(pj_ctx *h, pj_dataset a, pj_dataset b, int32_t grid,
+                           double *cells_out, pj_estimate *out) {
+  Ctx *ctx = reinterpret_cast<Ctx *>(h);
+  if (!ctx || !out) return PJ_ERR_INVALID_ARG;
+  std::lock_guard<std::mutex> lk(ctx->mu);
+  clear_err(ctx);
+  Dataset *A = get_ds(ctx, a), *B = get_ds(ctx, b);
+  if (!A || !B) return fail(ctx, PJ_ERR_INVALID_ARG, "unknown dataset");
+  if (grid < 0) return fail(ctx, PJ_ERR_INVALID_ARG, "negative grid");
+  cudaSetDevice(ctx->device);
+  return run_estimate(ctx, A, B, grid, cells_out, out, ctx->stream);
+}
+
 pj_status pj_submit(pj_ctx *h, const pj_query *q, pj_ticket *out) {
   Ctx *ctx = reinterpret_cast<Ctx *>(h);
   if (!ctx || !q || !out) return PJ_ERR_INVALID_ARG;

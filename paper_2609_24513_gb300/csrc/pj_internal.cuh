@@ -185,6 +185,8 @@ pj_status run_join(Ctx *ctx, Dataset *A, Dataset *B, const int32_t *cand,
                    const int32_t *cand_off, int64_t n_cand, int cand_on_device,
                    int self_join, const pj_join_opts *opts, cudaStream_t s,
                    pj_pairs *out, bool safe = false);
+pj_status run_estimate(Ctx *ctx, Dataset *A, Dataset *B, int G, double *cells_out,
+                       pj_estimate *out, cudaStream_t s);
 pj_status run_join_noalloc(Ctx *ctx, Dataset *A, Dataset *B, const int32_t *d_cand,
                            int64_t n, uint8_t *d_flags, int32_t *d_pairs, int64_t *d_count,
                            cudaStream_t s);

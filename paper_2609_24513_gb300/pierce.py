@@ -115,12 +115,19 @@ class pj_query_stats(ctypes.Structure):
                 ("batch_queries", ctypes.c_int32)]
 
 
+class pj_estimate(ctypes.Structure):
+    _fields_ = [("e_final", ctypes.c_double), ("slots", ctypes.c_double),
+                ("cells_occupied", ctypes.c_int64), ("grid", ctypes.c_int32),
+                ("ms", ctypes.c_float)]
+
+
 _vp = ctypes.c_void_p
 _i64 = ctypes.c_int64
 _i32 = ctypes.c_int32
 
 # name -> (restype, argtypes)
 SIGNATURES = {
+    "pj_estimate_join": (_i32, [_vp, _i32, _i32, _i32, _vp, ctypes.POINTER(pj_estimate)]),
     "pj_create": (_i32, [ctypes.POINTER(pj_config), ctypes.POINTER(_vp)]),
     "pj_destroy": (_i32, [_vp]),
     "pj_last_error": (ctypes.c_char_p, [_vp]),
@@ -292,6 +299,21 @@ def pj_join_intersects_ex(ctx, a: int, b: int, cand=None, cand_offsets=None, sel
                                       _stream_ptr(stream), ctypes.byref(res))
     _check(ctx, rc)
     return res
+
+
+def pj_estimate_join(ctx, a: int, b: int, grid: int = 16, cells: bool = False):
+    """The paper's selectivity estimate (Sec. 3.5) of the join of datasets a
+    and b on a grid x grid x grid grid.  Returns a dict (e_final, slots,
+    cells_occupied, grid, ms), with the per-cell E_i (grid^3 float64, index
+    (x G + y) G + z) under "cells" when asked for."""
+    out = pj_estimate()
+    g = grid if grid > 0 else 16
+    buf = np.zeros(g ** 3, np.float64) if cells else None
+    _check(ctx, load().pj_estimate_join(ctx, a, b, int(grid), _ptr(buf), ctypes.byref(out)))
+    r = {k: getattr(out, k) for k, _ in pj_estimate._fields_}
+    if cells:
+        r["cells"] = buf
+    return r
 
 
 def pj_join_intersects(ctx, a: int, b: int, cand=None, self_join=False, stream=None):
