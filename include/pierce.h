@@ -338,6 +338,68 @@ pj_status pj_join_intersects_noalloc(pj_ctx *ctx, pj_dataset a, pj_dataset b,
                                      int64_t *d_count, void *cuda_stream);
 
 /* --------------------------------------------------------------------------
+ * Dataset-level join (the paper's formulation, Sec. 3.1-3.5)
+ * ------------------------------------------------------------------------ */
+
+/* How the deduplicated pair set is materialised (Sec. 3.5, Fig. 5). */
+enum {
+  PJ_MAT_ESTIMATED = 0,   /* one tracing pass inserting pairs into a hashmap
+                             of pj_estimate_join's slot count (doubled and
+                             rerun if it overflows)                          */
+  PJ_MAT_TWO_PASS = 1,    /* a counting pass, a prefix sum, an emitting pass
+                             into a flat buffer, then sort and unique        */
+  PJ_MAT_FIXED = 2        /* one pass into a hashmap of a fixed slot count   */
+};
+
+typedef struct {
+  int32_t width;            /* W of the dataset BVHs (0: 4)                  */
+  int32_t leaf_size;        /* L (0: 2)                                      */
+  int32_t predicate;        /* PJ_PRED_INTERSECTS or PJ_PRED_OVERLAP          */
+  int32_t materialize;      /* PJ_MAT_*                                      */
+  int64_t fixed_slots;      /* PJ_MAT_FIXED: hashmap slots (0: 2^26)         */
+  int32_t grid;             /* estimate grid per axis (0: 16)                */
+  int32_t out_host;         /* 1: pairs in library-owned host memory          */
+} pj_dsjoin_opts;
+
+typedef struct {
+  int64_t edges;            /* owned edges traced (both directions)          */
+  int64_t node_visits;      /* BVH nodes visited by edges and parity rays    */
+  int64_t tri_tests;        /* strict segment/triangle tests                 */
+  int64_t hits;             /* crossings found, repeats included             */
+  int64_t parity_rays;      /* one per object with a vertex in the other box */
+  int64_t recheck_pairs;    /* pairs the per-pair join decided (a parity
+                               vertex on a surface, or a ray that met more
+                               candidate objects than it can track)          */
+  int64_t slots;            /* hashmap slots, or flat records (two-pass)     */
+  int32_t relaunches;       /* hashmap overflows (each doubles the table)    */
+  int32_t reserved;
+  double estimate;          /* E_final used for sizing (estimated mode)      */
+  float ms_total;           /* device time of the join (CUDA events)         */
+  float ms_estimate;        /* of which: the estimate                        */
+  float ms_trace;           /* tracing passes (edges and parity rays)        */
+  float ms_materialize;     /* hashmap extraction or sort, unique, output    */
+} pj_dsjoin_stats;
+
+/* The join as the paper formulates it, without candidate pairs: one BVH
+ * over all triangles of each dataset (built and cached per W, L on first
+ * use); every owned edge of A traced as a bounded segment through B's BVH
+ * and every owned edge of B through A's (Alg. 1 both ways, Sec. 3.2), every
+ * strict crossing recorded (the multi-hit loop: an edge may pierce several
+ * objects) as the pair (idA, idB), duplicates merged by the chosen
+ * materialisation (Sec. 3.5).  For PJ_PRED_INTERSECTS each object also casts
+ * one parity ray from its lexicographically first vertex against the other
+ * dataset's BVH, toggling a parity bit per object it crosses (Sec. 3.3-3.4);
+ * odd parity with the vertex off that object's surface records the pair.
+ * Where the vertex lies on a surface, or the ray meets more objects whose
+ * box holds the vertex than it tracks, those pairs are decided by the
+ * per-pair join instead, so the result equals pj_join_intersects over the
+ * bounding-box candidates exactly.  self_join: a == b, pairs i < j.
+ * out: sorted unique pairs (free with pj_free_pairs); stats may be NULL.
+ * Synchronous. */
+pj_status pj_dataset_join(pj_ctx *ctx, pj_dataset a, pj_dataset b, int32_t self_join,
+                          const pj_dsjoin_opts *opts, pj_pairs *out, pj_dsjoin_stats *stats);
+
+/* --------------------------------------------------------------------------
  * Selectivity estimate (paper Sec. 3.5, "Result Materialization")
  * ------------------------------------------------------------------------ */
 

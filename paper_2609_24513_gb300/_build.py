@@ -14,7 +14,8 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libpierce.so")
-SOURCES = ["pj_api.cu", "pj_bvh.cu", "pj_join.cu", "pj_tune.cu", "pj_serve.cu", "pj_estimate.cu"]
+SOURCES = ["pj_api.cu", "pj_bvh.cu", "pj_join.cu", "pj_tune.cu", "pj_serve.cu", "pj_estimate.cu",
+           "pj_dsjoin.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

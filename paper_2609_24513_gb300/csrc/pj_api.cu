@@ -338,6 +338,7 @@ void free_bvh(Bvh &b) {
 
 static void free_dataset(Dataset *d) {
   for (auto &kv : d->bvhs) free_bvh(kv.second);
+  for (auto &kv : d->dbvhs) free_bvh(kv.second);
   cudaFree(d->d_xyz);
   cudaFree(d->d_tris);
   cudaFree(d->d_voff);
@@ -696,6 +697,22 @@ pj_status pj_join_intersects_noalloc(pj_ctx *h, pj_dataset a, pj_dataset b,
   cudaSetDevice(ctx->device);
   return run_join_noalloc(ctx, A, B, d_cand, n_cand, d_flags, d_pairs, d_count,
                           stream ? (cudaStream_t)stream : ctx->stream);
+}
+
+pj_status pj_dataset_join(pj_ctx *h, pj_dataset a, pj_dataset b, int32_t self_join,
+                          const pj_dsjoin_opts *opts, pj_pairs *out, pj_dsjoin_stats *stats) {
+  Ctx *ctx = reinterpret_cast<Ctx *>(h);
+  if (!ctx || !out) return PJ_ERR_INVALID_ARG;
+  std::lock_guard<std::mutex> lk(ctx->mu);
+  clear_err(ctx);
+  memset(out, 0, sizeof(*out));
+  Dataset *A = get_ds(ctx, a), *B = get_ds(ctx, b);
+  if (!A || !B) return fail(ctx, PJ_ERR_INVALID_ARG, "unknown dataset");
+  if (self_join && a != b) return fail(ctx, PJ_ERR_INVALID_ARG, "self_join needs a == b");
+  cudaSetDevice(ctx->device);
+  pj_dsjoin_opts o{};
+  if (opts) o = *opts;
+  return run_dataset_join(ctx, A, B, self_join, &o, out, stats, ctx->stream);
 }
 
 pj_status pj_estimate_join(pj_ctx *h, pj_dataset a, pj_dataset b, int32_t grid,

@@ -70,6 +70,9 @@ struct Dataset {
   float4 *d_mrec = nullptr;     // M * 3
   std::map<std::pair<int, int>, Bvh> bvhs;
   std::pair<int, int> last_bvh{0, 0};
+  // one BVH over all of the dataset's triangles per (W, L), for the
+  // dataset-level join; its triangle records carry the owning mesh id
+  std::map<std::pair<int, int>, Bvh> dbvhs;
   int64_t bytes = 0;
 };
 
@@ -187,6 +190,9 @@ pj_status run_join(Ctx *ctx, Dataset *A, Dataset *B, const int32_t *cand,
                    pj_pairs *out, bool safe = false);
 pj_status run_estimate(Ctx *ctx, Dataset *A, Dataset *B, int G, double *cells_out,
                        pj_estimate *out, cudaStream_t s);
+pj_status run_dataset_join(Ctx *ctx, Dataset *A, Dataset *B, int self_join,
+                           const pj_dsjoin_opts *o, pj_pairs *out, pj_dsjoin_stats *stats,
+                           cudaStream_t s);
 pj_status run_join_noalloc(Ctx *ctx, Dataset *A, Dataset *B, const int32_t *d_cand,
                            int64_t n, uint8_t *d_flags, int32_t *d_pairs, int64_t *d_count,
                            cudaStream_t s);

@@ -397,11 +397,7 @@ __device__ __forceinline__ WarpMem carve(unsigned char *base, int stack_cap) {
   return m;
 }
 
-__device__ __forceinline__ F3 ld3(const float *p) { return mkf3(p[0], p[1], p[2]); }
 
-struct Box {
-  F3 lo, hi;
-};
 
 // slot k of a node (k = -1: the node's own box): box and child word
 template <int W>
@@ -422,35 +418,6 @@ __device__ __forceinline__ bool overlap(const Box &a, const Box &b) {
 
 __device__ __forceinline__ float extent(const Box &b) {
   return fmaxf(fmaxf(b.hi.x - b.lo.x, b.hi.y - b.lo.y), b.hi.z - b.lo.z);
-}
-
-// The parity ray leaves along the axis and direction with the shortest way out
-// of the target's box (see ray_axis_hit: the parity does not depend on it).
-__device__ __forceinline__ void ray_axis_choice(F3 v, F3 lo, F3 hi, int &ax, int &dir) {
-  float best = hi.z - v.z;
-  ax = 2;
-  dir = 1;
-  const float d[6] = {hi.x - v.x, v.x - lo.x, hi.y - v.y, v.y - lo.y, hi.z - v.z, v.z - lo.z};
-  for (int k = 0; k < 6; ++k)
-    if (d[k] < best) {
-      best = d[k];
-      ax = k >> 1;
-      dir = (k & 1) ? -1 : 1;
-    }
-}
-
-// does the ray (ax, dir) from v meet the closed box?
-__device__ __forceinline__ bool ray_axis_box(F3 v, const Box &b, int ax, int dir) {
-  const float vu = ax == 0 ? v.y : (ax == 1 ? v.z : v.x);
-  const float vw = ax == 0 ? v.z : (ax == 1 ? v.x : v.y);
-  const float lu = ax == 0 ? b.lo.y : (ax == 1 ? b.lo.z : b.lo.x);
-  const float hu = ax == 0 ? b.hi.y : (ax == 1 ? b.hi.z : b.hi.x);
-  const float lw = ax == 0 ? b.lo.z : (ax == 1 ? b.lo.x : b.lo.y);
-  const float hw = ax == 0 ? b.hi.z : (ax == 1 ? b.hi.x : b.hi.y);
-  const float va = ax == 0 ? v.x : (ax == 1 ? v.y : v.z);
-  const float la = ax == 0 ? b.lo.x : (ax == 1 ? b.lo.y : b.lo.z);
-  const float ha = ax == 0 ? b.hi.x : (ax == 1 ? b.hi.y : b.hi.z);
-  return lu <= vu && vu <= hu && lw <= vw && vw <= hw && (dir > 0 ? va <= ha : la <= va);
 }
 
 // Build a task from two items (flags stripped) and their boxes: a leaf never

@@ -121,12 +121,35 @@ class pj_estimate(ctypes.Structure):
                 ("ms", ctypes.c_float)]
 
 
+class pj_dsjoin_opts(ctypes.Structure):
+    _fields_ = [("width", ctypes.c_int32), ("leaf_size", ctypes.c_int32),
+                ("predicate", ctypes.c_int32), ("materialize", ctypes.c_int32),
+                ("fixed_slots", ctypes.c_int64), ("grid", ctypes.c_int32),
+                ("out_host", ctypes.c_int32)]
+
+
+class pj_dsjoin_stats(ctypes.Structure):
+    _fields_ = [("edges", ctypes.c_int64), ("node_visits", ctypes.c_int64),
+                ("tri_tests", ctypes.c_int64), ("hits", ctypes.c_int64),
+                ("parity_rays", ctypes.c_int64), ("recheck_pairs", ctypes.c_int64),
+                ("slots", ctypes.c_int64), ("relaunches", ctypes.c_int32),
+                ("reserved", ctypes.c_int32), ("estimate", ctypes.c_double),
+                ("ms_total", ctypes.c_float), ("ms_estimate", ctypes.c_float),
+                ("ms_trace", ctypes.c_float), ("ms_materialize", ctypes.c_float)]
+
+
+# pj_dsjoin_opts.materialize (the paper's strategies, Sec. 3.5)
+PJ_MAT_ESTIMATED, PJ_MAT_TWO_PASS, PJ_MAT_FIXED = range(3)
+MATERIALIZE = {"estimated": 0, "two_pass": 1, "fixed": 2}
+
 _vp = ctypes.c_void_p
 _i64 = ctypes.c_int64
 _i32 = ctypes.c_int32
 
 # name -> (restype, argtypes)
 SIGNATURES = {
+    "pj_dataset_join": (_i32, [_vp, _i32, _i32, _i32, ctypes.POINTER(pj_dsjoin_opts),
+                               ctypes.POINTER(pj_pairs), ctypes.POINTER(pj_dsjoin_stats)]),
     "pj_estimate_join": (_i32, [_vp, _i32, _i32, _i32, _vp, ctypes.POINTER(pj_estimate)]),
     "pj_create": (_i32, [ctypes.POINTER(pj_config), ctypes.POINTER(_vp)]),
     "pj_destroy": (_i32, [_vp]),
@@ -299,6 +322,24 @@ def pj_join_intersects_ex(ctx, a: int, b: int, cand=None, cand_offsets=None, sel
                                       _stream_ptr(stream), ctypes.byref(res))
     _check(ctx, rc)
     return res
+
+
+def pj_dataset_join(ctx, a: int, b: int, self_join=False, width=0, leaf_size=0,
+                    predicate="intersects", materialize="estimated", fixed_slots=0, grid=0):
+    """The dataset-level join (one BVH per dataset, every edge traced, pairs
+    deduplicated by the chosen materialisation).  Returns (pairs K x 2 int32
+    sorted, stats dict)."""
+    opts = pj_dsjoin_opts(int(width), int(leaf_size), int(PREDICATES.get(predicate, predicate)),
+                          int(MATERIALIZE.get(materialize, materialize)), int(fixed_slots),
+                          int(grid), 1)
+    res, st = pj_pairs(), pj_dsjoin_stats()
+    _check(ctx, load().pj_dataset_join(ctx, a, b, int(bool(self_join)), ctypes.byref(opts),
+                                       ctypes.byref(res), ctypes.byref(st)))
+    try:
+        pairs = pairs_to_numpy(res)
+    finally:
+        pj_free_pairs(ctx, res)
+    return pairs, {k: getattr(st, k) for k, _ in pj_dsjoin_stats._fields_}
 
 
 def pj_estimate_join(ctx, a: int, b: int, grid: int = 16, cells: bool = False):
