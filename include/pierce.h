@@ -338,6 +338,59 @@ pj_status pj_join_intersects_noalloc(pj_ctx *ctx, pj_dataset a, pj_dataset b,
                                      int64_t *d_count, void *cuda_stream);
 
 /* --------------------------------------------------------------------------
+ * Out-of-core execution by grid tiling (paper Sec. 3.6, "Out-of-GPU-core
+ * execution")
+ * ------------------------------------------------------------------------ */
+
+/* Meshes in host memory, in the layout of pj_load_meshes. */
+typedef struct {
+  const float *xyz;              /* n_verts x 3, integer valued in [0, 2^18)  */
+  const int32_t *tris;           /* n_tris x 3, mesh-local vertex ids          */
+  const int64_t *mesh_vert_off;  /* n_meshes + 1                               */
+  const int64_t *mesh_tri_off;   /* n_meshes + 1                               */
+  int64_t n_meshes;
+} pj_host_meshes;
+
+typedef struct {
+  int64_t device_budget;    /* device bytes one cell's meshes and BVHs may
+                               take (0: a quarter of the free memory)        */
+  int32_t grid;             /* cells per axis (0: the smallest power of two,
+                               at most 16, whose cells fit the budget)       */
+  int32_t width;            /* per-cell BVH shape (0: 4)                     */
+  int32_t leaf_size;        /* (0: 2)                                        */
+  int32_t out_host;         /* 1: pairs in library-owned host memory          */
+  pj_join_opts join;        /* each cell's join (predicate, leaf mode, ...)  */
+} pj_tiled_opts;
+
+typedef struct {
+  int32_t grid;             /* cells per axis used                           */
+  int32_t reserved;
+  int64_t cells_joined;     /* cells holding meshes of both datasets         */
+  int64_t mesh_copies;      /* meshes uploaded, replicas across cells included */
+  int64_t max_cell_bytes;   /* largest cell's estimated device footprint     */
+  int64_t pairs_in_cells;   /* pairs the cells reported, before each pair is
+                               kept in the one cell that holds its reference
+                               point                                          */
+  float ms_total;           /* wall time of the whole join                   */
+  float ms_gather;          /* host time gathering cells (overlapped)        */
+  float ms_device;          /* load, BVH build and join of the cells         */
+  float reserved2;
+} pj_tiled_stats;
+
+/* A join of two datasets that need not fit in device memory: a coarse grid
+ * over both datasets' box, each mesh copied to every cell its closed box
+ * touches, the cells loaded, indexed and joined one after another with the
+ * same kernels as pj_join_intersects_ex (the next cell is gathered on the
+ * host while the current one runs).  A pair is kept only in the cell that
+ * holds the lower corner of its two boxes' intersection, a point of both
+ * boxes, so every pair is reported exactly once.  Global mesh ids, sorted.
+ * self_join: b is ignored (a with itself, pairs i < j).  A mesh larger than
+ * the budget fails with PJ_ERR_NO_MEMORY.  Synchronous. */
+pj_status pj_join_tiled(pj_ctx *ctx, const pj_host_meshes *a, const pj_host_meshes *b,
+                        int32_t self_join, const pj_tiled_opts *opts, pj_pairs *out,
+                        pj_tiled_stats *stats);
+
+/* --------------------------------------------------------------------------
  * Dataset-level join (the paper's formulation, Sec. 3.1-3.5)
  * ------------------------------------------------------------------------ */
 

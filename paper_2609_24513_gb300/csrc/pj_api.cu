@@ -336,7 +336,7 @@ void free_bvh(Bvh &b) {
   b = Bvh();
 }
 
-static void free_dataset(Dataset *d) {
+void free_dataset(Dataset *d) {
   for (auto &kv : d->bvhs) free_bvh(kv.second);
   for (auto &kv : d->dbvhs) free_bvh(kv.second);
   cudaFree(d->d_xyz);
@@ -363,7 +363,7 @@ struct Tmp {
   }
 };
 
-static pj_status load_impl(Ctx *ctx, const float *xyz, int64_t V,
+pj_status load_impl(Ctx *ctx, const float *xyz, int64_t V,
                            const int32_t *tris, int64_t F, const int64_t *voff,
                            const int64_t *toff, int64_t M, int dev_ptrs,
                            Dataset *d) {
@@ -697,6 +697,20 @@ pj_status pj_join_intersects_noalloc(pj_ctx *h, pj_dataset a, pj_dataset b,
   cudaSetDevice(ctx->device);
   return run_join_noalloc(ctx, A, B, d_cand, n_cand, d_flags, d_pairs, d_count,
                           stream ? (cudaStream_t)stream : ctx->stream);
+}
+
+pj_status pj_join_tiled(pj_ctx *h, const pj_host_meshes *a, const pj_host_meshes *b,
+                        int32_t self_join, const pj_tiled_opts *opts, pj_pairs *out,
+                        pj_tiled_stats *stats) {
+  Ctx *ctx = reinterpret_cast<Ctx *>(h);
+  if (!ctx || !out || !a || (!self_join && !b)) return PJ_ERR_INVALID_ARG;
+  std::lock_guard<std::mutex> lk(ctx->mu);
+  clear_err(ctx);
+  memset(out, 0, sizeof(*out));
+  cudaSetDevice(ctx->device);
+  pj_tiled_opts o{};
+  if (opts) o = *opts;
+  return run_join_tiled(ctx, a, b, self_join, &o, out, stats);
 }
 
 pj_status pj_dataset_join(pj_ctx *h, pj_dataset a, pj_dataset b, int32_t self_join,

@@ -190,6 +190,14 @@ pj_status run_join(Ctx *ctx, Dataset *A, Dataset *B, const int32_t *cand,
                    pj_pairs *out, bool safe = false);
 pj_status run_estimate(Ctx *ctx, Dataset *A, Dataset *B, int G, double *cells_out,
                        pj_estimate *out, cudaStream_t s);
+// load meshes (host or device arrays) into *d, and free a dataset's buffers
+pj_status load_impl(Ctx *ctx, const float *xyz, int64_t V, const int32_t *tris, int64_t F,
+                    const int64_t *voff, const int64_t *toff, int64_t M, int dev_ptrs,
+                    Dataset *d);
+void free_dataset(Dataset *d);
+pj_status run_join_tiled(Ctx *ctx, const pj_host_meshes *A, const pj_host_meshes *B,
+                         int self_join, const pj_tiled_opts *o, pj_pairs *out,
+                         pj_tiled_stats *stats);
 pj_status run_dataset_join(Ctx *ctx, Dataset *A, Dataset *B, int self_join,
                            const pj_dsjoin_opts *o, pj_pairs *out, pj_dsjoin_stats *stats,
                            cudaStream_t s);

@@ -138,6 +138,26 @@ class pj_dsjoin_stats(ctypes.Structure):
                 ("ms_trace", ctypes.c_float), ("ms_materialize", ctypes.c_float)]
 
 
+class pj_host_meshes(ctypes.Structure):
+    _fields_ = [("xyz", ctypes.c_void_p), ("tris", ctypes.c_void_p),
+                ("mesh_vert_off", ctypes.c_void_p), ("mesh_tri_off", ctypes.c_void_p),
+                ("n_meshes", ctypes.c_int64)]
+
+
+class pj_tiled_opts(ctypes.Structure):
+    _fields_ = [("device_budget", ctypes.c_int64), ("grid", ctypes.c_int32),
+                ("width", ctypes.c_int32), ("leaf_size", ctypes.c_int32),
+                ("out_host", ctypes.c_int32), ("join", pj_join_opts)]
+
+
+class pj_tiled_stats(ctypes.Structure):
+    _fields_ = [("grid", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("cells_joined", ctypes.c_int64), ("mesh_copies", ctypes.c_int64),
+                ("max_cell_bytes", ctypes.c_int64), ("pairs_in_cells", ctypes.c_int64),
+                ("ms_total", ctypes.c_float), ("ms_gather", ctypes.c_float),
+                ("ms_device", ctypes.c_float), ("reserved2", ctypes.c_float)]
+
+
 # pj_dsjoin_opts.materialize (the paper's strategies, Sec. 3.5)
 PJ_MAT_ESTIMATED, PJ_MAT_TWO_PASS, PJ_MAT_FIXED = range(3)
 MATERIALIZE = {"estimated": 0, "two_pass": 1, "fixed": 2}
@@ -148,6 +168,9 @@ _i32 = ctypes.c_int32
 
 # name -> (restype, argtypes)
 SIGNATURES = {
+    "pj_join_tiled": (_i32, [_vp, ctypes.POINTER(pj_host_meshes), ctypes.POINTER(pj_host_meshes),
+                             _i32, ctypes.POINTER(pj_tiled_opts), ctypes.POINTER(pj_pairs),
+                             ctypes.POINTER(pj_tiled_stats)]),
     "pj_dataset_join": (_i32, [_vp, _i32, _i32, _i32, ctypes.POINTER(pj_dsjoin_opts),
                                ctypes.POINTER(pj_pairs), ctypes.POINTER(pj_dsjoin_stats)]),
     "pj_estimate_join": (_i32, [_vp, _i32, _i32, _i32, _vp, ctypes.POINTER(pj_estimate)]),
@@ -322,6 +345,38 @@ def pj_join_intersects_ex(ctx, a: int, b: int, cand=None, cand_offsets=None, sel
                                       _stream_ptr(stream), ctypes.byref(res))
     _check(ctx, rc)
     return res
+
+
+def _host_meshes(ds):
+    xyz = np.ascontiguousarray(ds.xyz, dtype=np.float32)
+    tris = np.ascontiguousarray(ds.tris, dtype=np.int32)
+    voff = np.ascontiguousarray(ds.voff, dtype=np.int64)
+    toff = np.ascontiguousarray(ds.toff, dtype=np.int64)
+    keep = (xyz, tris, voff, toff)
+    return pj_host_meshes(xyz.ctypes.data, tris.ctypes.data, voff.ctypes.data,
+                          toff.ctypes.data, len(voff) - 1), keep
+
+
+def pj_join_tiled(ctx, dsA, dsB=None, self_join=False, device_budget=0, grid=0, width=0,
+                  leaf_size=0, **join_kw):
+    """Out-of-core join of two host datasets (objects with xyz/tris/voff/toff)
+    by grid tiling.  join_kw: pj_join_opts fields for each cell's join
+    (predicate, leaf_mode, ...).  Returns (pairs K x 2 int32 sorted, stats)."""
+    ha, keep_a = _host_meshes(dsA)
+    hb, keep_b = _host_meshes(dsB if dsB is not None else dsA)
+    jo = pj_join_opts()
+    for k, v in join_kw.items():
+        setattr(jo, k, int(PREDICATES.get(v, v)) if k == "predicate" else int(v))
+    opts = pj_tiled_opts(int(device_budget), int(grid), int(width), int(leaf_size), 1, jo)
+    res, st = pj_pairs(), pj_tiled_stats()
+    _check(ctx, load().pj_join_tiled(ctx, ctypes.byref(ha), ctypes.byref(hb), int(bool(self_join)),
+                                     ctypes.byref(opts), ctypes.byref(res), ctypes.byref(st)))
+    try:
+        pairs = pairs_to_numpy(res)
+    finally:
+        pj_free_pairs(ctx, res)
+    del keep_a, keep_b
+    return pairs, {k: getattr(st, k) for k, _ in pj_tiled_stats._fields_}
 
 
 def pj_dataset_join(ctx, a: int, b: int, self_join=False, width=0, leaf_size=0,

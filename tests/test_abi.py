@@ -50,7 +50,8 @@ def test_struct_sizes_match_header_layout():
 
 _STRUCTS = ("pj_config", "pj_bvh_params", "pj_join_opts", "pj_pairs", "pj_counters",
             "pj_dataset_info", "pj_tune_space", "pj_tune_entry", "pj_query", "pj_query_stats",
-            "pj_estimate", "pj_dsjoin_opts", "pj_dsjoin_stats")
+            "pj_estimate", "pj_dsjoin_opts", "pj_dsjoin_stats", "pj_host_meshes",
+            "pj_tiled_opts", "pj_tiled_stats")
 
 
 def test_struct_layout_matches_the_c_compiler(tmp_path):
