@@ -411,6 +411,19 @@ __device__ __forceinline__ void load_slot(const float *nodes, uint32_t node, int
   child = __float_as_uint(v.z);
 }
 
+// Open (strict) overlap on every axis.  Exact for the crossing traversal:
+// if on some axis the boxes of a segment (or of a subtree's segments) and of
+// a triangle only touch at a value c, a strict crossing point would have
+// coordinate c, an extreme of both the open segment and the open triangle,
+// which forces both into the plane at c -- a coplanar configuration the
+// strict test rejects.  So boxes that only touch hold no crossing, and
+// pruning them loses nothing (pinned on the CPU against the oracle's strict
+// predicate on configurations full of exact contacts).
+__device__ __forceinline__ bool overlap_open(const Box &a, const Box &b) {
+  return a.lo.x < b.hi.x && b.lo.x < a.hi.x && a.lo.y < b.hi.y && b.lo.y < a.hi.y &&
+         a.lo.z < b.hi.z && b.lo.z < a.hi.z;
+}
+
 __device__ __forceinline__ bool overlap(const Box &a, const Box &b) {
   return a.lo.x <= b.hi.x && b.lo.x <= a.hi.x && a.lo.y <= b.hi.y && b.lo.y <= a.hi.y &&
          a.lo.z <= b.hi.z && b.lo.z <= a.hi.z;
@@ -2057,17 +2070,17 @@ __global__ void __launch_bounds__(128, 4) k_stream(StreamArgs P) {
             ehi[k] = mkf3(fmaxf(pp.x, qq.x), fmaxf(pp.y, qq.y), fmaxf(pp.z, qq.z));
             if (!((own >> k) & 1)) continue;
             lc.slab += 1;
-            if (!(elo[k].x > thi.x || tlo.x > ehi[k].x || elo[k].y > thi.y || tlo.y > ehi[k].y ||
-                  elo[k].z > thi.z || tlo.z > ehi[k].z))
-              ek |= 1u << k;
+            if (!(elo[k].x >= thi.x || tlo.x >= ehi[k].x || elo[k].y >= thi.y ||
+                  tlo.y >= ehi[k].y || elo[k].z >= thi.z || tlo.z >= ehi[k].z))
+              ek |= 1u << k;  // open overlap (exact for crossings, see overlap_open)
           }
           for (int t = 0; ek && t < nt; ++t) {
             const float *tp = tbx + 6 * t;
             const float t0 = tp[0], t1 = tp[1], t2 = tp[2], t3 = tp[3], t4 = tp[4], t5 = tp[5];
 #pragma unroll
             for (int k = 0; k < 3; ++k) {
-              if (((ek >> k) & 1) && !(t0 > ehi[k].x || elo[k].x > t3 || t1 > ehi[k].y ||
-                                       elo[k].y > t4 || t2 > ehi[k].z || elo[k].z > t5))
+              if (((ek >> k) & 1) && !(t0 >= ehi[k].x || elo[k].x >= t3 || t1 >= ehi[k].y ||
+                                       elo[k].y >= t4 || t2 >= ehi[k].z || elo[k].z >= t5))
                 mask |= 1u << (k * L + t);
             }
           }
@@ -2195,7 +2208,7 @@ __global__ void __launch_bounds__(128, 4) k_stream(StreamArgs P) {
           ba.hi = mkf3(a1.x, a1.y, a1.z);
           bb.lo = add(mkf3(b0.x, b0.y, b0.z), off);
           bb.hi = add(mkf3(b1.x, b1.y, b1.z), off);
-          if (overlap(ba, bb)) {
+          if (overlap_open(ba, bb)) {  // crossings only (parity runs apart)
             const uint2 t = make_task(ra, ba, rb, bb);
             ent = make_uint4((uint32_t)idx, t.x, t.y, 0u);
             P.cbase[idx] = make_int2(__float_as_int(ta), __float_as_int(tbs));
@@ -2381,7 +2394,7 @@ __global__ void __launch_bounds__(128, 4) k_stream(StreamArgs P) {
         for (int m = 0; m < MB; ++m) {
           if (m >= nbl) break;
           if (xb && bwd[m] == kEmpty) continue;
-          if (!overlap(ba, bbx[m])) continue;
+          if (!overlap_open(ba, bbx[m])) continue;
           const bool lb = xb ? (bwd[m] & kLeafBit) != 0 : (t.z & kLeafBit) != 0;
           const int k = ia * nbl + m;
           if (la && lb) lmask |= 1u << k;
