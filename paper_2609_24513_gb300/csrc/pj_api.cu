@@ -503,7 +503,46 @@ pj_status load_impl(Ctx *ctx, const float *xyz, int64_t V,
   d->h_aabb.resize(6 * (size_t)M);
   if (M > 0)
     PJ_CK(cudaMemcpy(d->h_aabb.data(), d->d_aabb, sizeof(float) * 6 * M, cudaMemcpyDeviceToHost));
+  // the admission grid: per cell the meshes whose box touches it, then the
+  // summed-area table of those counts
+  const int G = kOccG, G1 = kOccG + 1;
+  const double cw = 262144.0 / G;
+  std::vector<int64_t> cnt((size_t)G * G * G, 0);
+  for (int64_t m = 0; m < M; ++m) {
+    int lo[3], hi[3];
+    for (int k = 0; k < 3; ++k) {
+      lo[k] = std::min(G - 1, std::max(0, (int)(d->h_aabb[6 * m + k] / cw)));
+      hi[k] = std::min(G - 1, std::max(0, (int)(d->h_aabb[6 * m + 3 + k] / cw)));
+    }
+    for (int x = lo[0]; x <= hi[0]; ++x)
+      for (int y = lo[1]; y <= hi[1]; ++y)
+        for (int z = lo[2]; z <= hi[2]; ++z) cnt[((size_t)x * G + y) * G + z] += 1;
+  }
+  d->occ_sat.assign((size_t)G1 * G1 * G1, 0);
+  auto S = [&](int x, int y, int z) -> int64_t & { return d->occ_sat[((size_t)x * G1 + y) * G1 + z]; };
+  for (int x = 1; x <= G; ++x)
+    for (int y = 1; y <= G; ++y)
+      for (int z = 1; z <= G; ++z)
+        S(x, y, z) = cnt[((size_t)(x - 1) * G + (y - 1)) * G + (z - 1)] + S(x - 1, y, z) +
+                     S(x, y - 1, z) + S(x, y, z - 1) - S(x - 1, y - 1, z) - S(x - 1, y, z - 1) -
+                     S(x, y - 1, z - 1) + S(x - 1, y - 1, z - 1);
   return PJ_OK;
+}
+
+int64_t window_mesh_bound(const Dataset *d, const int32_t *wlo, const int32_t *whi) {
+  const int G = kOccG, G1 = kOccG + 1;
+  if (d->occ_sat.size() != (size_t)G1 * G1 * G1) return d->M;
+  const double cw = 262144.0 / G;
+  int a[3], b[3];
+  for (int k = 0; k < 3; ++k) {
+    a[k] = std::min(G - 1, std::max(0, (int)(wlo[k] / cw)));
+    b[k] = std::min(G - 1, std::max(0, (int)(whi[k] / cw))) + 1;
+  }
+  auto S = [&](int x, int y, int z) { return d->occ_sat[((size_t)x * G1 + y) * G1 + z]; };
+  const int64_t sum = S(b[0], b[1], b[2]) - S(a[0], b[1], b[2]) - S(b[0], a[1], b[2]) -
+                      S(b[0], b[1], a[2]) + S(a[0], a[1], b[2]) + S(a[0], b[1], a[2]) +
+                      S(b[0], a[1], a[2]) - S(a[0], a[1], a[2]);
+  return std::min(sum, d->M);
 }
 
 }  // namespace pj

@@ -73,8 +73,16 @@ struct Dataset {
   // one BVH over all of the dataset's triangles per (W, L), for the
   // dataset-level join; its triangle records carry the owning mesh id
   std::map<std::pair<int, int>, Bvh> dbvhs;
+  // serving admission: summed-area table over a kOccG^3 grid of the 2^18
+  // cube of the number of meshes whose box touches each cell ((kOccG + 1)^3
+  // entries), so that a window's mesh count has an O(1) upper bound
+  std::vector<int64_t> occ_sat;
   int64_t bytes = 0;
 };
+
+constexpr int kOccG = 32;  // cells per axis of the admission grid (8,192 grid units)
+// upper bound on the meshes of d whose closed box meets [lo, hi] (at most M)
+int64_t window_mesh_bound(const Dataset *d, const int32_t *lo, const int32_t *hi);
 
 // Counter slots (match pj_counters order)
 enum {

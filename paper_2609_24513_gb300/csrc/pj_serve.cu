@@ -3,8 +3,10 @@
 //
 // The paper evaluates one join at a time (Sec. 4); serving adds the request
 // loop around the same refinement.  A query selects, on each side, the meshes
-// whose closed box meets its window (host side, from the boxes computed at
-// load time) and asks for the intersecting pairs among them.
+// whose closed box meets its window and asks for the intersecting pairs among
+// them.  Admission bounds a query's device bytes in O(1) from a grid of mesh
+// counts built at load time; the selection itself runs on the device, per
+// batch (one block per query and side, in mesh order).
 //
 // Continuous batching: each serving stream has a worker thread.  A free
 // worker takes the oldest pending query and every following pending query on
@@ -37,7 +39,7 @@ struct Query {
   pj_ticket id = 0;
   Dataset *A = nullptr, *B = nullptr;
   int self_join = 0;
-  std::vector<int32_t> selA, selB;
+  int32_t lo[3], hi[3];   // window (closed, grid units)
   int64_t est_bytes = 0;
   pj_query_stats st{};
   std::vector<int32_t> pairs;
@@ -61,15 +63,77 @@ struct Serve {
   std::map<const Dataset *, int64_t> uses;  // unpolled queries per dataset
 };
 
-// warp per selected A mesh: count (EMIT = false) or emit (EMIT = true) the
-// selected B meshes of the same query whose closed boxes meet it
+// block per (query, side): the ids of the side's meshes whose closed box
+// meets the query's window, in id order, to sel[q * M + k], and their number
+// to cnt[side * nq + q] (a self join selects one side, read for both)
+__global__ void __launch_bounds__(256) k_select(const float *aabbA, int64_t MA, const float *aabbB,
+                                                int64_t MB, const int32_t *win, int nq,
+                                                int self_join, int32_t *selA, int32_t *selB,
+                                                int64_t *cnt) {
+  const int q = blockIdx.x, side = blockIdx.y;
+  if (side == 1 && self_join) return;
+  const int64_t M = side ? MB : MA;
+  const float *box = side ? aabbB : aabbA;
+  int32_t *sel = (side ? selB : selA) + (int64_t)q * M;
+  const int32_t *w = win + 6 * q;
+  const float lx = (float)w[0], ly = (float)w[1], lz = (float)w[2];
+  const float hx = (float)w[3], hy = (float)w[4], hz = (float)w[5];
+  __shared__ int ws[8];
+  __shared__ int64_t s_run;
+  if (threadIdx.x == 0) s_run = 0;
+  __syncthreads();
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  for (int64_t base = 0; base < M; base += 256) {
+    const int64_t m = base + threadIdx.x;
+    bool in = false;
+    if (m < M) {
+      const float *b = box + 6 * m;
+      in = b[0] <= hx && lx <= b[3] && b[1] <= hy && ly <= b[4] && b[2] <= hz && lz <= b[5];
+    }
+    const unsigned bal = __ballot_sync(0xffffffffu, in);
+    if (lane == 0) ws[wid] = __popc(bal);
+    __syncthreads();
+    int before = 0, tot = 0;
+    for (int k = 0; k < 8; ++k) {
+      before += k < wid ? ws[k] : 0;
+      tot += ws[k];
+    }
+    const int64_t run = s_run;
+    if (in) sel[run + before + __popc(bal & ((1u << lane) - 1u))] = (int32_t)m;
+    __syncthreads();
+    if (threadIdx.x == 0) s_run = run + tot;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) cnt[side * nq + q] = s_run;
+}
+
+// one block: offA / offB = exclusive prefixes of the per-query counts
+// (nq + 1 entries each; a self join's B side is its A side)
+__global__ void k_sel_offsets(const int64_t *cnt, int nq, int self_join, int64_t *offA,
+                              int64_t *offB) {
+  if (threadIdx.x != 0) return;
+  int64_t a = 0, b = 0;
+  for (int q = 0; q < nq; ++q) {
+    offA[q] = a;
+    offB[q] = b;
+    a += cnt[q];
+    b += cnt[(self_join ? 0 : nq) + q];
+  }
+  offA[nq] = a;
+  offB[nq] = b;
+}
+
+// warp per selected A mesh g (over all queries): count (EMIT = false) or
+// emit (EMIT = true) the same query's selected B meshes whose closed boxes
+// meet it, in B order -- so candidates come out query by query, sorted
 template <bool EMIT>
-__global__ void k_mbb_subset(const float *aabbA, const float *aabbB, const int32_t *selA,
-                             const int32_t *selB, const int64_t *offA, const int64_t *offB,
-                             int nq, int64_t nA, int self_join, int64_t *counts,
+__global__ void k_mbb_subset(const float *aabbA, int64_t MA, const float *aabbB, int64_t MB,
+                             const int32_t *selA, const int32_t *selB, const int64_t *offA,
+                             const int64_t *cntB, int nq, int self_join, int64_t *counts,
                              const int64_t *offs, int32_t *cand) {
   const int lane = threadIdx.x & 31;
   const int64_t warps = (int64_t)gridDim.x * (blockDim.x / 32);
+  const int64_t nA = offA[nq];
   for (int64_t g = blockIdx.x * (int64_t)(blockDim.x / 32) + (threadIdx.x >> 5); g < nA;
        g += warps) {
     int lo = 0, hi = nq - 1;  // query of g: largest q with offA[q] <= g
@@ -78,15 +142,17 @@ __global__ void k_mbb_subset(const float *aabbA, const float *aabbB, const int32
       if (offA[mid] <= g) lo = mid; else hi = mid - 1;
     }
     const int q = lo;
-    const int32_t i = selA[g];
+    const int32_t i = selA[(int64_t)q * MA + (g - offA[q])];
     const float *a = aabbA + 6 * (int64_t)i;
+    const int32_t *sb = self_join ? selA + (int64_t)q * MA : selB + (int64_t)q * MB;
+    const int64_t nb = cntB[q];
     int64_t cnt = 0, pos = EMIT ? offs[g] : 0;
-    for (int64_t k0 = offB[q]; k0 < offB[q + 1]; k0 += 32) {
+    for (int64_t k0 = 0; k0 < nb; k0 += 32) {
       const int64_t k = k0 + lane;
       bool ov = false;
       int32_t j = 0;
-      if (k < offB[q + 1]) {
-        j = selB[k];
+      if (k < nb) {
+        j = sb[k];
         const float *b = aabbB + 6 * (int64_t)j;
         ov = (!self_join || j > i) && a[0] <= b[3] && b[0] <= a[3] && a[1] <= b[4] &&
              b[1] <= a[4] && a[2] <= b[5] && b[2] <= a[5];
@@ -102,6 +168,13 @@ __global__ void k_mbb_subset(const float *aabbA, const float *aabbB, const int32
     }
     if (!EMIT && lane == 0) counts[g] = cnt;
   }
+}
+
+// per query: the position of its first candidate (the scan at its first
+// selected A mesh; past the last one, the total)
+__global__ void k_query_starts(const int64_t *offs, const int64_t *offA, int nq, int64_t *qcand) {
+  for (int q = blockIdx.x * blockDim.x + threadIdx.x; q <= nq; q += gridDim.x * blockDim.x)
+    qcand[q] = offs[offA[q]];
 }
 
 // per-query number of intersecting candidates
@@ -124,77 +197,70 @@ __global__ void k_query_counts(const uint8_t *flags, const int64_t *cand_off, in
   }
 }
 
-__global__ void k_gather_i64(const int64_t *src, const int64_t *idx, int n, int64_t *dst) {
-  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x)
-    dst[k] = src[idx[k]];
-}
-
-// Run one batch on the worker's stream and scratch.  Fills each query's
-// pairs and counts, or its status on failure.
+// Run one batch on the worker's stream and scratch: window selection, box
+// filter and refinement on the device, with one host synchronisation after
+// the candidates are counted and one at the end.  Fills each query's pairs
+// and counts, or returns the status of a failure.
 static pj_status run_batch(Ctx *ctx, Exec *ex, cudaStream_t s,
                            std::vector<std::shared_ptr<Query>> &batch) {
   Dataset *A = batch[0]->A, *B = batch[0]->B;
   const int self_join = batch[0]->self_join;
   const int nq = (int)batch.size();
-  std::vector<int64_t> offA(nq + 1, 0), offB(nq + 1, 0);
-  for (int q = 0; q < nq; ++q) {
-    offA[q + 1] = offA[q] + (int64_t)batch[q]->selA.size();
-    offB[q + 1] = offB[q] + (int64_t)batch[q]->selB.size();
-  }
-  const int64_t nA = offA[nq], nB = offB[nq];
-  std::vector<int32_t> selA, selB;
-  selA.reserve(nA);
-  selB.reserve(nB);
-  for (auto &q : batch) {
-    selA.insert(selA.end(), q->selA.begin(), q->selA.end());
-    selB.insert(selB.end(), q->selB.begin(), q->selB.end());
-  }
+  const int64_t MA = A->M, MB = B->M;
   pj_status st;
   auto get = [&](const char *name, size_t bytes) { return ws_get(ctx, name, bytes, &st); };
-  int32_t *d_selA = (int32_t *)get("srv_sel_a", 4 * (size_t)std::max<int64_t>(nA, 1));
-  int32_t *d_selB = (int32_t *)get("srv_sel_b", 4 * (size_t)std::max<int64_t>(nB, 1));
-  int64_t *d_offA = (int64_t *)get("srv_off_a", 8 * (size_t)(nq + 1));
-  int64_t *d_offB = (int64_t *)get("srv_off_b", 8 * (size_t)(nq + 1));
-  int64_t *d_counts = (int64_t *)get("srv_counts", 8 * (size_t)std::max<int64_t>(nA, 1));
-  int64_t *d_offs = (int64_t *)get("srv_offs", 8 * (size_t)std::max<int64_t>(nA, 1) + 8);
-  int64_t *d_small = (int64_t *)get("srv_small", 8 * (size_t)(3 * (nq + 1) + 8));
-  if (!d_selA || !d_selB || !d_offA || !d_offB || !d_counts || !d_offs || !d_small) return st;
-  int64_t *d_total = d_small, *d_qcand = d_small + 1, *d_qidx = d_qcand + (nq + 1),
-          *d_qcount = d_qidx + (nq + 1);
-  PJ_CK(cudaMemcpyAsync(d_selA, selA.data(), 4 * nA, cudaMemcpyHostToDevice, s));
-  PJ_CK(cudaMemcpyAsync(d_selB, selB.data(), 4 * nB, cudaMemcpyHostToDevice, s));
-  PJ_CK(cudaMemcpyAsync(d_offA, offA.data(), 8 * (nq + 1), cudaMemcpyHostToDevice, s));
-  PJ_CK(cudaMemcpyAsync(d_offB, offB.data(), 8 * (nq + 1), cudaMemcpyHostToDevice, s));
-  const int nb = (int)std::max<int64_t>(1, std::min<int64_t>((nA + 7) / 8, (int64_t)ctx->num_sms * 64));
-  if (nA > 0)
-    k_mbb_subset<false><<<nb, 256, 0, s>>>(A->d_aabb, B->d_aabb, d_selA, d_selB, d_offA, d_offB,
-                                           nq, nA, self_join, d_counts, nullptr, nullptr);
-  ctx->launches += nA > 0 ? 1 : 0;
-  if (nA > 0 && (st = scan_i64(ctx, d_counts, d_offs, nA, d_total, s)) != PJ_OK) return st;
-  if (nA == 0) PJ_CK(cudaMemsetAsync(d_total, 0, 8, s));
-  int64_t *h = (int64_t *)ex->h_pinned;
-  PJ_CK(cudaMemcpyAsync(h, d_total, 8, cudaMemcpyDeviceToHost, s));
+  // selection slots per query, counts of selected A meshes' candidates
+  const int64_t capA = (int64_t)nq * MA;
+  int32_t *d_win = (int32_t *)get("srv_win", sizeof(int32_t) * 6 * (size_t)nq);
+  int32_t *d_selA = (int32_t *)get("srv_sel_a", 4 * (size_t)std::max<int64_t>(capA, 1));
+  int32_t *d_selB = self_join ? d_selA
+                              : (int32_t *)get("srv_sel_b", 4 * (size_t)std::max<int64_t>((int64_t)nq * MB, 1));
+  int64_t *d_small = (int64_t *)get("srv_small", 8 * (size_t)(6 * (nq + 1) + 8));
+  int64_t *d_counts = (int64_t *)get("srv_counts", 8 * (size_t)(capA + 1));
+  int64_t *d_offs = (int64_t *)get("srv_offs", 8 * (size_t)(capA + 1));
+  if (!d_win || !d_selA || !d_selB || !d_small || !d_counts || !d_offs) return st;
+  // per query: selection counts (2 nq), offsets (2 (nq + 1)), first
+  // candidate (nq + 1), pair count (nq); then the candidate total
+  int64_t *d_cnt = d_small, *d_offA = d_cnt + 2 * nq, *d_offB = d_offA + (nq + 1),
+          *d_qcand = d_offB + (nq + 1), *d_qcount = d_qcand + (nq + 1),
+          *d_total = d_qcount + nq;
+  std::vector<int32_t> win(6 * (size_t)nq);
+  for (int q = 0; q < nq; ++q)
+    for (int k = 0; k < 3; ++k) {
+      win[6 * q + k] = batch[q]->lo[k];
+      win[6 * q + 3 + k] = batch[q]->hi[k];
+    }
+  PJ_CK(cudaMemcpyAsync(d_win, win.data(), sizeof(int32_t) * 6 * nq, cudaMemcpyHostToDevice, s));
+  k_select<<<dim3(nq, 2), 256, 0, s>>>(A->d_aabb, MA, B->d_aabb, MB, d_win, nq, self_join, d_selA,
+                                       d_selB, d_cnt);
+  k_sel_offsets<<<1, 32, 0, s>>>(d_cnt, nq, self_join, d_offA, d_offB);
+  PJ_CK(cudaMemsetAsync(d_counts, 0, 8 * (size_t)(capA + 1), s));
+  const int nb = (int)std::max<int64_t>(1, std::min<int64_t>((capA + 7) / 8, (int64_t)ctx->num_sms * 64));
+  const int64_t *cntB = d_cnt + (self_join ? 0 : nq);
+  k_mbb_subset<false><<<nb, 256, 0, s>>>(A->d_aabb, MA, B->d_aabb, MB, d_selA, d_selB, d_offA,
+                                         cntB, nq, self_join, d_counts, nullptr, nullptr);
+  if ((st = scan_i64(ctx, d_counts, d_offs, capA + 1, d_total, s)) != PJ_OK) return st;
+  k_query_starts<<<1, 256, 0, s>>>(d_offs, d_offA, nq, d_qcand);
+  ctx->launches += 4;
+  PJ_CK(cudaGetLastError());
+  // one round trip: the candidate count, each query's first candidate and
+  // selection sizes
+  (void)ex;
+  std::vector<int64_t> qcand(nq + 1), cnt(2 * (size_t)nq);
+  PJ_CK(cudaMemcpyAsync(qcand.data(), d_qcand, 8 * (size_t)(nq + 1), cudaMemcpyDeviceToHost, s));
+  PJ_CK(cudaMemcpyAsync(cnt.data(), d_cnt, 8 * 2 * (size_t)nq, cudaMemcpyDeviceToHost, s));
   PJ_CK(cudaStreamSynchronize(s));
-  const int64_t C = h[0];
-  // candidate offsets of each query: the scan at its first selected A mesh
-  std::vector<int64_t> qidx(nq + 1);
-  for (int q = 0; q <= nq; ++q) qidx[q] = std::min(offA[q], std::max<int64_t>(nA - 1, 0));
+  const int64_t C = qcand[nq];
+  for (int q = 0; q < nq; ++q) {
+    batch[q]->st.n_a = cnt[q];
+    batch[q]->st.n_b = cnt[(self_join ? 0 : nq) + q];
+  }
   int32_t *d_cand = (int32_t *)get("srv_cand", 8 * (size_t)std::max<int64_t>(C, 1));
   if (!d_cand) return st;
-  if (C > 0)
-    k_mbb_subset<true><<<nb, 256, 0, s>>>(A->d_aabb, B->d_aabb, d_selA, d_selB, d_offA, d_offB,
-                                          nq, nA, self_join, nullptr, d_offs, d_cand);
-  ctx->launches += C > 0 ? 1 : 0;
-  std::vector<int64_t> qcand(nq + 1, 0);
-  if (nA > 0) {
-    PJ_CK(cudaMemcpyAsync(d_qidx, qidx.data(), 8 * (nq + 1), cudaMemcpyHostToDevice, s));
-    k_gather_i64<<<1, 256, 0, s>>>(d_offs, d_qidx, nq + 1, d_qcand);
-    PJ_CK(cudaMemcpyAsync(qcand.data(), d_qcand, 8 * (nq + 1), cudaMemcpyDeviceToHost, s));
-    PJ_CK(cudaStreamSynchronize(s));
-    for (int q = 0; q <= nq; ++q)
-      if (offA[q] >= nA) qcand[q] = C;  // queries with no selected A mesh at the end
-    qcand[nq] = C;
-    PJ_CK(cudaMemcpyAsync(d_qcand, qcand.data(), 8 * (nq + 1), cudaMemcpyHostToDevice, s));
+  if (C > 0) {
+    k_mbb_subset<true><<<nb, 256, 0, s>>>(A->d_aabb, MA, B->d_aabb, MB, d_selA, d_selB, d_offA,
+                                          cntB, nq, self_join, nullptr, d_offs, d_cand);
+    ctx->launches += 1;
   }
   for (auto &q : batch) q->st.t_launch = now_s();
   std::vector<int64_t> qcount(nq, 0);
@@ -340,17 +406,6 @@ void serve_stop(Ctx *ctx) {
   ctx->serve = nullptr;
 }
 
-static void select_meshes(const Dataset *D, const std::vector<float> &box, const int32_t *lo,
-                          const int32_t *hi, std::vector<int32_t> &out) {
-  out.clear();
-  for (int64_t m = 0; m < D->M; ++m) {
-    const float *b = &box[6 * m];
-    if (b[0] <= hi[0] && lo[0] <= b[3] && b[1] <= hi[1] && lo[1] <= b[4] && b[2] <= hi[2] &&
-        lo[2] <= b[5])
-      out.push_back((int32_t)m);
-  }
-}
-
 pj_status serve_submit(Ctx *ctx, Dataset *A, Dataset *B, const pj_query *q, pj_ticket *out) {
   if (A->bvhs.find(A->last_bvh) == A->bvhs.end() || B->bvhs.find(A->last_bvh) == B->bvhs.end())
     return fail(ctx, PJ_ERR_INVALID_ARG, "both datasets need a BVH of the same shape (pj_build_bvh)");
@@ -363,15 +418,17 @@ pj_status serve_submit(Ctx *ctx, Dataset *A, Dataset *B, const pj_query *q, pj_t
   qq->A = A;
   qq->B = B;
   qq->self_join = q->self_join;
-  if (A->h_aabb.empty() || B->h_aabb.empty()) return fail(ctx, PJ_ERR_INTERNAL, "no host boxes");
-  select_meshes(A, A->h_aabb, q->window_lo, q->window_hi, qq->selA);
-  if (A == B && q->self_join) qq->selB = qq->selA;
-  else select_meshes(B, B->h_aabb, q->window_lo, q->window_hi, qq->selB);
-  qq->st.n_a = (int64_t)qq->selA.size();
-  qq->st.n_b = (int64_t)qq->selB.size();
+  for (int k = 0; k < 3; ++k) {
+    qq->lo[k] = q->window_lo[k];
+    qq->hi[k] = q->window_hi[k];
+  }
+  // admission: an upper bound of each side's selection from the load-time
+  // grid of mesh counts (O(1); the exact selection runs on the device)
+  const int64_t na = window_mesh_bound(A, q->window_lo, q->window_hi);
+  const int64_t nb = (A == B && q->self_join) ? na : window_mesh_bound(B, q->window_lo, q->window_hi);
   // device bytes: every selected pair as a candidate (id pair, flag, output
   // pair), the selections, and the scans over them
-  qq->est_bytes = qq->st.n_a * qq->st.n_b * 17 + (qq->st.n_a + qq->st.n_b) * 24 + 4096;
+  qq->est_bytes = na * nb * 17 + (na + nb) * 24 + 4096;
   Serve *sv = ctx->serve;
   if (qq->est_bytes > sv->budget)
     return fail(ctx, PJ_ERR_BUSY, "the query needs more device memory than the serving budget");
