@@ -290,7 +290,8 @@ def run_ours(args, rank, world, local_rank):
     # CUDA events on the join's stream between the phases and around every
     # breadth-first launch)
     ctx.reset_counters()
-    keys = ("parity_ms", "front_ms", "tasks_ms", "refine_ms", "expand_ms", "leaf_ms")
+    keys = ("mbb_ms", "parity_ms", "front_ms", "tasks_ms", "refine_ms", "compact_ms", "expand_ms",
+            "leaf_ms", "device_ms")
     ph = {k: [] for k in keys}
     for _ in range(args.steps):
         flush.zero_()
@@ -357,7 +358,9 @@ def run_ours(args, rank, world, local_rank):
                              "achieved_gbs": per_step["bytes_fetched"] /
                              (phase_ms["refine_ms"] / 1000.0) / 1e9,
                              "parity_ms": phase_ms["parity_ms"], "front_ms": phase_ms["front_ms"],
-                             "tasks_ms": phase_ms["tasks_ms"]}},
+                             "tasks_ms": phase_ms["tasks_ms"], "mbb_ms": phase_ms["mbb_ms"],
+                             "compact_ms": phase_ms["compact_ms"],
+                             "join_ms_not_replayed": phase_ms["device_ms"]}},
             "e2e": line_e2e,
             "clocks": clk}
     if serving:

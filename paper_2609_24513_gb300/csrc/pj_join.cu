@@ -1799,6 +1799,17 @@ __device__ __forceinline__ unsigned *sq(const StreamArgs &P, int k) {
 template <int W>
 __host__ __device__ constexpr int stream_warp_bytes() { return StreamCfg<W>::warp_bytes; }
 
+// release store / acquire load at device scope: a queue slot's ready word
+// publishes the entry its lane wrote before it, without a full fence
+__device__ __forceinline__ void st_release(unsigned *p, unsigned v) {
+  asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+__device__ __forceinline__ unsigned ld_acquire(const unsigned *p) {
+  unsigned v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+
 __device__ __forceinline__ unsigned ld_vol(const unsigned *p) {
   return *reinterpret_cast<volatile const unsigned *>(p);
 }
@@ -1823,12 +1834,12 @@ __device__ __forceinline__ bool queue_push(const StreamArgs &P, const uint4 *src
     d->y = v.y;
     d->z = v.z;
   }
-  __threadfence();
+  // each lane publishes the slots it wrote (a release store orders that
+  // lane's entry before its ready word); no fence is needed before the
+  // count either: a consumer waits for each slot's ready word, which may
+  // become visible after the count
   for (int k = lane; k < n; k += 32)
-    *reinterpret_cast<volatile unsigned *>(&P.dq[base + k].w) =
-        leaves ? (kLeafEntry | src[k].w) : 1u;
-  // no fence needed before publishing: a consumer waits for each slot's
-  // ready flag, which may become visible after the count
+    st_release(&P.dq[base + k].w, leaves ? (kLeafEntry | src[k].w) : 1u);
   __syncwarp();
   if (lane == 0) atomicAdd(reinterpret_cast<int *>(sq(P, SQ_AVAIL)), n);
   return true;
@@ -2113,10 +2124,10 @@ __global__ void __launch_bounds__(128, 4) k_stream(StreamArgs P) {
     bool tpush = false, lpush = false, late = false;
     uint4 ent = make_uint4(0u, 0u, 0u, 0u);
     if (lane < k) {
-      volatile unsigned *rdy = reinterpret_cast<volatile unsigned *>(&P.dq[h + lane].w);
+      unsigned *rdy = &P.dq[h + lane].w;
       unsigned it = 0;
       unsigned w = 0;
-      while ((w = *rdy) == 0u) {
+      while ((w = ld_acquire(rdy)) == 0u) {  // acquire: the entry is visible after it
         if (++it >= P.spin_limit) {
           late = true;
           break;
@@ -2124,9 +2135,8 @@ __global__ void __launch_bounds__(128, 4) k_stream(StreamArgs P) {
         __nanosleep(64);
       }
       if (!late) {
-        __threadfence();
         ent = __ldcg(P.dq + h + lane);
-        *rdy = 0u;
+        *reinterpret_cast<volatile unsigned *>(rdy) = 0u;
         const bool alive = vflags[ent.x] == 0;
         lpush = alive && (w & kLeafEntry);
         tpush = alive && !(w & kLeafEntry);
@@ -2235,10 +2245,7 @@ __global__ void __launch_bounds__(128, 4) k_stream(StreamArgs P) {
         // entries it pushed itself might otherwise outlive every waiting warp
         int *avail = reinterpret_cast<int *>(sq(P, SQ_AVAIL));
         bool wait = atomicAdd(sq(P, SQ_HUNGRY), 1u) < P.hungry_max;
-        if (!wait) {
-          __threadfence();
-          wait = *reinterpret_cast<volatile int *>(avail) > 0;
-        }
+        if (!wait) wait = (int)ld_acquire(reinterpret_cast<const unsigned *>(avail)) > 0;
         unsigned nap = 128;
         for (unsigned it = 0; wait; ++it) {
           if (it >= P.spin_limit) {
@@ -2248,7 +2255,7 @@ __global__ void __launch_bounds__(128, 4) k_stream(StreamArgs P) {
           if (ld_vol(reinterpret_cast<const unsigned *>(Q.err)) != 0u) break;  // failing
           const int av = *reinterpret_cast<volatile int *>(avail);
           if (av > 0) {
-            const int want = min(av, Cf::NT);
+            const int want = min(av, Cf::NT);  // (2 NT measured slower: hoarding)
             if (atomicSub(avail, want) >= want) {
               h = atomicAdd(sq(P, SQ_HEAD), (unsigned)want);
               atomicAdd(sq(P, SQ_ACTIVE), 1u);
@@ -2257,12 +2264,11 @@ __global__ void __launch_bounds__(128, 4) k_stream(StreamArgs P) {
             }
             atomicAdd(avail, want);  // fewer were left: undo, retry
             nap = 64;
-          } else {
-            __threadfence();
-            if (ld_vol(sq(P, SQ_ACTIVE)) == 0u) {
-              __threadfence();
-              if (*reinterpret_cast<volatile int *>(avail) <= 0) break;  // nothing left: leave
-            }
+          } else if (ld_acquire(sq(P, SQ_ACTIVE)) == 0u) {
+            // a producer fences its pushes before it stops counting as
+            // active, so with no warp active an acquire read of the count
+            // sees everything published
+            if ((int)ld_acquire(reinterpret_cast<const unsigned *>(avail)) <= 0) break;  // leave
           }
           __nanosleep(nap);
           nap = min(nap * 2, 1024u);
