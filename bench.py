@@ -308,9 +308,11 @@ def run_ours(args, rank, world, local_rank):
     peak, peak_kind = measured_peaks()
     # kernel families of one step: (step ms, algorithmic bytes, launches)
     if args.front == "stream":
-        fam = {"k_stream": (phase_ms["front_ms"],
-                            per_step["bytes_expand"] + per_step["bytes_leaf"], 1),
-               "k_wave_parity+handover": (phase_ms["parity_ms"], per_step["bytes_parity"], 2)}
+        # k_stream also takes the long parity rays (bytes_tasks)
+        fam = {"k_stream": (phase_ms["front_ms"], per_step["bytes_expand"] + per_step["bytes_leaf"]
+                            + per_step["bytes_tasks"], 1),
+               "k_wave_parity": (phase_ms["parity_ms"],
+                                 per_step["bytes_parity"] - per_step["bytes_tasks"], 1)}
     elif args.front == "wave":
         levels = FRONT_LEVELS["wave"]
         fam = {"k_wave_expand": (phase_ms["expand_ms"], per_step["bytes_expand"], levels),

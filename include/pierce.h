@@ -191,7 +191,9 @@ typedef struct {
   uint64_t kernel_launches;     /* kernels launched by joins (host count)       */
   uint64_t tasks_spilled;       /* traversal tasks (streaming: and leaf pairs) handed to another warp or pass */
   uint64_t tasks_resumed;       /* of those, taken up by another warp or pass    */
-  uint64_t bytes_tasks;         /* of bytes_fetched: the per-warp passes        */
+  uint64_t bytes_tasks;         /* of bytes_fetched: the per-warp passes (with
+                                   the streaming front end: the long parity
+                                   rays its warps take, also in bytes_parity) */
   uint64_t bytes_parity;        /* of bytes_fetched: the parity rays            */
   uint64_t bytes_expand;        /* of bytes_fetched: breadth-first node pairs   */
   uint64_t bytes_leaf;          /* of bytes_fetched: breadth-first leaf pairs   */

@@ -1789,6 +1789,10 @@ struct StreamArgs {
   unsigned int spin_limit;  // bound on the polls of every wait (each sleeps <= 1 us)
   unsigned int hungry_max;  // warps that may wait for queued tasks
   long long give_after;     // SM cycles without new work that make a straggler
+  // parity rays over the per-thread node budget (w.q_par, w.q_par_n): one
+  // warp each, claimed at this position before the warp's first intake
+  unsigned int *q_par_pos;
+  int par_stack_cap;        // the rays' traversal stack, in the warp's own memory
 };
 
 // the launch's control word k
@@ -1818,6 +1822,9 @@ __device__ __forceinline__ unsigned ld_vol(const unsigned *p) {
 // item B); kLeafEntry | the leaf-queue counts word for a leaf pair
 // (candidate, first triangle of A's leaf, first triangle of B's leaf).
 constexpr unsigned kLeafEntry = 0x80000000u;
+
+// queue entries a waiting warp claims at least (while there are as many)
+constexpr int kClaimMin = 4;
 
 // give src[0, n) to the queue (all lanes; n > 0), tasks or (leaves) leaf
 // pairs; false if it is full
@@ -1903,6 +1910,58 @@ __global__ void __launch_bounds__(128, 4) k_stream(StreamArgs P) {
   bool peeked = false, peek_more = false;
   bool registered = true;  // counted in SQ_ACTIVE
   if (lane == 0) atomicAdd(sq(P, SQ_ACTIVE), 1u);
+
+  // The parity rays the per-thread kernel handed over: the longest rays,
+  // taken first, one warp each, so that they overlap the crossing traversal
+  // instead of forming a launch of their own.  The warp's stack, leaf queue
+  // and stage are still empty here; the ray traversal borrows them.
+  if (Q.q_par && Q.q_par_n && P.q_par_pos) {
+    const unsigned npar = min(*Q.q_par_n, Q.q_par_cap);
+    if (npar > 0) {
+      constexpr int extra = Cfg<W>::extra_bytes;
+      const int cap = min(P.par_stack_cap, (Cf::warp_bytes - extra) / 8 - 1);
+      WarpMem pm = carve<W>(reinterpret_cast<unsigned char *>(stk), cap);
+      Cnt pc;
+      for (int i = 0; i < C_WARP_NUM; ++i) pc.v[i] = 0;
+      for (;;) {
+        unsigned t = 0;
+        if (lane == 0) t = atomicAdd(P.q_par_pos, 1u);
+        t = __shfl_sync(FULL, t, 0);
+        if (t >= npar) break;
+        const uint4 e = Q.q_par[t];
+        const uint32_t c = e.x;
+        volatile uint8_t *flag = (Q.pflags ? Q.pflags : Q.flags) + c;
+        const int done = lane == 0 ? (int)*flag : 0;
+        if (__shfl_sync(FULL, done, 0)) continue;
+        const int ia = Q.cand[2 * (int64_t)c], ib = Q.cand[2 * (int64_t)c + 1];
+        const F3 off = cand_offset(Q, c);
+        // direction 0: B's representative vertex against A; 1: A's against B
+        const int r = e.z == 0u
+            ? pair_inside<W>(Q.B, ib, off, Q.A, ia, zero, pm, lane, cap, 32, pc)
+            : pair_inside<W>(Q.A, ia, zero, Q.B, ib, off, pm, lane, cap, 32, pc);
+        if (r == 1) {
+          if (lane == 0) *flag = 1;
+        } else if (r < 0) {
+          if (lane == 0) atomicCAS(Q.err, 0, DERR_STACK);  // the join is redone safely
+          break;
+        }
+      }
+      // their bytes count as parity bytes and as this launch's per-warp
+      // passes (the bytes_tasks counter)
+      const int ps[6] = {C_PARITY_RAYS, C_PARITY_NODES, C_PARITY_TRIS, C_BYTES, C_BYTES_PARITY,
+                         C_BYTES_TASKS};
+      const unsigned long long pv[6] = {pc.v[C_PARITY_RAYS], pc.v[C_PARITY_NODES],
+                                        pc.v[C_PARITY_TRIS], pc.v[C_BYTES], pc.v[C_BYTES],
+                                        pc.v[C_BYTES]};
+#pragma unroll
+      for (int i = 0; i < 6; ++i) {
+        unsigned long long v = pv[i];
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(FULL, v, o);
+        if (lane == 0 && v) atomicAdd(Q.counters + ps[i], v);
+      }
+      __syncwarp();
+    }
+  }
 
   // one leaf round: the triangles of up to np leaf pairs from the top of the
   // queue are copied to shared memory (cp.async, all at once), each leaf's
@@ -2255,7 +2314,13 @@ __global__ void __launch_bounds__(128, 4) k_stream(StreamArgs P) {
           if (ld_vol(reinterpret_cast<const unsigned *>(Q.err)) != 0u) break;  // failing
           const int av = *reinterpret_cast<volatile int *>(avail);
           if (av > 0) {
-            const int want = min(av, Cf::NT);  // (2 NT measured slower: hoarding)
+            // a share of what is published: the entries split over the
+            // waiting warps, at least kClaimMin and at most NT of them
+            // (claiming up to NT, or 2 NT, regardless left most waiting
+            // warps without work in the tail)
+            const unsigned hg = max(1u, ld_vol(sq(P, SQ_HUNGRY)));
+            const int want = min(min(av, Cf::NT),
+                                 max(kClaimMin, (int)(((unsigned)av + hg - 1u) / hg)));
             if (atomicSub(avail, want) >= want) {
               h = atomicAdd(sq(P, SQ_HEAD), (unsigned)want);
               atomicAdd(sq(P, SQ_ACTIVE), 1u);
@@ -3291,35 +3356,40 @@ pj_status run_join(Ctx *ctx, Dataset *A, Dataset *B, const int32_t *cand,
         args.single = -1;
         ctx->launches += C;
       } else if (front && stream) {
-        // parity rays (per thread, then the long ones per warp), then the
-        // streaming refinement in one persistent launch
+        // parity rays per thread, then the streaming refinement in one
+        // persistent launch, whose warps first take the rays the per-thread
+        // kernel handed over
         PJ_CK(cudaMemsetAsync(wctr, 0, sizeof(unsigned int) * wctr_words, s));
         PJ_CK(cudaMemsetAsync(d_flags, 0, (size_t)Ccap, s));
         WaveArgs wa = make_wave_args();
         // words: [0, SQ_WORDS) the streaming launch's control words, then the
-        // parity hand-over fill and position, a zero count and the intake
-        // position of the hand-over launch
+        // parity hand-over fill and claim position, a zero count and the
+        // intake position of a hand-over launch
         unsigned int *sc = wctr, *hc = wctr + SQ_WORDS;
         wa.q_par_n = hc;
-        RefineArgs ap = args;
-        ap.q_in = q1;
-        ap.q_in_n = hc + 2;
-        ap.q_in_pos = hc + 3;
-        ap.q_out = nullptr;
-        ap.q_out_n = nullptr;
-        ap.budget = 0;
-        ap.q_par = wpar;
-        ap.q_par_n = hc;
-        ap.q_par_pos = hc + 1;
-        ap.q_par_cap = wpar_cap;
         // the long rays go to warps before the traversal: a containment-only
         // pair (no crossing to stop at) is the costliest kind to traverse.
         // (Running the parity launches on a second stream beside the
         // streaming one measured slower: its persistent grid holds the SMs,
         // so the parity flags came late -- 0.445 against 0.437 ms a step.)
-        if (parity_rays) {
-          PJ_CK(launch_pdl(pick_wave_parity(W), wave_grid[2], 128, 0, s, wa));
+        if (parity_rays) PJ_CK(launch_pdl(pick_wave_parity(W), wave_grid[2], 128, 0, s, wa));
+        if (parity_rays && split) {
+          // contains / within: the streaming intake reads the parity results
+          // (it traverses only where they hold), so the long rays finish
+          // first, in a launch of their own
+          RefineArgs ap = args;
+          ap.q_in = q1;
+          ap.q_in_n = hc + 2;  // stays zero: no traversal tasks in this launch
+          ap.q_in_pos = hc + 3;
+          ap.q_out = nullptr;
+          ap.q_out_n = nullptr;
+          ap.budget = 0;
+          ap.q_par = wpar;
+          ap.q_par_n = hc;
+          ap.q_par_pos = hc + 1;
+          ap.q_par_cap = wpar_cap;
           PJ_CK(launch_pdl(kern_tasks, (int)blocks, threads, smem, s, ap));
+          ctx->launches += 1;
         }
         if (timed) PJ_CK(cudaEventRecord(ev[4], s));
         StreamArgs sa{};
@@ -3331,6 +3401,8 @@ pj_status run_join(Ctx *ctx, Dataset *A, Dataset *B, const int32_t *cand,
         sa.spin_limit = o->wait_polls > 0 ? (unsigned)o->wait_polls : (1u << 19);
         sa.hungry_max = 2u * (unsigned)ctx->num_sms;
         sa.give_after = 5000;
+        sa.q_par_pos = split ? nullptr : hc + 1;
+        sa.par_stack_cap = args.stack_cap;
         const bool kt = timed && !kev.empty();
         if (kt) PJ_CK(cudaEventRecord(kev[0], s));
         PJ_CK(launch_pdl(ks, stream_grid, 128, stream_smem, s, sa));
@@ -3342,7 +3414,7 @@ pj_status run_join(Ctx *ctx, Dataset *A, Dataset *B, const int32_t *cand,
           PJ_CK(cudaEventRecord(ev[5], s));
           phases = true;
         }
-        ctx->launches += 3;
+        ctx->launches += parity_rays ? 2 : 1;
       } else if (front) {
         // wavefront front end, then the warp passes over what is left
         PJ_CK(cudaMemsetAsync(d_misc + 2, 0, 48, s));  // work and spill counters
@@ -3531,8 +3603,8 @@ pj_status run_join(Ctx *ctx, Dataset *A, Dataset *B, const int32_t *cand,
   }
   PJ_CK(cudaEventRecord(e1, s));
   PJ_CK(cudaMemcpyAsync(h_misc, d_misc, 16, cudaMemcpyDeviceToHost, s));
-  int herr[4];
-  PJ_CK(cudaMemcpyAsync(herr, d_err, sizeof(herr), cudaMemcpyDeviceToHost, s));
+  int *herr = reinterpret_cast<int *>(h_misc + 4);  // pinned, beside the counts
+  PJ_CK(cudaMemcpyAsync(herr, d_err, sizeof(int) * 4, cudaMemcpyDeviceToHost, s));
   PJ_CK(cudaStreamSynchronize(s));
   if (herr[1]) return fail(ctx, PJ_ERR_INVALID_ARG, "a candidate mesh id is out of range");
   if (herr[2]) return fail(ctx, PJ_ERR_INVALID_ARG, "a translated candidate mesh leaves the 2^18 grid");
