@@ -52,7 +52,13 @@ pj_status exec_init(Ctx *ctx, Exec *e) {
 }
 
 void exec_free(Exec *e) {
-  for (auto &kv : e->ws) cudaFree(kv.second.ptr);
+  if (e->stream) {
+    for (auto &kv : e->ws)
+      if (kv.second.ptr) cudaFreeAsync(kv.second.ptr, e->stream);
+    cudaStreamSynchronize(e->stream);
+  } else {
+    for (auto &kv : e->ws) cudaFree(kv.second.ptr);
+  }
   e->ws.clear();
   cudaFree(e->d_err);
   cudaFreeHost(e->h_pinned);
@@ -69,11 +75,26 @@ void *ws_get(Ctx *ctx, const char *name, size_t bytes, pj_status *st) {
   Workspace &w = ex->ws[name];
   if (bytes == 0) bytes = 16;
   if (w.cap >= bytes) return w.ptr;
-  if (w.ptr) cudaFree(w.ptr);
-  w.ptr = nullptr;
-  w.cap = 0;
+  const size_t old_cap = w.cap;
+  w.zeroed = false;  // a new block, even at the same address, holds anything
   size_t want = bytes + bytes / 4;
-  cudaError_t e = cudaMalloc(&w.ptr, want);
+  cudaError_t e;
+  if (ex->stream) {
+    // a serving slot: the old block is released and the new one taken in
+    // the slot's stream order, so a growth does not wait for the batches of
+    // the other slots (cudaFree would wait for the whole device); it grows
+    // at least twofold, so that it grows a few times at most
+    want = std::max(want, 2 * old_cap);
+    if (w.ptr) cudaFreeAsync(w.ptr, ex->stream);
+    w.ptr = nullptr;
+    w.cap = 0;
+    e = cudaMallocAsync(&w.ptr, want, ex->stream);
+  } else {
+    if (w.ptr) cudaFree(w.ptr);
+    w.ptr = nullptr;
+    w.cap = 0;
+    e = cudaMalloc(&w.ptr, want);
+  }
   if (e != cudaSuccess) {
     cudaGetLastError();
     w.ptr = nullptr;

@@ -109,6 +109,9 @@ struct Exec {
   std::string err;           // last failure message of a serving thread
   bool borrow_out = false;   // join results stay in the workspaces (serving)
   cudaEvent_t ev[6] = {};    // a join's phase events, created once
+  // a serving slot's stream: its workspaces are released and taken in that
+  // stream's order (null: the API calls' scratch, plain cudaMalloc)
+  cudaStream_t stream = nullptr;
 };
 
 struct Serve;  // serving state (pj_serve.cu)

@@ -373,6 +373,7 @@ static pj_status serve_start(Ctx *ctx) {
       for (auto q : sv->streams) cudaStreamDestroy(q);
       return st;
     }
+    ex->stream = s;
     sv->execs.push_back(std::move(ex));
     sv->streams.push_back(s);
   }
@@ -397,11 +398,9 @@ void serve_stop(Ctx *ctx) {
   }
   sv->cv_work.notify_all();
   for (auto &t : sv->workers) t.join();
-  for (auto s : sv->streams) {
-    cudaStreamSynchronize(s);
-    cudaStreamDestroy(s);
-  }
-  for (auto &e : sv->execs) exec_free(e.get());
+  for (auto s : sv->streams) cudaStreamSynchronize(s);
+  for (auto &e : sv->execs) exec_free(e.get());  // on their streams
+  for (auto s : sv->streams) cudaStreamDestroy(s);
   delete sv;
   ctx->serve = nullptr;
 }
