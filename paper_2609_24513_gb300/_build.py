@@ -15,7 +15,7 @@ CSRC = os.path.join(HERE, "csrc")
 OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libpierce.so")
 SOURCES = ["pj_api.cu", "pj_bvh.cu", "pj_join.cu", "pj_tune.cu", "pj_serve.cu", "pj_estimate.cu",
-           "pj_dsjoin.cu", "pj_tiled.cu"]
+           "pj_dsjoin.cu", "pj_tiled.cu", "pj_mbb.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -219,6 +219,12 @@ pj_status run_segtri_batch(Ctx *ctx, const float *pq, const float *abc,
                            int64_t n, int mode, uint8_t *res,
                            int64_t *n_fallback, cudaStream_t s);
 
+// the bounding-box filter join by sort and sweep along x (pj_mbb.cu): the
+// candidate pairs in (id A, id B) order in the "cand" workspace, their count
+// in *d_count (device) and *C (host)
+pj_status mbb_sweep(Ctx *ctx, const Dataset *A, const Dataset *B, bool self_join,
+                    cudaStream_t s, int64_t *d_count, int32_t **d_cand, int64_t *C);
+
 // exclusive scan of n int64 values (device), total -> *d_total (device)
 pj_status scan_i64(Ctx *ctx, const int64_t *d_in, int64_t *d_out, int64_t n,
                    int64_t *d_total, cudaStream_t s);

@@ -3101,6 +3101,10 @@ pj_status run_join(Ctx *ctx, Dataset *A, Dataset *B, const int32_t *cand,
                                       de, polls);
         return cudaGetLastError();
       };
+    } else if (count_on_host && !safe) {
+      // too many pairs to test them all: sort and sweep along x
+      if ((st = mbb_sweep(ctx, A, B, self_join, s, d_misc, &d_cand, &C)) != PJ_OK) return st;
+      Ccap = C;
     } else {
       k_mbb<false><<<nb, MBB_T, 0, s>>>(A->d_aabb, MA, B->d_aabb, MB, self_join, counts, nullptr, nullptr);
       ++ctx->launches;
