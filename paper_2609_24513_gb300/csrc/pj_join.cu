@@ -865,27 +865,115 @@ __device__ int parity_query(const Side &T, int it, F3 toff, F3 vf, int ax, int d
   return parity | (on_any ? 2 : 0);
 }
 
+// Whether the exact point v lies on a triangle of mesh `it` of side T
+// (translated by toff), by one thread: a descent through the nodes whose
+// closed box contains v.  Every triangle through v lies in a leaf whose box
+// contains v, and a parity ray from v visits those leaves too, so this is
+// the ray walk's on-surface answer without the rest of the ray.  Returns 1 /
+// 0, or -1 when its stack (kPointStack entries) would overflow.
+constexpr int kPointStack = 64;
+
+template <int W>
+__device__ int point_on_surface(const Side &T, int it, int64_t tbase, F3 toff, F3 vf,
+                               unsigned long long &nodes, unsigned long long &tris) {
+  const I3 v = toi(vf);
+  uint32_t stk[kPointStack];
+  int sp = 0;
+  stk[sp++] = (uint32_t)T.roots[it];
+  while (sp > 0) {
+    const uint32_t node = stk[--sp];
+    nodes += 1;
+#pragma unroll 1
+    for (int c = 0; c < W; ++c) {
+      Box b;
+      uint32_t ch;
+      load_slot<W>(T.nodes, node, c, toff, b, ch);
+      if (ch == kEmpty || vf.x < b.lo.x || vf.x > b.hi.x || vf.y < b.lo.y || vf.y > b.hi.y ||
+          vf.z < b.lo.z || vf.z > b.hi.z)
+        continue;
+      if (ch & kLeafBit) {
+        const int64_t first = tbase + ((ch >> 3) & 0x0FFFFFFFu);
+        const int cntl = (int)(ch & 7u) + 1;
+        for (int t = 0; t < cntl; ++t) {
+          F3 a, bb, cc;
+          int own;
+          load_tri(T.trirec, first + t, toff, a, bb, cc, own);
+          tris += 1;
+          if (on_triangle(v, toi(a), toi(bb), toi(cc))) return 1;
+        }
+      } else {
+        if (sp >= kPointStack) return -1;
+        stk[sp++] = ch;
+      }
+    }
+  }
+  return 0;
+}
+
 // inside(Q_iq, T_it): representative vertex of Q (lexicographically smallest
 // not on T's surface) has odd +z parity against T.  A vertex outside T's
 // closed box is off T's surface and has even parity (T is closed), which
-// ends the search.  Returns 1/0, or -1 on a capacity error.
+// ends the search.  The first vertex takes one ray (it decides in most
+// pairs); if it lies on T's surface, the following vertices are checked 32 at
+// a time, one per lane, by point queries, and a ray runs for the first that
+// is not on the surface (a vertex whose query overflowed takes the ray,
+// which then decides whether it is on the surface).  Returns 1/0, or -1 on a
+// capacity error.
 template <int W>
 __device__ int pair_inside(const Side &Q, int iq, F3 qoff, const Side &T, int it, F3 toff,
                            WarpMem &sm, int lane, int stack_cap, int max_pop, Cnt &cnt) {
   const int64_t v0 = Q.voff[iq], nv = Q.voff[iq + 1] - v0;
   const float *tb = T.aabb + 6 * (int64_t)it;
   F3 lo = add(ld3(tb), toff), hi = add(ld3(tb + 3), toff);
-  for (int64_t k = 0; k < nv; ++k) {
-    int64_t vid = Q.lexorder[v0 + k];
-    F3 v = add(ld3(Q.xyz + 3 * vid), qoff);
+  auto outside = [&](F3 v) {
+    return v.x < lo.x || v.x > hi.x || v.y < lo.y || v.y > hi.y || v.z < lo.z || v.z > hi.z;
+  };
+  if (nv <= 0) return 0;
+  {
+    const F3 v = add(ld3(Q.xyz + 3 * Q.lexorder[v0]), qoff);
     if (lane == 0) cnt.v[C_BYTES] += 16;
-    if (v.x < lo.x || v.x > hi.x || v.y < lo.y || v.y > hi.y || v.z < lo.z || v.z > hi.z)
-      return 0;
+    if (outside(v)) return 0;
     int ax, dir;
     ray_axis_choice(v, lo, hi, ax, dir);
-    int r = parity_query<W>(T, it, toff, v, ax, dir, sm, lane, stack_cap, max_pop, cnt);
+    const int r = parity_query<W>(T, it, toff, v, ax, dir, sm, lane, stack_cap, max_pop, cnt);
     if (r < 0) return -1;
     if (!(r & 2)) return r & 1;
+  }
+  const int64_t tbase = T.toff[it];
+  for (int64_t k0 = 1; k0 < nv; k0 += 32) {
+    const int64_t k = k0 + lane;
+    // 0: on T's surface (skipped), 1: outside T's box, 2: off the surface,
+    // 3: not known (the query's stack overflowed)
+    int status = 0;
+    F3 v = mkf3(0.f, 0.f, 0.f);
+    if (k < nv) {
+      v = add(ld3(Q.xyz + 3 * Q.lexorder[v0 + k]), qoff);
+      if (outside(v)) {
+        status = 1;
+      } else {
+        unsigned long long nn = 0, tt = 0;
+        const int on = point_on_surface<W>(T, it, tbase, toff, v, nn, tt);
+        status = on == 1 ? 0 : (on == 0 ? 2 : 3);
+        cnt.v[C_PARITY_NODES] += nn;
+        cnt.v[C_PARITY_TRIS] += tt;
+        cnt.v[C_BYTES] += nn * W * 32 + tt * 48;
+      }
+      cnt.v[C_BYTES] += 16;
+    }
+    unsigned m = __ballot_sync(FULL, status != 0);
+    while (m) {
+      const int l = __ffs(m) - 1;
+      m &= m - 1;
+      const int st = __shfl_sync(FULL, status, l);
+      if (st == 1) return 0;
+      const F3 vl = mkf3(__shfl_sync(FULL, v.x, l), __shfl_sync(FULL, v.y, l),
+                         __shfl_sync(FULL, v.z, l));
+      int ax, dir;
+      ray_axis_choice(vl, lo, hi, ax, dir);
+      const int r = parity_query<W>(T, it, toff, vl, ax, dir, sm, lane, stack_cap, max_pop, cnt);
+      if (r < 0) return -1;
+      if (!(r & 2)) return r & 1;
+    }
   }
   return 0;
 }
