@@ -2850,6 +2850,9 @@ __global__ void __launch_bounds__(MBB_T) k_mbb1(const float *aabbA, int64_t MA,
   __shared__ unsigned s_tile;
   __shared__ long long s_wcnt[MBB_T / 32];
   __shared__ long long s_excl;
+  // when every B box fits one tile, the count pass keeps its ballot masks and
+  // the emit pass writes from them (no second load and test of the boxes)
+  __shared__ unsigned s_mask[MBB_T / 32][MBB_TILE / 32];
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
   constexpr int WPB = MBB_T / 32;
   const int64_t ntiles = (MA + WPB - 1) / WPB;
@@ -2872,25 +2875,37 @@ __global__ void __launch_bounds__(MBB_T) k_mbb1(const float *aabbA, int64_t MA,
     }
     // in a self join only j > i counts: tiles below the block's first i are skipped
     const int64_t jstart = self_join ? ((i0 + 1) / MBB_TILE) * MBB_TILE : 0;
+    const bool one = MB - jstart <= MBB_TILE;  // a single B tile: masks kept
     int64_t pos = 0;
     for (int pass = 0; pass < 2; ++pass) {
       int64_t cnt = 0;
       for (int64_t t0 = jstart; t0 < MB; t0 += MBB_TILE) {
         const int n = MB - t0 < MBB_TILE ? (int)(MB - t0) : MBB_TILE;
-        __syncthreads();  // the previous tile is no longer read
-        for (int k = threadIdx.x; k < n * 6; k += MBB_T) sb[k] = aabbB[6 * t0 + k];
-        __syncthreads();
+        const bool kept = one && pass == 1;
+        if (!kept) {
+          __syncthreads();  // the previous tile is no longer read
+          for (int k = threadIdx.x; k < n * 6; k += MBB_T) sb[k] = aabbB[6 * t0 + k];
+          __syncthreads();
+        }
         if (!has) continue;
         for (int j0 = 0; j0 < n; j0 += 32) {
           const int jj = j0 + lane;
           const int64_t j = t0 + jj;
-          bool ov = false;
-          if (jj < n && (!self_join || j > i)) {
-            const float *bb = sb + 6 * jj;
-            ov = ax0 <= bb[3] && bb[0] <= ax1 && ay0 <= bb[4] && bb[1] <= ay1 && az0 <= bb[5] &&
-                 bb[2] <= az1;
+          unsigned m;
+          bool ov;
+          if (kept) {
+            m = s_mask[wib][j0 >> 5];
+            ov = (m >> lane) & 1u;
+          } else {
+            ov = false;
+            if (jj < n && (!self_join || j > i)) {
+              const float *bb = sb + 6 * jj;
+              ov = ax0 <= bb[3] && bb[0] <= ax1 && ay0 <= bb[4] && bb[1] <= ay1 &&
+                   az0 <= bb[5] && bb[2] <= az1;
+            }
+            m = __ballot_sync(FULL, ov);
+            if (one && lane == 0) s_mask[wib][j0 >> 5] = m;
           }
-          const unsigned m = __ballot_sync(FULL, ov);
           if (pass == 1 && ov) {
             const int64_t p = pos + __popc(m & ((1u << lane) - 1u));
             cand[2 * p] = (int32_t)i;
