@@ -210,6 +210,11 @@ constexpr int MBB_T = 256;
 // hits in j order (ballot prefix), so candidates come out sorted by (i, j).
 // B boxes staged in shared memory per tile
 constexpr int MBB_TILE = 1024;
+// single-pass box join tiles: MBB_RPW A meshes per warp, MBB_TA per tile (a
+// tile is one block's unit of look-back; fewer, larger tiles fit the
+// resident grid in one round)
+constexpr int MBB_RPW = 2;
+constexpr int MBB_TA = (MBB_T / 32) * MBB_RPW;
 
 template <bool EMIT>
 __global__ void __launch_bounds__(MBB_T) k_mbb(const float *aabbA, int64_t MA,
@@ -2839,23 +2844,24 @@ __global__ void __launch_bounds__(CMP_T) k_compact(const uint8_t *flags, const i
 // take the tile's output offset by look-back, then test again and write.
 // Persistent blocks take tiles from the ticket counter until none is left;
 // the last tile writes the candidate count.
-__global__ void __launch_bounds__(MBB_T) k_mbb1(const float *aabbA, int64_t MA,
+__global__ void __launch_bounds__(MBB_T, 5) k_mbb1(const float *aabbA, int64_t MA,
                                                const float *aabbB, int64_t MB, int self_join,
                                                unsigned *ticket, unsigned long long *state,
                                                int32_t *cand, int64_t *count, int *err,
                                                unsigned spin_limit) {
   pdl_wait();
   pdl_trigger();
+  constexpr int WPB = MBB_T / 32;
   __shared__ float sb[MBB_TILE * 6];
   __shared__ unsigned s_tile;
-  __shared__ long long s_wcnt[MBB_T / 32];
+  __shared__ long long s_wcnt[MBB_RPW][WPB];
   __shared__ long long s_excl;
   // when every B box fits one tile, the count pass keeps its ballot masks and
   // the emit pass writes from them (no second load and test of the boxes)
-  __shared__ unsigned s_mask[MBB_T / 32][MBB_TILE / 32];
+  __shared__ unsigned s_mask[MBB_RPW][WPB][MBB_TILE / 32];
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
-  constexpr int WPB = MBB_T / 32;
-  const int64_t ntiles = (MA + WPB - 1) / WPB;
+  const unsigned lt = (1u << lane) - 1u;
+  const int64_t ntiles = (MA + MBB_TA - 1) / MBB_TA;
   if (ntiles == 0) {
     if (blockIdx.x == 0 && threadIdx.x == 0) *count = 0;
     return;
@@ -2866,19 +2872,29 @@ __global__ void __launch_bounds__(MBB_T) k_mbb1(const float *aabbA, int64_t MA,
     __syncthreads();
     const unsigned tile = s_tile;
     if ((int64_t)tile >= ntiles) return;
-    const int64_t i0 = (int64_t)tile * WPB, i = i0 + wib;
-    const bool has = i < MA;
-    float ax0 = 0.f, ay0 = 0.f, az0 = 0.f, ax1 = -1.f, ay1 = -1.f, az1 = -1.f;
-    if (has) {
-      const float *a = aabbA + 6 * i;
-      ax0 = a[0], ay0 = a[1], az0 = a[2], ax1 = a[3], ay1 = a[4], az1 = a[5];
+    // the tile's A meshes i0 + r WPB + warp: candidate order is mesh order,
+    // so the offsets run over (r, warp)
+    const int64_t i0 = (int64_t)tile * MBB_TA;
+    int64_t ii[MBB_RPW];
+    bool has[MBB_RPW];
+    float ab[MBB_RPW][6];
+#pragma unroll
+    for (int r = 0; r < MBB_RPW; ++r) {
+      ii[r] = i0 + r * WPB + wib;
+      has[r] = ii[r] < MA;
+#pragma unroll
+      for (int q = 0; q < 6; ++q) ab[r][q] = has[r] ? aabbA[6 * ii[r] + q] : (q < 3 ? 0.f : -1.f);
     }
     // in a self join only j > i counts: tiles below the block's first i are skipped
     const int64_t jstart = self_join ? ((i0 + 1) / MBB_TILE) * MBB_TILE : 0;
     const bool one = MB - jstart <= MBB_TILE;  // a single B tile: masks kept
-    int64_t pos = 0;
+    int64_t pos[MBB_RPW];
+#pragma unroll
+    for (int r = 0; r < MBB_RPW; ++r) pos[r] = 0;
     for (int pass = 0; pass < 2; ++pass) {
-      int64_t cnt = 0;
+      int64_t cnt[MBB_RPW];
+#pragma unroll
+      for (int r = 0; r < MBB_RPW; ++r) cnt[r] = 0;
       for (int64_t t0 = jstart; t0 < MB; t0 += MBB_TILE) {
         const int n = MB - t0 < MBB_TILE ? (int)(MB - t0) : MBB_TILE;
         const bool kept = one && pass == 1;
@@ -2887,43 +2903,56 @@ __global__ void __launch_bounds__(MBB_T) k_mbb1(const float *aabbA, int64_t MA,
           for (int k = threadIdx.x; k < n * 6; k += MBB_T) sb[k] = aabbB[6 * t0 + k];
           __syncthreads();
         }
-        if (!has) continue;
-        for (int j0 = 0; j0 < n; j0 += 32) {
-          const int jj = j0 + lane;
-          const int64_t j = t0 + jj;
-          unsigned m;
-          bool ov;
-          if (kept) {
-            m = s_mask[wib][j0 >> 5];
-            ov = (m >> lane) & 1u;
-          } else {
-            ov = false;
-            if (jj < n && (!self_join || j > i)) {
-              const float *bb = sb + 6 * jj;
-              ov = ax0 <= bb[3] && bb[0] <= ax1 && ay0 <= bb[4] && bb[1] <= ay1 &&
-                   az0 <= bb[5] && bb[2] <= az1;
+#pragma unroll
+        for (int r = 0; r < MBB_RPW; ++r) {
+          if (!has[r]) continue;
+          const int64_t i = ii[r];
+          for (int j0 = 0; j0 < n; j0 += 32) {
+            const int jj = j0 + lane;
+            const int64_t j = t0 + jj;
+            unsigned m;
+            bool ov;
+            if (kept) {
+              m = s_mask[r][wib][j0 >> 5];
+              ov = (m >> lane) & 1u;
+            } else {
+              ov = false;
+              if (jj < n && (!self_join || j > i)) {
+                const float *bb = sb + 6 * jj;
+                ov = ab[r][0] <= bb[3] && bb[0] <= ab[r][3] && ab[r][1] <= bb[4] &&
+                     bb[1] <= ab[r][4] && ab[r][2] <= bb[5] && bb[2] <= ab[r][5];
+              }
+              m = __ballot_sync(FULL, ov);
+              if (one && lane == 0) s_mask[r][wib][j0 >> 5] = m;
             }
-            m = __ballot_sync(FULL, ov);
-            if (one && lane == 0) s_mask[wib][j0 >> 5] = m;
+            if (pass == 1 && ov) {
+              const int64_t p = pos[r] + __popc(m & lt);
+              cand[2 * p] = (int32_t)i;
+              cand[2 * p + 1] = (int32_t)j;
+            }
+            if (pass == 1) pos[r] += __popc(m);
+            else cnt[r] += __popc(m);
           }
-          if (pass == 1 && ov) {
-            const int64_t p = pos + __popc(m & ((1u << lane) - 1u));
-            cand[2 * p] = (int32_t)i;
-            cand[2 * p + 1] = (int32_t)j;
-          }
-          if (pass == 1) pos += __popc(m);
-          else cnt += __popc(m);
         }
       }
       if (pass == 1) break;
-      // the tile's count, its offset by look-back, each warp's start
-      if (lane == 0) s_wcnt[wib] = cnt;
-      __syncthreads();
-      long long agg = 0, before = 0;
-      for (int k = 0; k < WPB; ++k) {
-        before += k < wib ? s_wcnt[k] : 0;
-        agg += s_wcnt[k];
+      // the tile's count, its offset by look-back, each (r, warp)'s start
+      if (lane == 0) {
+#pragma unroll
+        for (int r = 0; r < MBB_RPW; ++r) s_wcnt[r][wib] = cnt[r];
       }
+      __syncthreads();
+      long long agg = 0, before[MBB_RPW];
+#pragma unroll
+      for (int r = 0; r < MBB_RPW; ++r) before[r] = 0;
+      for (int r2 = 0; r2 < MBB_RPW; ++r2)
+        for (int k = 0; k < WPB; ++k) {
+          const long long c = s_wcnt[r2][k];
+          agg += c;
+#pragma unroll
+          for (int r = 0; r < MBB_RPW; ++r)
+            if (r2 < r || (r2 == r && k < wib)) before[r] += c;
+        }
       if (threadIdx.x == 0)
         lb_publish(state, tile, (tile == 0 ? LB_INC : LB_AGG) | (unsigned long long)agg);
       if (wib == 0) {
@@ -2940,7 +2969,8 @@ __global__ void __launch_bounds__(MBB_T) k_mbb1(const float *aabbA, int64_t MA,
       }
       __syncthreads();
       if (s_excl < 0) return;  // (the whole block: s_excl is shared)
-      pos = s_excl + before;
+#pragma unroll
+      for (int r = 0; r < MBB_RPW; ++r) pos[r] = s_excl + before[r];
     }
   }
 }
@@ -3178,11 +3208,11 @@ pj_status run_join(Ctx *ctx, Dataset *A, Dataset *B, const int32_t *cand,
       count_on_host = false;
     }
     if (!count_on_host && !safe) {
-      // one launch: count, offset by look-back, emit (tiles of 8 A meshes);
+      // one launch: count, offset by look-back, emit (tiles of MBB_TA A meshes);
       // it is part of the device sequence below (captured with it)
       d_cand = (int32_t *)ws_get(ctx, "cand", sizeof(int32_t) * 2 * (size_t)Ccap, &st);
       if (!d_cand) return st;
-      const int64_t tiles = (MA + (MBB_T / 32) - 1) / (MBB_T / 32);
+      const int64_t tiles = (MA + MBB_TA - 1) / MBB_TA;
       unsigned long long *lb =
           (unsigned long long *)ws_get(ctx, "mbb_lookback", 8 * (size_t)(tiles + 1), &st);
       if (!lb) return st;
