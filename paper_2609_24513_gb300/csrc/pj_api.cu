@@ -173,6 +173,60 @@ void pool_release(Ctx *ctx) {
   }
   ctx->pool.clear();
   ctx->pool_bytes = 0;
+  for (auto &kv : ctx->hpool) {
+    cudaFreeHost(kv.second);
+    ctx->hpool_cap.erase(kv.second);
+  }
+  ctx->hpool.clear();
+  ctx->hpool_bytes = 0;
+}
+
+void *hpool_get(Ctx *ctx, size_t bytes, cudaError_t *e) {
+  *e = cudaSuccess;
+  auto it = ctx->hpool.lower_bound(bytes);
+  if (it != ctx->hpool.end() && it->first <= 4 * std::max<size_t>(bytes, 4096)) {
+    void *p = it->second;
+    ctx->hpool_bytes -= it->first;
+    ctx->hpool.erase(it);
+    return p;
+  }
+  size_t cap = 4096;
+  while (cap < bytes) cap *= 2;
+  void *p = nullptr;
+  *e = cudaMallocHost(&p, cap);
+  if (*e != cudaSuccess) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  ctx->hpool_cap[p] = cap;
+  return p;
+}
+
+void hpool_put(Ctx *ctx, void *p) {
+  if (!p) return;
+  auto it = ctx->hpool_cap.find(p);
+  if (it == ctx->hpool_cap.end()) {
+    cudaFreeHost(p);
+    return;
+  }
+  if (ctx->hpool_bytes + it->second > (size_t(1) << 28)) {
+    cudaFreeHost(p);
+    ctx->hpool_cap.erase(it);
+    return;
+  }
+  ctx->hpool.emplace(it->second, p);
+  ctx->hpool_bytes += it->second;
+}
+
+void pairs_release(Ctx *ctx, pj_pairs *r) {
+  if (r->pairs) {
+    if (r->on_device) pool_put(ctx, r->pairs);
+    else if (r->pairs_malloc) free(r->pairs);
+    else hpool_put(ctx, r->pairs);
+  }
+  pool_put(ctx, r->flags);
+  pool_put(ctx, r->cycles);
+  memset(r, 0, sizeof(*r));
 }
 
 // ---------------------------------------------------------------------------
@@ -824,14 +878,7 @@ pj_status pj_free_pairs(pj_ctx *h, pj_pairs *res) {
   if (!ctx || !res) return PJ_ERR_INVALID_ARG;
   std::lock_guard<std::mutex> lk(ctx->mu);
   cudaSetDevice(ctx->device);
-  if (res->pairs) {
-    if (res->on_device) pool_put(ctx, res->pairs);
-    else if (res->pairs_malloc) free(res->pairs);
-    else cudaFreeHost(res->pairs);
-  }
-  pool_put(ctx, res->flags);
-  pool_put(ctx, res->cycles);
-  memset(res, 0, sizeof(*res));
+  pairs_release(ctx, res);
   return PJ_OK;
 }
 

@@ -652,7 +652,7 @@ pj_status run_dataset_join(Ctx *ctx, Dataset *A, Dataset *B, int self_join,
     for (int64_t k = 0; k < r.count; ++k)
       extra.push_back(((unsigned long long)(unsigned)r.pairs[2 * k] << 32) |
                       (unsigned)r.pairs[2 * k + 1]);
-    cudaFreeHost(r.pairs);
+    pairs_release(ctx, &r);
   }
   // 4. sort and unique (with the rechecked pairs), then (idA, idB)
   PJ_CK(cudaEventRecord(ev[5], s));

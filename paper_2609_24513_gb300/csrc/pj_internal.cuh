@@ -144,6 +144,10 @@ struct Ctx {
   std::multimap<size_t, void *> pool;
   std::map<void *, size_t> pool_cap;
   size_t pool_bytes = 0;  // capacity of the free buffers
+  // the same for host results (pinned memory: cudaMallocHost / cudaFreeHost)
+  std::multimap<size_t, void *> hpool;
+  std::map<void *, size_t> hpool_cap;
+  size_t hpool_bytes = 0;
 };
 
 // A device buffer of at least `bytes` from the context's result pool (or a
@@ -152,7 +156,13 @@ void *pool_get(Ctx *c, size_t bytes, cudaError_t *e);
 // Give a buffer back: pooled if the pool made it (and the free buffers stay
 // under 1 GiB), else cudaFree.  The caller's work on it must be complete.
 void pool_put(Ctx *c, void *p);
-void pool_release(Ctx *c);  // cudaFree every free pooled buffer
+void pool_release(Ctx *c);  // free every free pooled buffer (device and host)
+// Pinned host buffers for host results, pooled the same way (under 256 MiB
+// of free buffers); a pointer the pool did not make is cudaFreeHost'ed.
+void *hpool_get(Ctx *c, size_t bytes, cudaError_t *e);
+void hpool_put(Ctx *c, void *p);
+// Release a result's buffers (pairs, flags, cycles) to where they came from.
+void pairs_release(Ctx *c, pj_pairs *r);
 
 // The scratch the calling thread works with: a serving thread's own, else
 // the context's.

@@ -3805,7 +3805,9 @@ pj_status run_join(Ctx *ctx, Dataset *A, Dataset *B, const int32_t *cand,
   }
   size_t bytes = sizeof(int32_t) * 2 * (size_t)std::max<int64_t>(K, 1);
   if (o->out_host) {
-    PJ_CK(cudaMallocHost((void **)&out->pairs, bytes));
+    cudaError_t pe;
+    out->pairs = (int32_t *)hpool_get(ctx, bytes, &pe);
+    PJ_CK(pe);
     out->on_device = 0;
     if (K > 0) PJ_CK(cudaMemcpyAsync(out->pairs, d_pairs, sizeof(int32_t) * 2 * K, cudaMemcpyDeviceToHost, s));
   } else {

@@ -241,7 +241,7 @@ pj_status run_join_tiled(Ctx *ctx, const pj_host_meshes *Am, const pj_host_meshe
     free_dataset(DA);
     if (!self_join && db) free_dataset(DB);
     if (st != PJ_OK) {
-      if (r.pairs) cudaFreeHost(r.pairs);
+      pairs_release(ctx, &r);
       if (n + 1 < todo.size()) next.get();
       return st;
     }
@@ -258,7 +258,7 @@ pj_status run_join_tiled(Ctx *ctx, const pj_host_meshes *Am, const pj_host_meshe
       if (rx == cx && ry == cy && rz == cz)
         keys.push_back(((unsigned long long)(unsigned)i << 32) | (unsigned)j);
     }
-    if (r.pairs) cudaFreeHost(r.pairs);
+    pairs_release(ctx, &r);
     t_device += now() - t0;
   }
   std::sort(keys.begin(), keys.end());

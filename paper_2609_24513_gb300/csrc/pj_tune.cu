@@ -111,9 +111,7 @@ pj_status run_autotune(Ctx *ctx, Dataset *A, Dataset *B, const int32_t *cand, in
                               ctx->stream, &res);
             if (result != PJ_OK) break;
             if (r > 0) t.push_back(res.device_ms);  // the first run warms up
-            if (res.pairs) {
-              if (res.on_device) cudaFree(res.pairs); else cudaFreeHost(res.pairs);
-            }
+            pairs_release(ctx, &res);
           }
           if (result != PJ_OK) break;
           std::sort(t.begin(), t.end());
