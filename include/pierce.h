@@ -300,7 +300,10 @@ pj_status pj_join_intersects_ex(pj_ctx *ctx, pj_dataset a, pj_dataset b,
 /* Free a join result.  Device buffers (pairs with out_host = 0, flags,
  * cycles) go back to a pool of the context that later joins reuse instead of
  * calling cudaMalloc / cudaFree: any work of the caller that reads them must
- * have completed (pj_destroy frees the pool). */
+ * have completed.  Host pairs of pj_join_intersects[_ex] (out_host = 1) are
+ * pinned buffers that go back to a pool of their own the same way
+ * (cudaMallocHost / cudaFreeHost are not paid per join); the caller must not
+ * touch them afterwards.  pj_destroy frees both pools. */
 pj_status pj_free_pairs(pj_ctx *ctx, pj_pairs *res);
 
 /* The join's device part with no allocation at all (the paper has no
